@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Benchmark of the mode-wise flexible st-HOSVD on B300: input GB/s.
+
+One step = one full st-HOSVD (Alg. 2) of each tensor of the workload:
+  * 640 x 640 x 640, ranks (64, 64, 64)
+  * 128 x 128 x 128 x 128, ranks (16, 16, 16, 16)
+Both are random Tucker tensors plus 1e-3 N(0,1) noise (synthetic).  They are
+float32, column-major, and resident in HBM before the timed region.  Each
+tensor (1.05 GB and 1.07 GB) is larger than the 126 MB L2, so nothing is
+flushed between steps.
+metric = sum of input bytes / step time.
+
+Printed JSON line (one, rank 0): value, e2e (host buffers through the C ABI,
+copies included), roofline of the dominant kernel (timed live with CUDA events
+inside the library on the launching stream), the CPU oracle baseline on a
+bounded sample, clocks sampled during the timed region, and kernel launches.
+
+``--impl reference`` times the CPU oracle (float64, explicit matricization) on
+a bounded sample of the same workload, per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "st-HOSVD input GB/s"
+UNIT = "GB/s"
+TENSORS = [((640, 640, 640), (64, 64, 64)), ((128, 128, 128, 128), (16, 16, 16, 16))]
+WORKLOAD = "plain FP32 st-HOSVD (EIG every mode): 640^3 R64 + 128^4 R16, random Tucker + 1e-3 noise"
+FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+CPU_SAMPLE = ((640, 640, 8), (64, 64, 8))       # cpu_baseline: a 640 x 640 x 8 slab of the workload
+REF_SAMPLE = ((640, 160, 8), (64, 64, 8))       # reference arm: one such slab sample per step
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def gram_flops(dims, ranks, solver, mode_order=None):
+    """Algorithmic Gram flops of one st-HOSVD, I_n^2 J_n per EIG mode (Eq. 4)."""
+    cur = list(dims)
+    total = 0.0
+    for n in (mode_order or range(len(dims))):
+        J = float(np.prod(cur)) / cur[n]
+        if solver[n] == 0:
+            total += float(cur[n]) ** 2 * J
+        cur[n] = ranks[n]
+    return total
+
+
+class ClockSampler:
+    """nvidia-smi clocks during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def cpu_oracle_sample(sample, reps=1):
+    import oracle
+    import synth
+    dims, ranks = sample
+    x, _, _ = synth.random_tucker(dims, ranks, seed=0)
+    x64 = x.astype(np.float64)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.sthosvd(x64, dims, ranks, solver=[0] * len(dims))
+        times.append(time.perf_counter() - t0)
+    return x.nbytes, times
+
+
+def run_reference(args):
+    rank, ws, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401  (builds the C oracle once before timing)
+    oracle.build()
+    dims, ranks = REF_SAMPLE
+    import synth
+    x, _, _ = synth.random_tucker(dims, ranks, seed=0)
+    x64 = x.astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.sthosvd(x64, dims, ranks, solver=[0] * len(dims))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sthosvd(x64, dims, ranks, solver=[0] * len(dims))
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    gbs = x.nbytes / dt / 1e9
+    cores = os.cpu_count()
+    sample = f"oracle st-HOSVD-EIG (float64, OpenMP loops) of a {dims[0]}x{dims[1]}x{dims[2]} slab sample, ranks {ranks}"
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": gbs, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbs, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, ws, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+    torch.cuda.set_device(local)
+    import paper_2010_10131_b300 as atk
+    import synth
+    atk.lib()
+    stream = torch.cuda.current_stream()
+    plans, xs, hosts = [], [], []
+    for dims, ranks in TENSORS:
+        x, _, _ = synth.random_tucker(dims, ranks, seed=rank)
+        xt = torch.from_numpy(x).cuda()
+        p = atk.Plan(dims, ranks, solver=[0] * len(dims), stream=stream)
+        core = torch.empty(p.core_numel, device="cuda")
+        fac = torch.empty(p.factors_numel, device="cuda")
+        plans.append((p, core, fac))
+        xs.append(xt)
+        hosts.append(torch.from_numpy(x).pin_memory())
+    in_bytes = sum(int(np.prod(d)) * 4 for d, _ in TENSORS)
+
+    def step():
+        for (p, core, fac), x in zip(plans, xs):
+            p.run(x, core, fac)
+
+    for _ in range(args.warmup):
+        step()
+    for p, _, _ in plans:
+        p.sync()
+        p.set_timing(True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1) / max(args.steps, 1)
+    for p, _, _ in plans:
+        p.sync()
+    tims = [p.timings() for p, _, _ in plans]
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = in_bytes * ws / (ms * 1e-3) / 1e9
+
+    # Dominant kernel: the Gram partial-tile kernel (float32 CUDA cores).
+    gram_ms = sum(t["gram"] for t in tims)
+    flops = sum(gram_flops(d, r, [0] * len(d)) for d, r in TENSORS) * args.steps
+    achieved = flops / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None
+    phases = {k: sum(t[k] for t in tims) / max(args.steps, 1) for k in
+              ("gram", "gram_reduce", "eig", "ttm", "als", "norms", "total")}
+    launches = int(sum(t["launches"] for t in tims))
+
+    # End to end through the C ABI with host buffers (copies inside the timed region).
+    cores_h = [torch.empty(p.core_numel).pin_memory() for p, _, _ in plans]
+    facs_h = [torch.empty(p.factors_numel).pin_memory() for p, _, _ in plans]
+    for (p, _, _), xh, ch, fh in zip(plans, hosts, cores_h, facs_h):
+        p.run_host(xh, ch, fh)
+    e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for (p, _, _), xh, ch, fh in zip(plans, hosts, cores_h, facs_h):
+            p.run_host(xh, ch, fh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    d2h = sum((p.core_numel + p.factors_numel) * 4 for p, _, _ in plans)
+
+    line = None
+    if rank == 0:
+        pk = peaks()
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            nb, ts = cpu_oracle_sample(CPU_SAMPLE)
+            cpu = {"value": nb / min(ts) / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"oracle st-HOSVD-EIG of one {CPU_SAMPLE[0]} slab of the workload, ranks "
+                             f"{CPU_SAMPLE[1]} ({min(ts):.1f} s)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tensors": [list(d) for d, _ in TENSORS],
+                       "ranks": [list(r) for _, r in TENSORS], "solver": "EIG every mode",
+                       "precision": "FP32 CUDA cores", "l2": "inputs (1.05 GB, 1.07 GB) larger than L2; no flush"},
+            "roofline": {"bound": "alu", "kernel": "gram_ci_kernel (float32 FMA)",
+                         "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": (achieved / FP32_ALU_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                         "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
+                         "flops_per_step": flops / max(args.steps, 1),
+                         "ms_per_step": gram_ms / max(args.steps, 1)},
+            "phases_ms_per_step": phases,
+            "e2e": {"value": in_bytes / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "hbm_peak_gbs": pk.get("hbm_gbs"),
+        }
+        print(json.dumps(line), flush=True)
+    for p, _, _ in plans:
+        p.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * atucker.h: C ABI of the B300 (sm_103a) mode-wise flexible st-HOSVD library.
+ *
+ * Method: a-Tucker (Li, Xiao, Yang; arXiv 2010.10131).  Alg. 2 is the
+ * mode-wise flexible st-HOSVD.  Per mode it runs either the EIG solver (Gram
+ * S = Y_(n) Y_(n)^T, its leading R_n eigenvectors, then the truncating TTM) or
+ * the ALS solver (Alg. 3, then QR of L, then TTM of the ALS factor by R^).
+ * Every tensor operation is matricization-free (Sec. V).  The tensor stays in
+ * its natural column-major layout, and mode n is viewed as a batch of
+ * (I_<n, I_n, I_>n) slabs.
+ *
+ * Conventions (apply to every entry point):
+ *   - Tensors are dense float32 and column-major, first index fastest (Sec. V).
+ *     A C-contiguous torch tensor of shape (d_N, ..., d_1) is the column-major
+ *     (d_1, ..., d_N) tensor.
+ *   - Matrices are column-major.  Factor U^(n) is I_n x R_n (Sec. II-B).
+ *   - Modes are 0-based; the paper counts from 1.
+ *   - Unless a parameter says "host", every pointer is a device pointer that the
+ *     caller owns.  The library never frees caller memory and never writes to
+ *     input tensors.
+ *   - `stream` is a cudaStream_t passed as void*.  NULL means the legacy default
+ *     stream.  Work is stream-ordered.  Calls return when the work is enqueued,
+ *     unless they are documented as synchronous.
+ *   - Every call returns an atucker_status.  On failure, atucker_last_error()
+ *     returns a thread-local message.  A status of ATK_ECUDA means the CUDA
+ *     runtime reported an error.  The library does not reset the device.
+ *   - Size limits: order <= 8, every I_n <= 1024 for EIG modes (Gram + Jacobi),
+ *     R_n <= 128, and the tensor has fewer than 2^31 elements.
+ */
+#ifndef ATUCKER_H
+#define ATUCKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ATK_OK = 0,
+  ATK_EINVAL = -1,   /* bad argument (null pointer, bad order, bad permutation) */
+  ATK_ERANK = -2,    /* infeasible ranks: need 1 <= R_n <= I_n and R_n <= prod_{k!=n} R_k,
+                        or a Cholesky factorisation inside ALS met a non-positive pivot */
+  ATK_ENOMEM = -3,   /* device allocation failed */
+  ATK_ECUDA = -4,    /* CUDA runtime error */
+  ATK_ENOCONV = -5,  /* the Jacobi eigensolver hit its sweep cap (results still written) */
+  ATK_ETIMEOUT = -6, /* a bounded device-side wait gave up (grid barrier) */
+  ATK_EUNSUPPORTED = -7 /* a size limit above was exceeded */
+} atucker_status;
+
+/* Per-mode solver, Alg. 2: 0 = EIG (Gram + eigen-decomposition), 1 = ALS (Alg. 3). */
+typedef enum { ATK_EIG = 0, ATK_ALS = 1 } atucker_solver;
+
+/* Arithmetic for the bulk Gram / TTM / ALS contractions.
+ * ATK_FP32 is plain float32 on the CUDA cores, accumulated in float32 and
+ * reduced in float64 across split-K partials. */
+typedef enum { ATK_FP32 = 0 } atucker_precision;
+
+/* Arithmetic of the Jacobi rotations in the eigensolver.  Either way, the
+ * Gram arrives in float64, and eigenvalue sums and the final
+ * orthonormalisation of U run in float64. */
+typedef enum { ATK_EIG_ROT_FP32 = 0, ATK_EIG_ROT_FP64 = 1 } atucker_eig_arith;
+
+/* Keys for atucker_plan_set_option. */
+typedef enum {
+  ATK_OPT_EIG_ARITH = 1,  /* atucker_eig_arith; default ATK_EIG_ROT_FP32 */
+  ATK_OPT_SYNC = 2,       /* 1: atucker_sthosvd synchronises and returns the device status (default 0) */
+  ATK_OPT_JACOBI_MAX_SWEEPS = 3, /* sweep cap of the Jacobi eigensolver (default 40) */
+  ATK_OPT_TIMING = 4      /* 1: record CUDA events around each phase (see atucker_plan_timings) */
+} atucker_option;
+
+typedef struct atucker_plan_s* atucker_plan_t;
+
+/* Build a plan for one tensor shape (Alg. 2 inputs, Sec. III-A).
+ *   order            N, 1 <= N <= 8
+ *   dims, ranks      host arrays of N entries: I_n and R_n
+ *   mode_order       host permutation of 0..N-1: the order modes are processed
+ *                    in (the paper's loop runs n = 1..N); NULL = 0,1,..,N-1
+ *   solver_per_mode  host array of N atucker_solver values indexed by mode;
+ *                    NULL = EIG for every mode
+ *   precision        atucker_precision
+ *   als_sweeps       ALS iterations (num_iters of Eq. 5; the paper's default is
+ *                    5); <= 0 selects 5
+ *   seed             seed of the ALS initial guess L_0.  For mode n, entry
+ *                    e = i + I_n r (column-major) is sqrt(-2 ln u1) cos(2 pi u2),
+ *                    with u1 = (w(2e+1) + 1) 2^-53 and u2 = w(2e+2) 2^-53.  Here
+ *                    w(c) is the top 53 bits of mix(s + c * 0x9E3779B97F4A7C15),
+ *                    with s = seed ^ (0x9E3779B97F4A7C15 * (n + 1)) and mix the
+ *                    splitmix64 output function.
+ *   stream           cudaStream_t used by every call on this plan
+ * The plan allocates its device workspace: two ping-pong buffers for the
+ * shrinking core, the Gram split-K scratch, and the small matrices.
+ * Returns ATK_ERANK for infeasible ranks, ATK_EUNSUPPORTED beyond the size
+ * limits, ATK_ENOMEM if the workspace cannot be allocated. */
+int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
+                        const int* mode_order, const int* solver_per_mode, int precision, int als_sweeps,
+                        uint64_t seed, void* stream);
+
+/* Set a plan option (atucker_option).  Returns ATK_EINVAL for unknown keys/values. */
+int atucker_plan_set_option(atucker_plan_t plan, int key, int64_t value);
+
+/* Run Alg. 2 on the device tensor x (I_1 x ... x I_N, column-major, not modified).
+ *   core_out      device, R_1 x ... x R_N column-major float32
+ *   factors_out   device, U^(1) .. U^(N) in mode-index order (not processing
+ *                 order), each I_n x R_n column-major float32, concatenated
+ *   discarded_out device, N float64 (nullable): energy removed at mode n's
+ *                 step.  EIG: the sum of the Gram eigenvalues beyond R_n.
+ *                 ALS: ||Y||^2 - ||Y'||^2.  With EIG modes only,
+ *                 ||X - X_hat||^2 = sum of these.
+ * Eigenvectors are ordered by descending eigenvalue.  Each column is signed
+ * so that its largest-magnitude entry is positive.  ALS factors come from a QR
+ * with positive diag(R^).
+ * Asynchronous on the plan's stream unless ATK_OPT_SYNC is set.  Device-side
+ * conditions (Jacobi sweep cap, barrier timeout) are reported by the next
+ * atucker_plan_sync. */
+int atucker_sthosvd(atucker_plan_t plan, const float* x, float* core_out, float* factors_out,
+                    double* discarded_out);
+
+/* Same as atucker_sthosvd, with HOST buffers (preferably pinned).  Copies x to
+ * the device, runs, copies core/factors/discarded back, and synchronises.
+ * discarded_out is host, nullable.  The plan keeps a device copy buffer for x,
+ * allocated on first use. */
+int atucker_sthosvd_host(atucker_plan_t plan, const float* x_host, float* core_host, float* factors_host,
+                         double* discarded_host);
+
+/* Wait for the plan's stream and return the device status word of the last
+ * run: ATK_OK, ATK_ENOCONV or ATK_ETIMEOUT. */
+int atucker_plan_sync(atucker_plan_t plan);
+
+/* Device time per phase of the runs since timing was enabled or last read,
+ * from CUDA events recorded on the plan's stream (ATK_OPT_TIMING = 1).
+ * Synchronises the stream.  out (host, count >= 10):
+ *   [0] Gram partial-tile kernel ms   [1] Gram split-K reduction ms
+ *   [2] eigensolver ms (Jacobi, selection, float64 polish)
+ *   [3] TTM ms   [4] ALS mode ms   [5] norms ms   [6] total ms
+ *   [7] Gram kernel launches   [8] kernel launches of this library   [9] runs
+ * Resets the accumulators. */
+int atucker_plan_timings(atucker_plan_t plan, double* out, int count);
+
+/* Free the plan and its workspace.  Safe on NULL. */
+void atucker_plan_destroy(atucker_plan_t plan);
+
+/* One-shot form of the problem statement (Alg. 2): plan, run synchronously on
+ * the default stream in FP32, free.  Device pointers as in atucker_sthosvd. */
+int atucker_sthosvd_oneshot(const float* x, int order, const int64_t* dims, const int64_t* ranks,
+                            const int* mode_order, const int* solver_per_mode, float* core_out,
+                            float* factors_out);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* atucker_last_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* atucker_version(void);
+
+/* ------------------------------------------------------------------------
+ * Step-level entry points: one row of the hot path each, on a mode-n slab view
+ * (lo, n, hi) = (I_<n, I_n, I_>n) of a column-major tensor.  Element (a, i, b)
+ * sits at a + lo * (i + n * b) (Sec. V: loops split outside/along/inside mode
+ * n).  Each call allocates its own scratch from the stream-ordered allocator
+ * and frees it before returning.
+ * ------------------------------------------------------------------------ */
+
+/* Gram matrix S = Y_(n) Y_(n)^T (Alg. 2, EIG branch; cost I_n^2 J_n, Eq. 4).
+ * y: lo*n*hi float32.  S_out: n x n float64, full symmetric.  Single-pass
+ * split-K: float32 partial tiles, reduced in float64 in a fixed order
+ * (deterministic). */
+int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precision, double* S_out,
+                 void* stream);
+
+/* Truncating TTM Y' = Y x_n U^T (Eq. 2 with the matrix U^T; Alg. 2, EIG branch).
+ * U: n x R float32 column-major.  out: lo x R x hi float32 column-major. */
+int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* U, int64_t R, int precision,
+                float* out, void* stream);
+
+/* Leading-R eigenpairs of the symmetric n x n float64 matrix S (Alg. 2, EIG
+ * branch) by parallel-order cyclic Jacobi.  Rotations run in float32 or
+ * float64 (atucker_eig_arith).  Matrices with n > 128 use block Jacobi with
+ * 64 x 64 pair sub-problems.
+ *   U_out       n x R float32: the eigenvectors of the R largest eigenvalues,
+ *               descending, sign rule as in atucker_sthosvd, orthonormalised
+ *               in float64 by one Newton-Schulz polar step
+ *   lambda_out  n float64 (nullable): all eigenvalues, descending
+ *   discarded_out 1 float64 (nullable): sum of the eigenvalues beyond R
+ * Returns ATK_ENOCONV if the sweep cap was reached.  Synchronous. */
+int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, float* U_out, double* lambda_out,
+                double* discarded_out, void* stream);
+
+/* ALS solver for one mode (Alg. 2, ALS branch, with Alg. 3).
+ *   L0       n x R float64, the initial guess (nullable: the plan's seeded
+ *            L_0 for mode index `mode` with `seed`, see atucker_plan_create)
+ *   sweeps   ALS iterations (exactly this many; <= 0 selects 5)
+ *   U_out    n x R float32: Q^ of the QR of L_K (diag(R^) > 0)
+ *   core_out lo x R x hi float32: the factor R_{K-1} tensorised, times R^ along mode n
+ * Synchronous.  ATK_ERANK if a Cholesky pivot is not positive. */
+int atucker_als_mode(const float* y, int64_t lo, int64_t n, int64_t hi, int64_t R, const double* L0,
+                     uint64_t seed, int mode, int sweeps, int precision, float* U_out, float* core_out,
+                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ATUCKER_H */

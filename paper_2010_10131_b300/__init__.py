@@ -1,0 +1,271 @@
+"""Python binding of the B300 mode-wise flexible st-HOSVD library (a-Tucker).
+
+Argument marshalling only: every step of the decomposition runs in the CUDA
+library ``_atucker.so`` (built from ``csrc/`` for sm_103a).  The functions
+named ``atucker_*`` mirror the C ABI in ``include/atucker.h`` one to one.  The
+lower-case helpers take torch CUDA tensors.  PyTorch supplies device memory and
+streams only.  If the shared library is missing or cannot be loaded, every call
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+__all__ = [
+    "lib", "abi_symbols", "AtuckerError", "Plan", "sthosvd", "gram", "ttm", "eig", "als_mode",
+    "EIG", "ALS", "FP32", "EIG_ROT_FP32", "EIG_ROT_FP64",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+LIB_PATH = os.path.join(_PKG, "_atucker.so")
+HEADER = os.path.join(_ROOT, "include", "atucker.h")
+
+OK, EINVAL, ERANK, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+EIG, ALS = 0, 1
+FP32 = 0
+EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
+OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING = 1, 2, 3, 4
+PHASES = ("gram", "gram_reduce", "eig", "ttm", "als", "norms", "total", "gram_launches", "launches", "runs")
+_STATUS = {EINVAL: "EINVAL", ERANK: "ERANK", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENOCONV: "ENOCONV",
+           ETIMEOUT: "ETIMEOUT", EUNSUPPORTED: "EUNSUPPORTED"}
+
+
+class AtuckerError(RuntimeError):
+    def __init__(self, status: int, what: str, msg: str):
+        super().__init__(f"{what}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp, _i64, _i32, _u64, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+_SIGS = {
+    "atucker_plan_create": (_i32, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _i32, _i32, _u64, _vp]),
+    "atucker_plan_set_option": (_i32, [_vp, _i32, _i64]),
+    "atucker_sthosvd": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "atucker_sthosvd_host": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "atucker_plan_sync": (_i32, [_vp]),
+    "atucker_plan_timings": (_i32, [_vp, _vp, _i32]),
+    "atucker_plan_destroy": (None, [_vp]),
+    "atucker_sthosvd_oneshot": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "atucker_last_error": (ctypes.c_char_p, []),
+    "atucker_version": (ctypes.c_char_p, []),
+    "atucker_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
+    "atucker_ttm": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _i32, _vp, _vp]),
+    "atucker_eig": (_i32, [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp]),
+    "atucker_als_mode": (_i32, [_vp, _i64, _i64, _i64, _i64, _vp, _u64, _i32, _i32, _i32, _vp, _vp, _vp]),
+}
+
+
+def abi_symbols() -> list[str]:
+    """Every function name declared in include/atucker.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(atucker_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib(build_if_missing: bool = True):
+    """Load the CUDA library (raises if it cannot be built or loaded)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            if not build_if_missing:
+                raise ImportError(f"CUDA library not built: {LIB_PATH}")
+            from . import build as _build
+            _build.build()
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(handle, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        msg = lib().atucker_last_error()
+        raise AtuckerError(status, what, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------ same-name wrappers
+def __getattr__(name):
+    if name.startswith("atucker_") and name in _SIGS:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+# ------------------------------------------------------------- torch helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _i64arr(vals):
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def _i32arr(vals):
+    return (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+
+
+def _dev(t, dtype):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA tensor of dtype {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A reusable st-HOSVD plan (atucker_plan_create) bound to one shape."""
+
+    def __init__(self, dims, ranks, mode_order=None, solver=None, precision: int = FP32, als_sweeps: int = 5,
+                 seed: int = 0, stream=None, eig_arith: int | None = None, sync: bool = False):
+        self.dims = [int(d) for d in dims]
+        self.ranks = [int(r) for r in ranks]
+        self.order = len(self.dims)
+        self._h = ctypes.c_void_p(None)
+        self.stream = stream
+        mo = _i32arr(mode_order) if mode_order is not None else None
+        sv = _i32arr(solver) if solver is not None else None
+        _check(lib().atucker_plan_create(ctypes.byref(self._h), self.order, _i64arr(self.dims), _i64arr(self.ranks),
+                                         mo, sv, int(precision), int(als_sweeps), int(seed) & (2**64 - 1),
+                                         _stream_ptr(stream)), "atucker_plan_create")
+        if eig_arith is not None:
+            _check(lib().atucker_plan_set_option(self._h, OPT_EIG_ARITH, int(eig_arith)), "set_option")
+        if sync:
+            _check(lib().atucker_plan_set_option(self._h, OPT_SYNC, 1), "set_option")
+
+    @property
+    def core_numel(self):
+        n = 1
+        for r in self.ranks:
+            n *= r
+        return n
+
+    @property
+    def factors_numel(self):
+        return sum(d * r for d, r in zip(self.dims, self.ranks))
+
+    def run(self, x, core=None, factors=None, discarded=None):
+        torch = _torch()
+        if core is None:
+            core = torch.empty(self.core_numel, device=x.device, dtype=torch.float32)
+        if factors is None:
+            factors = torch.empty(self.factors_numel, device=x.device, dtype=torch.float32)
+        dptr = _dev(discarded, torch.float64) if discarded is not None else None
+        _check(lib().atucker_sthosvd(self._h, _dev(x, torch.float32), _dev(core, torch.float32),
+                                     _dev(factors, torch.float32), dptr), "atucker_sthosvd")
+        return core, factors
+
+    def run_host(self, x_host, core_host, factors_host, discarded_host=None):
+        """Host-buffer form (atucker_sthosvd_host); tensors must be contiguous CPU tensors."""
+        torch = _torch()
+        for t in (x_host, core_host, factors_host):
+            assert t.device.type == "cpu" and t.is_contiguous() and t.dtype == torch.float32
+        d = ctypes.c_void_p(discarded_host.data_ptr()) if discarded_host is not None else None
+        _check(lib().atucker_sthosvd_host(self._h, ctypes.c_void_p(x_host.data_ptr()),
+                                          ctypes.c_void_p(core_host.data_ptr()),
+                                          ctypes.c_void_p(factors_host.data_ptr()), d), "atucker_sthosvd_host")
+
+    def set_timing(self, on: bool = True):
+        _check(lib().atucker_plan_set_option(self._h, OPT_TIMING, 1 if on else 0), "set_option")
+
+    def timings(self) -> dict:
+        """Per-phase device ms since timing was enabled / last read (atucker_plan_timings)."""
+        buf = (ctypes.c_double * 10)()
+        _check(lib().atucker_plan_timings(self._h, buf, 10), "atucker_plan_timings")
+        return dict(zip(PHASES, list(buf)))
+
+    def sync(self):
+        _check(lib().atucker_plan_sync(self._h), "atucker_plan_sync")
+
+    def split_factors(self, factors):
+        """View the concatenated factor buffer as [U^(n)] (I_n x R_n, column-major -> (I_n, R_n) tensors)."""
+        out, off = [], 0
+        for d, r in zip(self.dims, self.ranks):
+            out.append(factors[off:off + d * r].view(r, d).t())
+            off += d * r
+        return out
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().atucker_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sthosvd(x, dims, ranks, mode_order=None, solver=None, als_sweeps: int = 5, seed: int = 0,
+            eig_arith: int | None = None, with_discarded: bool = False):
+    """Decompose the column-major tensor x (flat CUDA float32).
+
+    Returns (core_flat, [U^(n)], discarded or None)."""
+    torch = _torch()
+    p = Plan(dims, ranks, mode_order, solver, FP32, als_sweeps, seed, eig_arith=eig_arith)
+    disc = torch.zeros(len(dims), device=x.device, dtype=torch.float64) if with_discarded else None
+    core, fac = p.run(x, discarded=disc)
+    p.sync()
+    facs = p.split_factors(fac)
+    p.close()
+    return core, facs, disc
+
+
+def gram(y, lo: int, n: int, hi: int, precision: int = FP32):
+    torch = _torch()
+    S = torch.empty(n * n, device=y.device, dtype=torch.float64)
+    _check(lib().atucker_gram(_dev(y, torch.float32), lo, n, hi, precision, _dev(S, torch.float64), _stream_ptr()),
+           "atucker_gram")
+    return S.view(n, n).t()
+
+
+def ttm(y, lo: int, n: int, hi: int, U, precision: int = FP32):
+    """U: (n, R) tensor (any layout); returns the flat (lo, R, hi) column-major output."""
+    torch = _torch()
+    R = U.shape[1]
+    Ucm = U.t().contiguous().to(torch.float32)
+    out = torch.empty(lo * R * hi, device=y.device, dtype=torch.float32)
+    _check(lib().atucker_ttm(_dev(y, torch.float32), lo, n, hi, _dev(Ucm, torch.float32), R, precision,
+                             _dev(out, torch.float32), _stream_ptr()), "atucker_ttm")
+    return out
+
+
+def eig(S, R: int, eig_arith: int = EIG_ROT_FP32):
+    """S: (n, n) float64 CUDA tensor (symmetric).  Returns (U (n,R) float32, lambda (n,), discarded)."""
+    torch = _torch()
+    n = S.shape[0]
+    Scm = S.t().contiguous().to(torch.float64)
+    U = torch.empty(n * R, device=S.device, dtype=torch.float32)
+    lam = torch.empty(n, device=S.device, dtype=torch.float64)
+    disc = torch.empty(1, device=S.device, dtype=torch.float64)
+    _check(lib().atucker_eig(_dev(Scm, torch.float64), n, R, eig_arith, _dev(U, torch.float32),
+                             _dev(lam, torch.float64), _dev(disc, torch.float64), _stream_ptr()), "atucker_eig")
+    return U.view(R, n).t(), lam, disc
+
+
+def als_mode(y, lo: int, n: int, hi: int, R: int, L0=None, seed: int = 0, mode: int = 0, sweeps: int = 5,
+             precision: int = FP32):
+    """ALS solver for one mode.  Returns (U (n,R) float32, core flat (lo, R, hi))."""
+    torch = _torch()
+    U = torch.empty(n * R, device=y.device, dtype=torch.float32)
+    core = torch.empty(lo * R * hi, device=y.device, dtype=torch.float32)
+    l0 = None
+    if L0 is not None:
+        L0cm = L0.t().contiguous().to(torch.float64)
+        l0 = _dev(L0cm, torch.float64)
+    _check(lib().atucker_als_mode(_dev(y, torch.float32), lo, n, hi, R, l0, int(seed) & (2**64 - 1), mode, sweeps,
+                                  precision, _dev(U, torch.float32), _dev(core, torch.float32), _stream_ptr()),
+           "atucker_als_mode")
+    return U.view(R, n).t(), core

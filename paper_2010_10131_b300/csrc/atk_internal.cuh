@@ -1,0 +1,163 @@
+// Internal definitions shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "atucker.h"
+
+namespace atk {
+
+// ---------------------------------------------------------------- stride view
+// Mode-n view of a column-major tensor (Sec. V): loops outside mode n merge into
+// `hi`, loops inside it into `lo`.  Element (a, i, b) sits at a + lo*(i + n*b).
+// The "other" index c in [0, lo*hi) enumerates (a, b) as c = a + lo*b; it is
+// the column index of the mode-n matricization X_(n) (Sec. II-A), so every
+// contraction over the non-n modes is a sum over c.
+struct View {
+  int64_t lo, n, hi;
+  __host__ __device__ int64_t J() const { return lo * hi; }
+  __host__ __device__ int64_t size() const { return lo * n * hi; }
+  // Offset of (c, i) given the precomputed split of c.
+  __host__ __device__ static int64_t off(int64_t a, int64_t b, int64_t i, int64_t lo, int64_t n) {
+    return a + lo * (i + n * b);
+  }
+};
+
+// View of mode `mode` for the current dims.
+inline View make_view(int order, const int64_t* cur, int mode) {
+  View v{1, cur[mode], 1};
+  for (int k = 0; k < mode; ++k) v.lo *= cur[k];
+  for (int k = mode + 1; k < order; ++k) v.hi *= cur[k];
+  return v;
+}
+
+// ------------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int cuda_status(cudaError_t e, const char* what);
+
+#define ATK_CUDA(call)                                    \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return ::atk::cuda_status(_e, #call); \
+  } while (0)
+// Every kernel launch site ends with ATK_LAUNCHED(): it checks the launch and
+// counts it (the count is reported by atucker_plan_timings).
+void count_launch();
+long long launch_count();
+#define ATK_LAUNCHED()                                                   \
+  do {                                                                   \
+    cudaError_t _e = cudaGetLastError();                                 \
+    if (_e != cudaSuccess) return ::atk::cuda_status(_e, "kernel launch"); \
+    ::atk::count_launch();                                               \
+  } while (0)
+#define ATK_TRY(call)            \
+  do {                           \
+    int _s = (call);             \
+    if (_s != ATK_OK) return _s; \
+  } while (0)
+
+// Device status word bits (written by kernels, read by atucker_plan_sync).
+enum : int { DEV_NOCONV = 1, DEV_TIMEOUT = 2, DEV_CHOL = 4 };
+
+// ------------------------------------------------------------ grid barrier
+// Sense-reversing barrier across the CTAs of a cooperative launch.  Every wait
+// is bounded: after `limit` polls the CTA sets DEV_TIMEOUT in *status and
+// leaves; callers check the return value and exit.  `bar` points at two
+// zero-initialised words: [0] arrival count, [1] generation.
+__device__ inline bool grid_barrier(unsigned* bar, unsigned nblocks, int* status, long long limit = 20000000LL) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    unsigned gen = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    ok = 1;
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*vgen == gen) {
+        if (++polls > limit) {
+          atomicOr(status, DEV_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (ok && (*(volatile int*)status & DEV_TIMEOUT)) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// ------------------------------------------------------------- host helpers
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int num_sms();
+
+// Device scratch carved from one allocation; each take() is 256-byte aligned.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  void* take(size_t bytes) {
+    size_t start = (used + 255) & ~size_t(255);
+    if (start + bytes > cap) return nullptr;
+    used = start + bytes;
+    return base + start;
+  }
+};
+
+// ------------------------------------------------------------ kernel entry points
+// FP32 CUDA-core contractions (fp32_ops.cu).
+size_t gram_scratch_bytes(const View& v);
+// `mid` (nullable) is recorded between the partial-tile kernel and the reduction.
+int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st,
+             cudaEvent_t mid = nullptr);
+int ttm_f32(const float* y, const View& v, const float* U, int64_t R, float* out, cudaStream_t st);
+// C (n x R, float64) = sum_c Y(c, i) P(c, r); P is a (lo, R, hi) tensor.
+size_t cross_scratch_bytes(const View& v, int64_t R);
+int cross_f32(const float* y, const View& v, const float* P, int64_t R, double* C, float* scratch,
+              size_t scratch_bytes, cudaStream_t st);
+
+// Jacobi eigensolver (jacobi.cu).
+size_t eig_scratch_bytes(int64_t n, int arith);
+int eig_top(const double* S, int64_t n, int64_t R, int arith, int max_sweeps, float* U_out, double* U64_out,
+            double* lambda_out, double* discarded_out, int* dev_status, char* scratch, size_t scratch_bytes,
+            cudaStream_t st);
+
+// Float64 small dense linear algebra (smallla.cu).
+size_t smallla_scratch_bytes(int64_t n, int64_t R);
+// G (R x R) = A^T B, A and B n x R float64.
+int gemm_tn_f64(const double* A, const double* B, int64_t n, int64_t R, double* G, double* scratch,
+                cudaStream_t st);
+// In place: X (m x R) <- X G^{-1}, G symmetric positive definite (R x R).
+int solve_spd_right_f64(double* X, int64_t m, int64_t R, const double* G, double* chol_scratch,
+                        int* dev_status, cudaStream_t st);
+// One Newton-Schulz polar step in float64: U <- U (3I - U^T U) / 2.
+int polar_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_t st);
+// CholeskyQR2 in float64: L (n x R) = Q R^, Q overwrites L, R^ (R x R) upper, diag > 0.
+int cholqr2_f64(double* L, int64_t n, int64_t R, double* Rhat, double* scratch, int* dev_status,
+                cudaStream_t st);
+// C (m x p) = A (m x k) B (k x p), column-major float64.
+int gemm_f64(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, cudaStream_t st);
+// Rayleigh quotients lam[r] = u_r^T S u_r of orthonormal U (n x R) and
+// disc = trace(S) - sum_r lam[r]; Z is n x R scratch.  Outputs nullable.
+int rayleigh_f64(const double* S, const double* U, int64_t n, int64_t R, double* Z, double* lam_out,
+                 double* disc_out, cudaStream_t st);
+int f64_to_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
+int f32_to_f64(const float* src, double* dst, int64_t count, cudaStream_t st);
+// Square of the Frobenius norm of a float32 tensor, accumulated in float64.
+// Needs NORM_SCRATCH_BYTES of scratch.
+constexpr size_t NORM_SCRATCH_BYTES = 1184 * 8 + 256;
+int norm2_f32(const float* x, int64_t count, double* out, double* scratch, cudaStream_t st);
+// dst (R x R float32) = transpose of src (R x R float64).
+int transpose_f64_to_f32(const double* src, int64_t R, float* dst, cudaStream_t st);
+
+}  // namespace atk

@@ -1,0 +1,499 @@
+// Matricization-free mode-n contractions on the CUDA cores, float32
+// (Sec. V; Alg. 2 and Alg. 3).
+//
+// Every contraction on the hot path is one of two shapes over the mode-n view
+// (lo, n, hi) of a column-major tensor, with c = a + lo*b the "other" index:
+//   CI  C[i][j] = sum_c A(c, i) B(c, j)  -- contraction over c (TTT, Eq. 3):
+//       the Gram S = Y_(n) Y_(n)^T, and the ALS products Y P and P^T P.
+//   CO  O(c, r) = sum_i A(c, i) M[i][r]  -- contraction over i (TTM, Eq. 2):
+//       the truncating TTM Y x_n U^T, the ALS product Y^T L~, and the ALS
+//       core update.
+// Both are one register-tiled kernel: 256 threads, a BM x BN output tile,
+// 16-deep k tiles staged through double-buffered shared memory.  Each thread
+// holds a TM x TN register block.  The loaders read the tensor in place through
+// the stride view.  Lanes run along whichever index is contiguous in memory:
+// i when lo == 1, c otherwise.  So no unfolding is ever materialised.
+// CI outputs are split over c (split-K) into float32 partial tiles.  A second
+// kernel sums them in float64 in a fixed order, so results are deterministic
+// and no float32 sum runs longer than one split (<= 8192 terms).
+#include <algorithm>
+
+#include "atk_internal.cuh"
+
+namespace atk {
+
+constexpr int NT = 256;   // threads per CTA
+constexpr int TK = 16;    // k-tile depth
+constexpr int PAD = 4;    // smem row padding (floats); keeps 16-byte row alignment
+constexpr int SPLIT_MAX_K = 8192;
+
+// ------------------------------------------------------------------ loaders
+// Each loader fetches a TK x W tile (k rows, W contiguous m columns in smem)
+// into registers, then stores it to shared memory as s[k * (W + PAD) + m].
+
+// A view operand with k = c (the other index) and m = i (mode index): CI role.
+template <int W>
+struct ViewLoaderKC {
+  static constexpr int PER = TK * W / NT;
+  const float* y;
+  int64_t lo, n, c_end, i0;
+  bool lanes_on_m;  // lo == 1: m (= i) is contiguous
+  int km, mm, step;
+  float r[PER];
+  __device__ void init(const float* y_, int64_t lo_, int64_t n_, int64_t c_end_, int64_t i0_) {
+    y = y_; lo = lo_; n = n_; c_end = c_end_; i0 = i0_;
+    lanes_on_m = (lo == 1);
+    int t = threadIdx.x;
+    if (lanes_on_m) { mm = t % W; km = t / W; step = NT / W; }
+    else { km = t % TK; mm = t / TK; step = NT / TK; }
+  }
+  __device__ void fetch(int64_t c0) {
+    if (lanes_on_m) {
+      const int64_t i = i0 + mm;
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        int64_t c = c0 + km + e * step;
+        r[e] = (c < c_end && i < n) ? __ldg(y + i + n * c) : 0.f;
+      }
+    } else {
+      int64_t c = c0 + km;
+      bool cv = c < c_end;
+      int64_t a = cv ? c % lo : 0, b = cv ? c / lo : 0;
+      const float* base = y + a + lo * n * b;
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        int64_t i = i0 + mm + e * step;
+        r[e] = (cv && i < n) ? __ldg(base + lo * i) : 0.f;
+      }
+    }
+  }
+  __device__ void store(float* s) const {
+    if (lanes_on_m) {
+#pragma unroll
+      for (int e = 0; e < PER; ++e) s[(km + e * step) * (W + PAD) + mm] = r[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < PER; ++e) s[km * (W + PAD) + mm + e * step] = r[e];
+    }
+  }
+};
+
+// A view operand with k = i (mode index) and m = c (other index): CO role.
+template <int W>
+struct ViewLoaderKI {
+  static constexpr int PER = TK * W / NT;
+  const float* y;
+  int64_t lo, n, J, c0, cbase_off;
+  bool lanes_on_k;  // lo == 1: k (= i) is contiguous
+  bool cvalid;
+  int km, mm, step;
+  float r[PER];
+  __device__ void init(const float* y_, int64_t lo_, int64_t n_, int64_t J_, int64_t c0_) {
+    y = y_; lo = lo_; n = n_; J = J_; c0 = c0_;
+    lanes_on_k = (lo == 1);
+    int t = threadIdx.x;
+    if (lanes_on_k) { km = t % TK; mm = t / TK; step = NT / TK; }
+    else {
+      mm = t % W; km = t / W; step = NT / W;
+      int64_t c = c0 + mm;
+      cvalid = c < J;
+      cbase_off = cvalid ? (c % lo) + lo * n * (c / lo) : 0;
+    }
+  }
+  __device__ void fetch(int64_t i0) {
+    if (lanes_on_k) {
+      int64_t i = i0 + km;
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        int64_t c = c0 + mm + e * step;
+        r[e] = (i < n && c < J) ? __ldg(y + i + n * c) : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        int64_t i = i0 + km + e * step;
+        r[e] = (cvalid && i < n) ? __ldg(y + cbase_off + lo * i) : 0.f;
+      }
+    }
+  }
+  __device__ void store(float* s) const {
+    if (lanes_on_k) {
+#pragma unroll
+      for (int e = 0; e < PER; ++e) s[km * (W + PAD) + mm + e * step] = r[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < PER; ++e) s[(km + e * step) * (W + PAD) + mm] = r[e];
+    }
+  }
+};
+
+// Dense column-major n x R matrix M, k = row i, m = column r (CO B operand).
+template <int W>
+struct MatLoader {
+  static constexpr int PER = (TK * W + NT - 1) / NT;
+  const float* M;
+  int64_t n, R, r0;
+  int km, mm;
+  float r[PER];
+  __device__ void init(const float* M_, int64_t n_, int64_t R_, int64_t r0_) {
+    M = M_; n = n_; R = R_; r0 = r0_;
+    km = threadIdx.x % TK; mm = threadIdx.x / TK;
+  }
+  __device__ void fetch(int64_t i0) {
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      int m = mm + e * (NT / TK);
+      int64_t i = i0 + km, rr = r0 + m;
+      r[e] = (m < W && i < n && rr < R) ? __ldg(M + i + n * rr) : 0.f;
+    }
+  }
+  __device__ void store(float* s) const {
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      int m = mm + e * (NT / TK);
+      if (m < W) s[km * (W + PAD) + m] = r[e];
+    }
+  }
+};
+
+// ----------------------------------------------------------- register block
+template <int BM, int BN, int TM, int TN>
+struct Block {
+  static constexpr int TX = BN / TN, TY = BM / TM;
+  static_assert(TX * TY == NT, "thread grid must cover 256 threads");
+  float acc[TM][TN];
+  int tx, ty;
+  __device__ void init() {
+    tx = threadIdx.x % TX; ty = threadIdx.x / TX;
+#pragma unroll
+    for (int u = 0; u < TM; ++u)
+#pragma unroll
+      for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
+  }
+  __device__ static int row_of(int ty, int u) {
+    return (u < TM / 2) ? ty * (TM / 2) + u : BM / 2 + ty * (TM / 2) + (u - TM / 2);
+  }
+  __device__ static int col_of(int tx, int v) {
+    if (TN == 1) return tx;
+    return (v < TN / 2) ? tx * (TN / 2) + v : BN / 2 + tx * (TN / 2) + (v - TN / 2);
+  }
+  // Load H = TM/2 (or TN/2) consecutive floats starting at a 4*H-byte aligned address.
+  template <int H>
+  __device__ static void ld(float* dst, const float* src) {
+    if (H == 4) {
+      float4 t = *reinterpret_cast<const float4*>(src);
+      dst[0] = t.x; dst[1] = t.y; dst[2] = t.z; dst[3] = t.w;
+    } else if (H == 2) {
+      float2 t = *reinterpret_cast<const float2*>(src);
+      dst[0] = t.x; dst[1] = t.y;
+    } else {
+#pragma unroll
+      for (int h = 0; h < H; ++h) dst[h] = src[h];
+    }
+  }
+  __device__ void mma(const float* sa, const float* sb) {
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      float a[TM], b[TN];
+      ld<TM / 2>(a, sa + k * (BM + PAD) + ty * (TM / 2));
+      ld<TM / 2>(a + TM / 2, sa + k * (BM + PAD) + BM / 2 + ty * (TM / 2));
+      if (TN == 1) {
+        b[0] = sb[k * (BN + PAD) + tx];
+      } else {
+        ld<TN / 2>(b, sb + k * (BN + PAD) + tx * (TN / 2));
+        ld<TN / 2>(b + TN / 2, sb + k * (BN + PAD) + BN / 2 + tx * (TN / 2));
+      }
+#pragma unroll
+      for (int u = 0; u < TM; ++u)
+#pragma unroll
+        for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+  }
+};
+
+// Upper-triangle tile enumeration of a T x T tile grid (row-major).
+__host__ __device__ inline void tri_tile(int id, int T, int& ti, int& tj) {
+  ti = 0;
+  while (id >= T - ti) { id -= T - ti; ++ti; }
+  tj = ti + id;
+}
+
+// ------------------------------------------------------------- CI kernels
+// Gram: C = sum_c Y(c, :)^T Y(c, :), upper-triangle tiles only; partial tile
+// (row-major BM x BN, float32) per (tile, split).
+template <int BM, int TM>
+__global__ void __launch_bounds__(NT, 2)
+gram_ci_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, int T, int64_t kc,
+               float* __restrict__ part) {
+  __shared__ __align__(16) float sA[2][TK * (BM + PAD)];
+  __shared__ __align__(16) float sB[2][TK * (BM + PAD)];
+  int tile = blockIdx.x, split = blockIdx.y;
+  int ti, tj;
+  tri_tile(tile, T, ti, tj);
+  const bool diag = ti == tj;
+  const int64_t J = lo * hi;
+  const int64_t cb = (int64_t)split * kc, ce = min(J, cb + kc);
+  ViewLoaderKC<BM> la, lb;
+  la.init(y, lo, n, ce, (int64_t)ti * BM);
+  lb.init(y, lo, n, ce, (int64_t)tj * BM);
+  Block<BM, BM, TM, TM> blk;
+  blk.init();
+  const int64_t ntile = cb < ce ? (ce - cb + TK - 1) / TK : 0;
+  if (ntile > 0) {
+    la.fetch(cb);
+    if (!diag) lb.fetch(cb);
+    la.store(sA[0]);
+    if (!diag) lb.store(sB[0]);
+    __syncthreads();
+    for (int64_t t = 0; t < ntile; ++t) {
+      const int buf = t & 1;
+      if (t + 1 < ntile) {
+        la.fetch(cb + (t + 1) * TK);
+        if (!diag) lb.fetch(cb + (t + 1) * TK);
+      }
+      blk.mma(sA[buf], diag ? sA[buf] : sB[buf]);
+      if (t + 1 < ntile) {
+        la.store(sA[buf ^ 1]);
+        if (!diag) lb.store(sB[buf ^ 1]);
+      }
+      __syncthreads();
+    }
+  }
+  float* out = part + ((int64_t)split * gridDim.x + tile) * (BM * BM);
+#pragma unroll
+  for (int u = 0; u < TM; ++u)
+#pragma unroll
+    for (int v = 0; v < TM; ++v)
+      out[Block<BM, BM, TM, TM>::row_of(blk.ty, u) * BM + Block<BM, BM, TM, TM>::col_of(blk.tx, v)] = blk.acc[u][v];
+}
+
+// Cross product C (n x R) = sum_c Y(c, i) P(c, r), P a (lo, R, hi) tensor.
+template <int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(NT, 2)
+cross_ci_kernel(const float* __restrict__ y, const float* __restrict__ p, int64_t lo, int64_t n, int64_t hi,
+                int64_t R, int TR, int64_t kc, float* __restrict__ part) {
+  __shared__ __align__(16) float sA[2][TK * (BM + PAD)];
+  __shared__ __align__(16) float sB[2][TK * (BN + PAD)];
+  int tile = blockIdx.x, split = blockIdx.y;
+  int ti = tile / TR, tr = tile % TR;
+  const int64_t J = lo * hi;
+  const int64_t cb = (int64_t)split * kc, ce = min(J, cb + kc);
+  ViewLoaderKC<BM> la;
+  ViewLoaderKC<BN> lb;
+  la.init(y, lo, n, ce, (int64_t)ti * BM);
+  lb.init(p, lo, R, ce, (int64_t)tr * BN);
+  Block<BM, BN, TM, TN> blk;
+  blk.init();
+  const int64_t ntile = cb < ce ? (ce - cb + TK - 1) / TK : 0;
+  if (ntile > 0) {
+    la.fetch(cb);
+    lb.fetch(cb);
+    la.store(sA[0]);
+    lb.store(sB[0]);
+    __syncthreads();
+    for (int64_t t = 0; t < ntile; ++t) {
+      const int buf = t & 1;
+      if (t + 1 < ntile) {
+        la.fetch(cb + (t + 1) * TK);
+        lb.fetch(cb + (t + 1) * TK);
+      }
+      blk.mma(sA[buf], sB[buf]);
+      if (t + 1 < ntile) {
+        la.store(sA[buf ^ 1]);
+        lb.store(sB[buf ^ 1]);
+      }
+      __syncthreads();
+    }
+  }
+  float* out = part + ((int64_t)split * gridDim.x + tile) * (BM * BN);
+#pragma unroll
+  for (int u = 0; u < TM; ++u)
+#pragma unroll
+    for (int v = 0; v < TN; ++v)
+      out[Block<BM, BN, TM, TN>::row_of(blk.ty, u) * BN + Block<BM, BN, TM, TN>::col_of(blk.tx, v)] =
+          blk.acc[u][v];
+}
+
+// Sum the split-K partial tiles in float64, in split order (deterministic).
+// sym: C is n x n from upper-triangle tiles (T x T grid of BM tiles).
+__global__ void reduce_sym_kernel(const float* __restrict__ part, int nsplit, int ntiles, int T, int BM, int64_t n,
+                                  double* __restrict__ C) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  int64_t i = idx / n, j = idx % n;  // lanes along j: contiguous within a tile row
+  if (i > j) return;  // written together with (j, i)
+  int ti = (int)(i / BM), tj = (int)(j / BM);
+  int id = ti * T - ti * (ti - 1) / 2 + (tj - ti);
+  int64_t o = (i - (int64_t)ti * BM) * BM + (j - (int64_t)tj * BM);
+  double s = 0.0;
+  for (int sp = 0; sp < nsplit; ++sp) s += (double)part[((int64_t)sp * ntiles + id) * BM * BM + o];
+  C[i + n * j] = s;
+  C[j + n * i] = s;
+}
+
+__global__ void reduce_cross_kernel(const float* __restrict__ part, int nsplit, int ntiles, int TR, int BM, int BN,
+                                    int64_t n, int64_t R, double* __restrict__ C) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * R) return;
+  int64_t i = idx / R, r = idx % R;  // lanes along r: contiguous within a tile row
+  int ti = (int)(i / BM), tr = (int)(r / BN);
+  int id = ti * TR + tr;
+  int64_t o = (i - (int64_t)ti * BM) * BN + (r - (int64_t)tr * BN);
+  double s = 0.0;
+  for (int sp = 0; sp < nsplit; ++sp) s += (double)part[((int64_t)sp * ntiles + id) * BM * BN + o];
+  C[i + n * r] = s;
+}
+
+// ------------------------------------------------------------- CO kernel
+// O(c, r) = sum_i Y(c, i) M[i][r]; O is a (lo, R, hi) tensor.
+template <int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(NT, 2)
+ttm_co_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, const float* __restrict__ M,
+              int64_t R, float* __restrict__ out) {
+  __shared__ __align__(16) float sA[2][TK * (BM + PAD)];
+  __shared__ __align__(16) float sB[2][TK * (BN + PAD)];
+  const int64_t J = lo * hi;
+  const int64_t c0 = (int64_t)blockIdx.x * BM;
+  const int64_t r0 = (int64_t)blockIdx.y * BN;
+  ViewLoaderKI<BM> la;
+  MatLoader<BN> lb;
+  la.init(y, lo, n, J, c0);
+  lb.init(M, n, R, r0);
+  Block<BM, BN, TM, TN> blk;
+  blk.init();
+  const int64_t ntile = (n + TK - 1) / TK;
+  la.fetch(0);
+  lb.fetch(0);
+  la.store(sA[0]);
+  lb.store(sB[0]);
+  __syncthreads();
+  for (int64_t t = 0; t < ntile; ++t) {
+    const int buf = t & 1;
+    if (t + 1 < ntile) {
+      la.fetch((t + 1) * TK);
+      lb.fetch((t + 1) * TK);
+    }
+    blk.mma(sA[buf], sB[buf]);
+    if (t + 1 < ntile) {
+      la.store(sA[buf ^ 1]);
+      lb.store(sB[buf ^ 1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < TM; ++u) {
+    int64_t c = c0 + Block<BM, BN, TM, TN>::row_of(blk.ty, u);
+    if (c >= J) continue;
+    int64_t base = (c % lo) + lo * R * (c / lo);
+#pragma unroll
+    for (int v = 0; v < TN; ++v) {
+      int64_t r = r0 + Block<BM, BN, TM, TN>::col_of(blk.tx, v);
+      if (r < R) out[base + lo * r] = blk.acc[u][v];
+    }
+  }
+}
+
+// ------------------------------------------------------------ host side
+namespace {
+struct SplitPlan {
+  int nsplit;
+  int64_t kc;
+};
+SplitPlan choose_split(int64_t J, int ntiles) {
+  const int slots = 2 * num_sms();
+  int64_t need = ceil_div(J, SPLIT_MAX_K) * ntiles;  // splits required for accuracy
+  int64_t waves = std::max<int64_t>(1, ceil_div(need, slots));
+  int64_t nsplit = std::max<int64_t>(1, ceil_div(waves * slots, ntiles));
+  nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, ceil_div(J, TK)));
+  int64_t kc = ceil_div(ceil_div(J, nsplit), TK) * TK;
+  nsplit = ceil_div(J, kc);
+  return {(int)std::max<int64_t>(1, nsplit), kc};
+}
+int gram_bm(int64_t n) { return n > 64 ? 128 : (n > 32 ? 64 : 32); }
+int cross_bn(int64_t R) { return R > 64 ? 128 : (R > 32 ? 64 : (R > 16 ? 32 : 16)); }
+}  // namespace
+
+size_t gram_scratch_bytes(const View& v) {
+  int bm = gram_bm(v.n);
+  int T = (int)ceil_div(v.n, bm);
+  int nt = T * (T + 1) / 2;
+  SplitPlan sp = choose_split(v.J(), nt);
+  return (size_t)sp.nsplit * nt * bm * bm * sizeof(float);
+}
+
+int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st,
+             cudaEvent_t mid) {
+  if (v.n <= 0) return ATK_OK;
+  if (v.J() == 0) {
+    ATK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * v.n * v.n, st));
+    return ATK_OK;
+  }
+  int bm = gram_bm(v.n);
+  int T = (int)ceil_div(v.n, bm);
+  int nt = T * (T + 1) / 2;
+  SplitPlan sp = choose_split(v.J(), nt);
+  if ((size_t)sp.nsplit * nt * bm * bm * sizeof(float) > scratch_bytes) {
+    set_error("gram_f32: scratch too small");
+    return ATK_EINVAL;
+  }
+  dim3 grid(nt, sp.nsplit);
+  if (bm == 128) gram_ci_kernel<128, 8><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
+  else if (bm == 64) gram_ci_kernel<64, 4><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
+  else gram_ci_kernel<32, 2><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
+  ATK_LAUNCHED();
+  if (mid) ATK_CUDA(cudaEventRecord(mid, st));
+  int64_t total = v.n * v.n;
+  reduce_sym_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(scratch, sp.nsplit, nt, T, bm, v.n, S);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+
+size_t cross_scratch_bytes(const View& v, int64_t R) {
+  int bn = cross_bn(R);
+  int TI = (int)ceil_div(v.n, 128), TR = (int)ceil_div(R, bn);
+  int nt = TI * TR;
+  SplitPlan sp = choose_split(v.J(), nt);
+  return (size_t)sp.nsplit * nt * 128 * bn * sizeof(float);
+}
+
+int cross_f32(const float* y, const View& v, const float* P, int64_t R, double* C, float* scratch,
+              size_t scratch_bytes, cudaStream_t st) {
+  if (v.n <= 0 || R <= 0) return ATK_OK;
+  if (v.J() == 0) {
+    ATK_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * v.n * R, st));
+    return ATK_OK;
+  }
+  int bn = cross_bn(R);
+  int TI = (int)ceil_div(v.n, 128), TR = (int)ceil_div(R, bn);
+  int nt = TI * TR;
+  SplitPlan sp = choose_split(v.J(), nt);
+  if ((size_t)sp.nsplit * nt * 128 * bn * sizeof(float) > scratch_bytes) {
+    set_error("cross_f32: scratch too small");
+    return ATK_EINVAL;
+  }
+  dim3 grid(nt, sp.nsplit);
+  if (bn == 128) cross_ci_kernel<128, 128, 8, 8><<<grid, NT, 0, st>>>(y, P, v.lo, v.n, v.hi, R, TR, sp.kc, scratch);
+  else if (bn == 64) cross_ci_kernel<128, 64, 8, 4><<<grid, NT, 0, st>>>(y, P, v.lo, v.n, v.hi, R, TR, sp.kc, scratch);
+  else if (bn == 32) cross_ci_kernel<128, 32, 8, 2><<<grid, NT, 0, st>>>(y, P, v.lo, v.n, v.hi, R, TR, sp.kc, scratch);
+  else cross_ci_kernel<128, 16, 8, 1><<<grid, NT, 0, st>>>(y, P, v.lo, v.n, v.hi, R, TR, sp.kc, scratch);
+  ATK_LAUNCHED();
+  int64_t total = v.n * R;
+  reduce_cross_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(scratch, sp.nsplit, nt, TR, 128, bn, v.n, R, C);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+
+int ttm_f32(const float* y, const View& v, const float* U, int64_t R, float* out, cudaStream_t st) {
+  const int64_t J = v.J();
+  if (J == 0 || R <= 0) return ATK_OK;
+  int bn = cross_bn(R);
+  dim3 grid((unsigned)ceil_div(J, 128), (unsigned)ceil_div(R, bn));
+  if (bn == 128) ttm_co_kernel<128, 128, 8, 8><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
+  else if (bn == 64) ttm_co_kernel<128, 64, 8, 4><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
+  else if (bn == 32) ttm_co_kernel<128, 32, 8, 2><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
+  else ttm_co_kernel<128, 16, 8, 1><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+
+}  // namespace atk

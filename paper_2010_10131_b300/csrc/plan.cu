@@ -1,0 +1,587 @@
+// Plan, mode loop (Alg. 2) and the C ABI of the library.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "atk_internal.cuh"
+
+namespace atk {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+int cuda_status(cudaError_t e, const char* what) {
+  g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return ATK_ENOMEM;
+  return ATK_ECUDA;
+}
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// ALS initial guess L_0 (Alg. 3 input; the paper leaves it open).  N(0,1)
+// entries: Box-Muller on a counter-based splitmix64 stream (Steele, Lea and
+// Flood, OOPSLA 2014).  The c-th output of the stream with state s is
+// mix(s + c * 0x9E3779B97F4A7C15).
+static uint64_t splitmix_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+static void als_initial_guess(uint64_t seed, int mode, int64_t I, int64_t R, double* out) {
+  const uint64_t gamma = 0x9E3779B97F4A7C15ULL;
+  const uint64_t state = seed ^ (gamma * (uint64_t)(mode + 1));
+  const double inv53 = 1.0 / 9007199254740992.0;
+  for (int64_t e = 0; e < I * R; ++e) {
+    uint64_t w1 = splitmix_mix(state + (2 * (uint64_t)e + 1) * gamma) >> 11;
+    uint64_t w2 = splitmix_mix(state + (2 * (uint64_t)e + 2) * gamma) >> 11;
+    double u1 = ((double)w1 + 1.0) * inv53, u2 = (double)w2 * inv53;
+    out[e] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  }
+}
+
+__global__ void sub_kernel(const double* a, const double* b, double* out) { *out = *a - *b; }
+
+// Phase slots of atucker_plan_timings.
+enum { PH_GRAM = 0, PH_GRAM_REDUCE, PH_EIG, PH_TTM, PH_ALS, PH_OTHER, PH_TOTAL, PH_SLOTS = PH_TOTAL + 4 };
+
+// ------------------------------------------------------------ ALS mode update
+struct AlsBufs {
+  double *L, *Lt, *G, *A, *B, *Rhat;
+  float *Lt32, *M32, *P;
+  char* scratch;
+  size_t scratch_bytes;
+  int* dev_status;
+};
+
+static size_t als_scratch_need(const View& v, int64_t R) {
+  View vp{v.lo, R, v.hi};
+  size_t s = std::max(cross_scratch_bytes(v, R), cross_scratch_bytes(vp, R));
+  s = std::max(s, smallla_scratch_bytes(std::max(v.n, R), R));
+  return s;
+}
+
+// One ALS solve (Alg. 3 with `sweeps` iterations), QR of L (CholeskyQR2 in
+// float64, the unique QR with diag(R^) > 0), and the core update
+// Y' = R_{K-1} x_n R^ written to `out` (a (lo, R, hi) tensor).
+static int als_mode_run(const float* y, const View& v, int64_t R, const double* L0, int sweeps, float* U_out,
+                        float* out, AlsBufs& b, cudaStream_t st) {
+  const int64_t n = v.n;
+  View vp{v.lo, R, v.hi};
+  double* ss = (double*)b.scratch;
+  ATK_CUDA(cudaMemcpyAsync(b.L, L0, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
+  for (int k = 0; k < sweeps; ++k) {
+    // R_k = (Y^T L_k)(L_k^T L_k)^{-1} = Y^T L~ with L~ = L_k (L_k^T L_k)^{-1}.
+    ATK_TRY(gemm_tn_f64(b.L, b.L, n, R, b.G, ss, st));
+    ATK_CUDA(cudaMemcpyAsync(b.Lt, b.L, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
+    ATK_TRY(solve_spd_right_f64(b.Lt, n, R, b.G, ss, b.dev_status, st));
+    ATK_TRY(f64_to_f32(b.Lt, b.Lt32, n * R, st));
+    ATK_TRY(ttm_f32(y, v, b.Lt32, R, b.P, st));  // P = R_k as a (lo, R, hi) tensor
+    // L_{k+1} = (Y R_k)(R_k^T R_k)^{-1}.
+    ATK_TRY(cross_f32(y, v, b.P, R, b.A, (float*)b.scratch, b.scratch_bytes, st));
+    ATK_TRY(cross_f32(b.P, vp, b.P, R, b.B, (float*)b.scratch, b.scratch_bytes, st));
+    ATK_TRY(solve_spd_right_f64(b.A, n, R, b.B, ss, b.dev_status, st));
+    ATK_CUDA(cudaMemcpyAsync(b.L, b.A, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
+  }
+  // L_K = Q^ R^; U = Q^; Y' = TTM(R_{K-1}, R^).
+  ATK_TRY(cholqr2_f64(b.L, n, R, b.Rhat, ss, b.dev_status, st));
+  ATK_TRY(f64_to_f32(b.L, U_out, n * R, st));
+  ATK_TRY(transpose_f64_to_f32(b.Rhat, R, b.M32, st));
+  ATK_TRY(ttm_f32(b.P, vp, b.M32, R, out, st));
+  return ATK_OK;
+}
+
+}  // namespace atk
+
+using namespace atk;
+
+// ====================================================================== plan
+struct atucker_plan_s {
+  int order = 0;
+  int64_t dims[8], ranks[8], foff[8];
+  int mode_order[8], solver[8];
+  int precision = ATK_FP32, als_sweeps = 5;
+  uint64_t seed = 0;
+  cudaStream_t st = nullptr;
+  int eig_arith = ATK_EIG_ROT_FP32, sync = 0, max_sweeps = 40;
+  // device workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  float* buf[2] = {nullptr, nullptr};
+  float* bufP = nullptr;
+  double *S = nullptr, *U64 = nullptr, *norms = nullptr, *L0 = nullptr;
+  int64_t l0off[8];
+  AlsBufs als{};
+  char* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int* dev_status = nullptr;
+  // phase timing (ATK_OPT_TIMING): events recorded on the plan's stream
+  int timing = 0;
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  struct Rec { int phase; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  long long gram_launches = 0, runs = 0, launches_mark = 0;
+  cudaEvent_t ev() {
+    if (evnext == evpool.size()) {
+      cudaEvent_t e = nullptr;
+      cudaEventCreate(&e);
+      evpool.push_back(e);
+    }
+    return evpool[evnext++];
+  }
+  // host-buffer entry point
+  float *x_dev = nullptr, *core_dev = nullptr, *fac_dev = nullptr;
+  double* disc_dev = nullptr;
+  int64_t total = 0, core_total = 0, fac_total = 0;
+};
+
+static int validate(int order, const int64_t* dims, const int64_t* ranks, const int* mode_order,
+                    const int* solver) {
+  if (order < 1 || order > 8 || !dims || !ranks) { set_error("order must be in [1, 8]; dims/ranks non-null"); return ATK_EINVAL; }
+  double total = 1.0;
+  for (int k = 0; k < order; ++k) {
+    if (dims[k] < 1) { set_error("dims must be >= 1"); return ATK_EINVAL; }
+    total *= (double)dims[k];
+  }
+  if (total >= 2147483648.0) { set_error("tensor must have fewer than 2^31 elements"); return ATK_EUNSUPPORTED; }
+  for (int k = 0; k < order; ++k) {
+    if (ranks[k] < 1 || ranks[k] > dims[k]) { set_error("need 1 <= R_n <= I_n"); return ATK_ERANK; }
+    double others = 1.0;
+    for (int j = 0; j < order; ++j)
+      if (j != k) others *= (double)ranks[j];
+    if (order > 1 && (double)ranks[k] > others) { set_error("need R_n <= prod_{k!=n} R_k"); return ATK_ERANK; }
+    if (ranks[k] > 128) { set_error("R_n > 128 is not supported"); return ATK_EUNSUPPORTED; }
+  }
+  if (mode_order) {
+    int seen[8] = {0};
+    for (int k = 0; k < order; ++k) {
+      if (mode_order[k] < 0 || mode_order[k] >= order || seen[mode_order[k]]) { set_error("mode_order must be a permutation"); return ATK_EINVAL; }
+      seen[mode_order[k]] = 1;
+    }
+  }
+  for (int k = 0; k < order; ++k) {
+    int s = solver ? solver[k] : ATK_EIG;
+    if (s != ATK_EIG && s != ATK_ALS) { set_error("solver_per_mode entries must be 0 (EIG) or 1 (ALS)"); return ATK_EINVAL; }
+    if (s == ATK_EIG && dims[k] > 1024) { set_error("EIG modes need I_n <= 1024"); return ATK_EUNSUPPORTED; }
+  }
+  return ATK_OK;
+}
+
+static int plan_alloc(atucker_plan_s* p) {
+  int64_t cur[8];
+  for (int k = 0; k < p->order; ++k) cur[k] = p->dims[k];
+  size_t bufsz[2] = {0, 0}, pbuf = 0, scratch = 4096, s_elems = 1, u_elems = 1, l0_elems = 0;
+  int64_t maxn = 1, maxr = 1;
+  bool any_als = false;
+  for (int step = 0; step < p->order; ++step) {
+    int n = p->mode_order[step];
+    View v = make_view(p->order, cur, n);
+    int64_t R = p->ranks[n];
+    size_t out_elems = (size_t)(v.J() * R);
+    if (step < p->order - 1) bufsz[step & 1] = std::max(bufsz[step & 1], out_elems);
+    u_elems = std::max(u_elems, (size_t)(v.n * R));
+    maxn = std::max(maxn, v.n);
+    maxr = std::max(maxr, R);
+    if (p->solver[n] == ATK_EIG) {
+      s_elems = std::max(s_elems, (size_t)(v.n * v.n));
+      scratch = std::max(scratch, gram_scratch_bytes(v));
+      scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP64));
+      scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP32));
+      scratch = std::max(scratch, smallla_scratch_bytes(v.n, R));
+    } else {
+      any_als = true;
+      pbuf = std::max(pbuf, out_elems);
+      scratch = std::max(scratch, als_scratch_need(v, R));
+      p->l0off[n] = (int64_t)l0_elems;
+      l0_elems += (size_t)(v.n * R);
+    }
+    cur[n] = R;
+  }
+  scratch = std::max(scratch, (size_t)NORM_SCRATCH_BYTES);
+  size_t need = 0;
+  auto add = [&](size_t b) { need += (b + 255) & ~size_t(255); };
+  add(bufsz[0] * 4); add(bufsz[1] * 4); add(pbuf * 4);
+  add(s_elems * 8); add(u_elems * 8); add(64 * 8); add(l0_elems * 8);
+  if (any_als) {
+    size_t nr = (size_t)(maxn * maxr), rr = (size_t)(maxr * maxr);
+    add(nr * 8); add(nr * 8); add(rr * 8); add(nr * 8); add(rr * 8); add(rr * 8);
+    add(nr * 4); add(rr * 4);
+  }
+  add(scratch); add(256);
+  cudaError_t e = cudaMalloc(&p->ws, need);
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc(plan workspace)");
+  p->ws_bytes = need;
+  Arena ar{p->ws, need, 0};
+  p->buf[0] = (float*)ar.take(bufsz[0] * 4);
+  p->buf[1] = (float*)ar.take(bufsz[1] * 4);
+  p->bufP = (float*)ar.take(pbuf * 4);
+  p->S = (double*)ar.take(s_elems * 8);
+  p->U64 = (double*)ar.take(u_elems * 8);
+  p->norms = (double*)ar.take(64 * 8);
+  p->L0 = (double*)ar.take(l0_elems * 8);
+  if (any_als) {
+    size_t nr = (size_t)(maxn * maxr), rr = (size_t)(maxr * maxr);
+    p->als.L = (double*)ar.take(nr * 8);
+    p->als.Lt = (double*)ar.take(nr * 8);
+    p->als.G = (double*)ar.take(rr * 8);
+    p->als.A = (double*)ar.take(nr * 8);
+    p->als.B = (double*)ar.take(rr * 8);
+    p->als.Rhat = (double*)ar.take(rr * 8);
+    p->als.Lt32 = (float*)ar.take(nr * 4);
+    p->als.M32 = (float*)ar.take(rr * 4);
+  }
+  p->scratch = (char*)ar.take(scratch);
+  p->scratch_bytes = scratch;
+  p->dev_status = (int*)ar.take(256);
+  p->als.P = p->bufP;
+  p->als.scratch = p->scratch;
+  p->als.scratch_bytes = scratch;
+  p->als.dev_status = p->dev_status;
+  ATK_CUDA(cudaMemsetAsync(p->dev_status, 0, sizeof(int), p->st));
+  if (l0_elems) {
+    std::vector<double> h(l0_elems);
+    for (int n = 0; n < p->order; ++n)
+      if (p->solver[n] == ATK_ALS) als_initial_guess(p->seed, n, p->dims[n], p->ranks[n], h.data() + p->l0off[n]);
+    ATK_CUDA(cudaMemcpyAsync(p->L0, h.data(), l0_elems * 8, cudaMemcpyHostToDevice, p->st));
+    ATK_CUDA(cudaStreamSynchronize(p->st));
+  }
+  return ATK_OK;
+}
+
+extern "C" {
+
+int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
+                        const int* mode_order, const int* solver_per_mode, int precision, int als_sweeps,
+                        uint64_t seed, void* stream) {
+  if (!plan) { set_error("plan is null"); return ATK_EINVAL; }
+  *plan = nullptr;
+  ATK_TRY(validate(order, dims, ranks, mode_order, solver_per_mode));
+  if (precision != ATK_FP32) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  atucker_plan_s* p = new atucker_plan_s();
+  p->order = order;
+  int64_t off = 0;
+  for (int k = 0; k < order; ++k) {
+    p->dims[k] = dims[k];
+    p->ranks[k] = ranks[k];
+    p->mode_order[k] = mode_order ? mode_order[k] : k;
+    p->solver[k] = solver_per_mode ? solver_per_mode[k] : ATK_EIG;
+    p->foff[k] = off;
+    off += dims[k] * ranks[k];
+  }
+  p->fac_total = off;
+  p->total = 1;
+  p->core_total = 1;
+  for (int k = 0; k < order; ++k) { p->total *= dims[k]; p->core_total *= ranks[k]; }
+  p->precision = precision;
+  p->als_sweeps = als_sweeps > 0 ? als_sweeps : 5;
+  p->seed = seed;
+  p->st = (cudaStream_t)stream;
+  int s = plan_alloc(p);
+  if (s != ATK_OK) { atucker_plan_destroy(p); return s; }
+  *plan = p;
+  return ATK_OK;
+}
+
+int atucker_plan_set_option(atucker_plan_t p, int key, int64_t value) {
+  if (!p) { set_error("plan is null"); return ATK_EINVAL; }
+  switch (key) {
+    case ATK_OPT_EIG_ARITH:
+      if (value != ATK_EIG_ROT_FP32 && value != ATK_EIG_ROT_FP64) break;
+      p->eig_arith = (int)value;
+      return ATK_OK;
+    case ATK_OPT_SYNC:
+      p->sync = value ? 1 : 0;
+      return ATK_OK;
+    case ATK_OPT_TIMING:
+      p->timing = value ? 1 : 0;
+      p->recs.clear();
+      p->evnext = 0;
+      p->gram_launches = p->runs = 0;
+      p->launches_mark = launch_count();
+      return ATK_OK;
+    case ATK_OPT_JACOBI_MAX_SWEEPS:
+      if (value < 1 || value > 200) break;
+      p->max_sweeps = (int)value;
+      return ATK_OK;
+    default:
+      break;
+  }
+  set_error("unknown option key or value");
+  return ATK_EINVAL;
+}
+
+int atucker_plan_sync(atucker_plan_t p) {
+  if (!p) { set_error("plan is null"); return ATK_EINVAL; }
+  int h = 0;
+  ATK_CUDA(cudaMemcpyAsync(&h, p->dev_status, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  ATK_CUDA(cudaStreamSynchronize(p->st));
+  ATK_CUDA(cudaMemsetAsync(p->dev_status, 0, sizeof(int), p->st));
+  if (h & DEV_TIMEOUT) { set_error("device-side bounded wait timed out"); return ATK_ETIMEOUT; }
+  if (h & DEV_CHOL) { set_error("ALS: Cholesky pivot not positive (rank-deficient L or R)"); return ATK_ERANK; }
+  if (h & DEV_NOCONV) { set_error("Jacobi eigensolver reached its sweep cap"); return ATK_ENOCONV; }
+  return ATK_OK;
+}
+
+int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* factors_out, double* discarded_out) {
+  if (!p || !x || !core_out || !factors_out) { set_error("null argument"); return ATK_EINVAL; }
+  cudaStream_t st = p->st;
+  int64_t cur[8];
+  for (int k = 0; k < p->order; ++k) cur[k] = p->dims[k];
+  const float* Y = x;
+  const bool need_norms = discarded_out != nullptr;
+  const bool tm = p->timing != 0;
+  cudaEvent_t e_first = nullptr, e_prev = nullptr;
+  // mark(phase): close the running phase at a new event (timing mode only).
+  auto mark = [&](int phase) -> int {
+    if (!tm) return ATK_OK;
+    cudaEvent_t e = p->ev();
+    ATK_CUDA(cudaEventRecord(e, st));
+    if (phase >= 0) p->recs.push_back({phase, e_prev, e});
+    e_prev = e;
+    return ATK_OK;
+  };
+  if (tm) {
+    ATK_TRY(mark(-1));
+    e_first = e_prev;
+    p->runs++;
+  }
+  for (int step = 0; step < p->order; ++step) {
+    const int n = p->mode_order[step];
+    const View v = make_view(p->order, cur, n);
+    const int64_t R = p->ranks[n];
+    float* out = (step == p->order - 1) ? core_out : p->buf[step & 1];
+    float* U32 = factors_out + p->foff[n];
+    double* disc = discarded_out ? discarded_out + n : nullptr;
+    if (p->solver[n] == ATK_EIG) {
+      // S = Y_(n) Y_(n)^T; U = leading eigenvectors; Y' = Y x_n U^T.
+      cudaEvent_t mid = tm ? p->ev() : nullptr;
+      ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid));
+      if (tm) {
+        p->recs.push_back({PH_GRAM, e_prev, mid});
+        e_prev = mid;
+        p->gram_launches++;
+      }
+      ATK_TRY(mark(PH_GRAM_REDUCE));
+      ATK_TRY(eig_top(p->S, v.n, R, p->eig_arith, p->max_sweeps, U32, p->U64, nullptr, disc, p->dev_status,
+                      p->scratch, p->scratch_bytes, st));
+      ATK_TRY(mark(PH_EIG));
+      ATK_TRY(ttm_f32(Y, v, U32, R, out, st));
+      ATK_TRY(mark(PH_TTM));
+    } else {
+      ATK_TRY(als_mode_run(Y, v, R, p->L0 + p->l0off[n], p->als_sweeps, U32, out, p->als, st));
+      ATK_TRY(mark(PH_ALS));
+      if (need_norms) {
+        ATK_TRY(norm2_f32(Y, v.size(), p->norms, (double*)p->scratch, st));
+        ATK_TRY(norm2_f32(out, v.J() * R, p->norms + 1, (double*)p->scratch, st));
+        sub_kernel<<<1, 1, 0, st>>>(p->norms, p->norms + 1, disc);
+        ATK_LAUNCHED();
+        ATK_TRY(mark(PH_OTHER));
+      }
+    }
+    cur[n] = R;
+    Y = out;
+  }
+  if (tm) p->recs.push_back({PH_TOTAL, e_first, e_prev});
+  if (p->order == 0) return ATK_OK;
+  if (p->sync) return atucker_plan_sync(p);
+  return ATK_OK;
+}
+
+int atucker_sthosvd_host(atucker_plan_t p, const float* x_host, float* core_host, float* factors_host,
+                         double* discarded_host) {
+  if (!p || !x_host || !core_host || !factors_host) { set_error("null argument"); return ATK_EINVAL; }
+  if (!p->x_dev) {
+    size_t need = (size_t)p->total * 4 + (size_t)p->core_total * 4 + (size_t)p->fac_total * 4 + 8 * 8 + 1024;
+    char* base = nullptr;
+    ATK_CUDA(cudaMalloc(&base, need));
+    Arena ar{base, need, 0};
+    p->x_dev = (float*)ar.take((size_t)p->total * 4);
+    p->core_dev = (float*)ar.take((size_t)p->core_total * 4);
+    p->fac_dev = (float*)ar.take((size_t)p->fac_total * 4);
+    p->disc_dev = (double*)ar.take(8 * 8);
+  }
+  ATK_CUDA(cudaMemcpyAsync(p->x_dev, x_host, (size_t)p->total * 4, cudaMemcpyHostToDevice, p->st));
+  int s = atucker_sthosvd(p, p->x_dev, p->core_dev, p->fac_dev, discarded_host ? p->disc_dev : nullptr);
+  if (s != ATK_OK) return s;
+  ATK_CUDA(cudaMemcpyAsync(core_host, p->core_dev, (size_t)p->core_total * 4, cudaMemcpyDeviceToHost, p->st));
+  ATK_CUDA(cudaMemcpyAsync(factors_host, p->fac_dev, (size_t)p->fac_total * 4, cudaMemcpyDeviceToHost, p->st));
+  if (discarded_host)
+    ATK_CUDA(cudaMemcpyAsync(discarded_host, p->disc_dev, (size_t)p->order * 8, cudaMemcpyDeviceToHost, p->st));
+  return atucker_plan_sync(p);
+}
+
+int atucker_plan_timings(atucker_plan_t p, double* out, int count) {
+  if (!p || !out || count < PH_SLOTS) { set_error("timings: need a plan and >= 10 output slots"); return ATK_EINVAL; }
+  ATK_CUDA(cudaStreamSynchronize(p->st));
+  for (int i = 0; i < count; ++i) out[i] = 0.0;
+  for (const auto& r : p->recs) {
+    float ms = 0.f;
+    ATK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    out[r.phase] += ms;
+  }
+  long long now = launch_count();
+  out[PH_TOTAL + 1] = (double)p->gram_launches;
+  out[PH_TOTAL + 2] = (double)(now - p->launches_mark);
+  out[PH_TOTAL + 3] = (double)p->runs;
+  p->recs.clear();
+  p->evnext = 0;
+  p->gram_launches = p->runs = 0;
+  p->launches_mark = now;
+  return ATK_OK;
+}
+
+void atucker_plan_destroy(atucker_plan_t p) {
+  if (!p) return;
+  if (p->st) cudaStreamSynchronize(p->st);
+  else cudaDeviceSynchronize();
+  for (cudaEvent_t e : p->evpool) cudaEventDestroy(e);
+  if (p->ws) cudaFree(p->ws);
+  if (p->x_dev) cudaFree(p->x_dev);
+  delete p;
+}
+
+int atucker_sthosvd_oneshot(const float* x, int order, const int64_t* dims, const int64_t* ranks, const int* mode_order,
+                            const int* solver_per_mode, float* core_out, float* factors_out) {
+  atucker_plan_t p = nullptr;
+  ATK_TRY(atucker_plan_create(&p, order, dims, ranks, mode_order, solver_per_mode, ATK_FP32, 5, 0, nullptr));
+  p->sync = 1;
+  int s = atucker_sthosvd(p, x, core_out, factors_out, nullptr);
+  atucker_plan_destroy(p);
+  return s;
+}
+
+const char* atucker_last_error(void) { return g_err.c_str(); }
+const char* atucker_version(void) { return "0.1.0"; }
+
+// ------------------------------------------------------ step-level entry points
+struct StreamScratch {
+  void* ptr = nullptr;
+  cudaStream_t st;
+  explicit StreamScratch(cudaStream_t s) : st(s) {}
+  int alloc(size_t bytes) {
+    cudaError_t e = cudaMallocAsync(&ptr, bytes, st);
+    if (e != cudaSuccess) { ptr = nullptr; return cuda_status(e, "cudaMallocAsync(scratch)"); }
+    return ATK_OK;
+  }
+  ~StreamScratch() {
+    if (ptr) cudaFreeAsync(ptr, st);
+  }
+};
+
+static int check_view(int64_t lo, int64_t n, int64_t hi) {
+  if (lo < 1 || n < 1 || hi < 1) { set_error("view extents must be >= 1"); return ATK_EINVAL; }
+  if ((double)lo * (double)n * (double)hi >= 2147483648.0) { set_error("tensor must have fewer than 2^31 elements"); return ATK_EUNSUPPORTED; }
+  return ATK_OK;
+}
+
+static int read_status(int* dev, cudaStream_t st) {
+  int h = 0;
+  ATK_CUDA(cudaMemcpyAsync(&h, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ATK_CUDA(cudaStreamSynchronize(st));
+  if (h & DEV_TIMEOUT) { set_error("device-side bounded wait timed out"); return ATK_ETIMEOUT; }
+  if (h & DEV_CHOL) { set_error("Cholesky pivot not positive"); return ATK_ERANK; }
+  if (h & DEV_NOCONV) { set_error("Jacobi eigensolver reached its sweep cap"); return ATK_ENOCONV; }
+  return ATK_OK;
+}
+
+int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precision, double* S_out, void* stream) {
+  if (!y || !S_out) { set_error("null argument"); return ATK_EINVAL; }
+  ATK_TRY(check_view(lo, n, hi));
+  if (precision != ATK_FP32) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  if (n > 4096) { set_error("Gram needs n <= 4096"); return ATK_EUNSUPPORTED; }
+  cudaStream_t st = (cudaStream_t)stream;
+  View v{lo, n, hi};
+  StreamScratch sc(st);
+  size_t bytes = gram_scratch_bytes(v);
+  ATK_TRY(sc.alloc(bytes));
+  return gram_f32(y, v, S_out, (float*)sc.ptr, bytes, st);
+}
+
+int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* U, int64_t R, int precision,
+                float* out, void* stream) {
+  if (!y || !U || !out) { set_error("null argument"); return ATK_EINVAL; }
+  ATK_TRY(check_view(lo, n, hi));
+  if (R < 1 || R > 1024) { set_error("TTM needs 1 <= R <= 1024"); return ATK_EUNSUPPORTED; }
+  if (precision != ATK_FP32) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  View v{lo, n, hi};
+  return ttm_f32(y, v, U, R, out, (cudaStream_t)stream);
+}
+
+int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, float* U_out, double* lambda_out,
+                double* discarded_out, void* stream) {
+  if (!S || !U_out) { set_error("null argument"); return ATK_EINVAL; }
+  if (n < 1 || R < 1 || R > n || n > 1024) { set_error("need 1 <= R <= n <= 1024"); return ATK_EUNSUPPORTED; }
+  if (eig_arith != ATK_EIG_ROT_FP32 && eig_arith != ATK_EIG_ROT_FP64) { set_error("bad eig_arith"); return ATK_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  StreamScratch sc(st);
+  size_t sb = std::max(eig_scratch_bytes(n, eig_arith), (size_t)n * R * 8 + smallla_scratch_bytes(n, R) + 1024);
+  size_t bytes = sb + (size_t)n * R * 8 + 1024;
+  ATK_TRY(sc.alloc(bytes));
+  Arena ar{(char*)sc.ptr, bytes, 0};
+  int* status = (int*)ar.take(256);
+  double* U64 = (double*)ar.take((size_t)n * R * 8);
+  char* scratch = (char*)ar.take(sb);
+  ATK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  ATK_TRY(eig_top(S, n, R, eig_arith, 40, U_out, U64, lambda_out, discarded_out, status, scratch, sb, st));
+  return read_status(status, st);
+}
+
+int atucker_als_mode(const float* y, int64_t lo, int64_t n, int64_t hi, int64_t R, const double* L0, uint64_t seed,
+                     int mode, int sweeps, int precision, float* U_out, float* core_out, void* stream) {
+  if (!y || !U_out || !core_out) { set_error("null argument"); return ATK_EINVAL; }
+  ATK_TRY(check_view(lo, n, hi));
+  if (R < 1 || R > n || R > 128 || R > lo * hi) { set_error("ALS needs 1 <= R <= min(n, J, 128)"); return ATK_ERANK; }
+  if (precision != ATK_FP32) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  cudaStream_t st = (cudaStream_t)stream;
+  View v{lo, n, hi};
+  size_t sb = als_scratch_need(v, R);
+  size_t nr = (size_t)(n * R), rr = (size_t)(R * R);
+  size_t bytes = sb + (nr * 8) * 4 + rr * 8 * 3 + nr * 4 + rr * 4 + (size_t)v.J() * R * 4 + 16 * 256;
+  StreamScratch sc(st);
+  ATK_TRY(sc.alloc(bytes));
+  Arena ar{(char*)sc.ptr, bytes, 0};
+  AlsBufs b{};
+  b.dev_status = (int*)ar.take(256);
+  b.L = (double*)ar.take(nr * 8);
+  b.Lt = (double*)ar.take(nr * 8);
+  b.A = (double*)ar.take(nr * 8);
+  double* l0d = (double*)ar.take(nr * 8);
+  b.G = (double*)ar.take(rr * 8);
+  b.B = (double*)ar.take(rr * 8);
+  b.Rhat = (double*)ar.take(rr * 8);
+  b.Lt32 = (float*)ar.take(nr * 4);
+  b.M32 = (float*)ar.take(rr * 4);
+  b.P = (float*)ar.take((size_t)v.J() * R * 4);
+  b.scratch = (char*)ar.take(sb);
+  b.scratch_bytes = sb;
+  if (!b.scratch) { set_error("als: scratch carve failed"); return ATK_EINVAL; }
+  ATK_CUDA(cudaMemsetAsync(b.dev_status, 0, sizeof(int), st));
+  if (L0) {
+    ATK_CUDA(cudaMemcpyAsync(l0d, L0, nr * 8, cudaMemcpyDeviceToDevice, st));
+  } else {
+    std::vector<double> h(nr);
+    als_initial_guess(seed, mode, n, R, h.data());
+    ATK_CUDA(cudaMemcpyAsync(l0d, h.data(), nr * 8, cudaMemcpyHostToDevice, st));
+    ATK_CUDA(cudaStreamSynchronize(st));
+  }
+  ATK_TRY(als_mode_run(y, v, R, l0d, sweeps > 0 ? sweeps : 5, U_out, core_out, b, st));
+  return read_status(b.dev_status, st);
+}
+
+}  // extern "C"
