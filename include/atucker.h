@@ -62,12 +62,27 @@ typedef enum { ATK_FP32 = 0 } atucker_precision;
  * orthonormalisation of U run in float64. */
 typedef enum { ATK_EIG_ROT_FP32 = 0, ATK_EIG_ROT_FP64 = 1 } atucker_eig_arith;
 
+/* Eigensolver method for EIG modes (all give the R leading eigenvectors of S).
+ * FULL_JACOBI diagonalises the whole I_n x I_n Gram.  SUBSPACE runs block
+ * subspace iteration on m = R + p columns (p = min(max(8, R), 32)), projects
+ * (Rayleigh-Ritz), and diagonalises the m x m projection with the same Jacobi.
+ * It iterates until (theta_m / theta_R) * max_j<R ||S q_j - theta_j q_j|| /
+ * (theta_R - theta_m) <= 1e-6.  That quantity is a Davis-Kahan bound times the
+ * contraction of the refinement step below.  It falls back to FULL_JACOBI
+ * when theta_m > theta_R / 2 (a clustered cut) or after 20 iterations.  AUTO uses SUBSPACE when
+ * 2m <= I_n and float32 rotations are selected.  Every method ends with the
+ * same float64 refinement of the leading block (the m Ritz vectors, or the R
+ * Jacobi vectors): one subspace-iteration step, a Rayleigh-Ritz projection
+ * and simultaneous Jacobi steps on it, all in float64. */
+typedef enum { ATK_EIG_AUTO = 0, ATK_EIG_FULL_JACOBI = 1, ATK_EIG_SUBSPACE = 2 } atucker_eig_method;
+
 /* Keys for atucker_plan_set_option. */
 typedef enum {
   ATK_OPT_EIG_ARITH = 1,  /* atucker_eig_arith; default ATK_EIG_ROT_FP32 */
   ATK_OPT_SYNC = 2,       /* 1: atucker_sthosvd synchronises and returns the device status (default 0) */
   ATK_OPT_JACOBI_MAX_SWEEPS = 3, /* sweep cap of the Jacobi eigensolver (default 40) */
-  ATK_OPT_TIMING = 4      /* 1: record CUDA events around each phase (see atucker_plan_timings) */
+  ATK_OPT_TIMING = 4,     /* 1: record CUDA events around each phase (see atucker_plan_timings) */
+  ATK_OPT_EIG_METHOD = 5  /* atucker_eig_method; default ATK_EIG_AUTO */
 } atucker_option;
 
 typedef struct atucker_plan_s* atucker_plan_t;
@@ -174,17 +189,22 @@ int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* 
                 float* out, void* stream);
 
 /* Leading-R eigenpairs of the symmetric n x n float64 matrix S (Alg. 2, EIG
- * branch) by parallel-order cyclic Jacobi.  Rotations run in float32 or
- * float64 (atucker_eig_arith).  Matrices with n > 128 use block Jacobi with
- * 64 x 64 pair sub-problems.
- *   U_out       n x R float32: the eigenvectors of the R largest eigenvalues,
- *               descending, sign rule as in atucker_sthosvd, orthonormalised
- *               in float64 by one Newton-Schulz polar step
- *   lambda_out  n float64 (nullable): all eigenvalues, descending
- *   discarded_out 1 float64 (nullable): sum of the eigenvalues beyond R
- * Returns ATK_ENOCONV if the sweep cap was reached.  Synchronous. */
-int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, float* U_out, double* lambda_out,
-                double* discarded_out, void* stream);
+ * branch) by parallel-order cyclic Jacobi, on the whole matrix or on a
+ * Rayleigh-Ritz projection (atucker_eig_method).  Rotations run in float32 or
+ * float64 (atucker_eig_arith).  Full Jacobi on n > 128 uses block Jacobi with
+ * 64 x 64 pair sub-problems.  The float64 refinement above follows, so the
+ * kept vectors are orthonormal and the kept eigenvalues are float64 Rayleigh
+ * quotients u^T S u.
+ *   U_out       n x R float32: eigenvectors of the R largest eigenvalues,
+ *               descending, sign rule as in atucker_sthosvd
+ *   lambda_out  n float64 (nullable): [0, R) the kept eigenvalues; [R, n)
+ *               the remaining eigenvalues, descending, from the full Jacobi
+ *               (NaN when the subspace method ran)
+ *   discarded_out 1 float64 (nullable): trace(S) minus the kept eigenvalues
+ * Needs 1 <= R <= n <= 1024 and R <= 128.  Returns ATK_ENOCONV if a sweep cap
+ * was reached.  Synchronous. */
+int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, int eig_method, float* U_out,
+                double* lambda_out, double* discarded_out, void* stream);
 
 /* ALS solver for one mode (Alg. 2, ALS branch, with Alg. 3).
  *   L0       n x R float64, the initial guess (nullable: the plan's seeded

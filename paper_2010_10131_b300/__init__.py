@@ -27,7 +27,8 @@ OK, EINVAL, ERANK, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -
 EIG, ALS = 0, 1
 FP32 = 0
 EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
-OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING = 1, 2, 3, 4
+OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD = 1, 2, 3, 4, 5
+EIG_AUTO, EIG_FULL_JACOBI, EIG_SUBSPACE = 0, 1, 2
 PHASES = ("gram", "gram_reduce", "eig", "ttm", "als", "norms", "total", "gram_launches", "launches", "runs")
 _STATUS = {EINVAL: "EINVAL", ERANK: "ERANK", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENOCONV: "ENOCONV",
            ETIMEOUT: "ETIMEOUT", EUNSUPPORTED: "EUNSUPPORTED"}
@@ -54,7 +55,7 @@ _SIGS = {
     "atucker_version": (ctypes.c_char_p, []),
     "atucker_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "atucker_ttm": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _i32, _vp, _vp]),
-    "atucker_eig": (_i32, [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp]),
+    "atucker_eig": (_i32, [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _vp, _vp]),
     "atucker_als_mode": (_i32, [_vp, _i64, _i64, _i64, _i64, _vp, _u64, _i32, _i32, _i32, _vp, _vp, _vp]),
 }
 
@@ -128,7 +129,8 @@ class Plan:
     """A reusable st-HOSVD plan (atucker_plan_create) bound to one shape."""
 
     def __init__(self, dims, ranks, mode_order=None, solver=None, precision: int = FP32, als_sweeps: int = 5,
-                 seed: int = 0, stream=None, eig_arith: int | None = None, sync: bool = False):
+                 seed: int = 0, stream=None, eig_arith: int | None = None, sync: bool = False,
+                 eig_method: int | None = None):
         self.dims = [int(d) for d in dims]
         self.ranks = [int(r) for r in ranks]
         self.order = len(self.dims)
@@ -143,6 +145,8 @@ class Plan:
             _check(lib().atucker_plan_set_option(self._h, OPT_EIG_ARITH, int(eig_arith)), "set_option")
         if sync:
             _check(lib().atucker_plan_set_option(self._h, OPT_SYNC, 1), "set_option")
+        if eig_method is not None:
+            _check(lib().atucker_plan_set_option(self._h, OPT_EIG_METHOD, int(eig_method)), "set_option")
 
     @property
     def core_numel(self):
@@ -209,12 +213,12 @@ class Plan:
 
 
 def sthosvd(x, dims, ranks, mode_order=None, solver=None, als_sweeps: int = 5, seed: int = 0,
-            eig_arith: int | None = None, with_discarded: bool = False):
+            eig_arith: int | None = None, with_discarded: bool = False, eig_method: int | None = None):
     """Decompose the column-major tensor x (flat CUDA float32).
 
     Returns (core_flat, [U^(n)], discarded or None)."""
     torch = _torch()
-    p = Plan(dims, ranks, mode_order, solver, FP32, als_sweeps, seed, eig_arith=eig_arith)
+    p = Plan(dims, ranks, mode_order, solver, FP32, als_sweeps, seed, eig_arith=eig_arith, eig_method=eig_method)
     disc = torch.zeros(len(dims), device=x.device, dtype=torch.float64) if with_discarded else None
     core, fac = p.run(x, discarded=disc)
     p.sync()
@@ -242,7 +246,7 @@ def ttm(y, lo: int, n: int, hi: int, U, precision: int = FP32):
     return out
 
 
-def eig(S, R: int, eig_arith: int = EIG_ROT_FP32):
+def eig(S, R: int, eig_arith: int = EIG_ROT_FP32, method: int = EIG_AUTO):
     """S: (n, n) float64 CUDA tensor (symmetric).  Returns (U (n,R) float32, lambda (n,), discarded)."""
     torch = _torch()
     n = S.shape[0]
@@ -250,7 +254,7 @@ def eig(S, R: int, eig_arith: int = EIG_ROT_FP32):
     U = torch.empty(n * R, device=S.device, dtype=torch.float32)
     lam = torch.empty(n, device=S.device, dtype=torch.float64)
     disc = torch.empty(1, device=S.device, dtype=torch.float64)
-    _check(lib().atucker_eig(_dev(Scm, torch.float64), n, R, eig_arith, _dev(U, torch.float32),
+    _check(lib().atucker_eig(_dev(Scm, torch.float64), n, R, eig_arith, method, _dev(U, torch.float32),
                              _dev(lam, torch.float64), _dev(disc, torch.float64), _stream_ptr()), "atucker_eig")
     return U.view(R, n).t(), lam, disc
 

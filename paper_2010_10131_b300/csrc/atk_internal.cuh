@@ -128,9 +128,11 @@ int cross_f32(const float* y, const View& v, const float* P, int64_t R, double* 
 
 // Jacobi eigensolver (jacobi.cu).
 size_t eig_scratch_bytes(int64_t n, int arith);
-int eig_top(const double* S, int64_t n, int64_t R, int arith, int max_sweeps, float* U_out, double* U64_out,
-            double* lambda_out, double* discarded_out, int* dev_status, char* scratch, size_t scratch_bytes,
-            cudaStream_t st);
+// method: ATK_EIG_AUTO (Rayleigh-Ritz when R + p <= n/2, else full Jacobi),
+// ATK_EIG_FULL_JACOBI, ATK_EIG_SUBSPACE.
+int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, float* U_out,
+            double* U64_out, double* lambda_out, double* discarded_out, int* dev_status, char* scratch,
+            size_t scratch_bytes, cudaStream_t st);
 
 // Float64 small dense linear algebra (smallla.cu).
 size_t smallla_scratch_bytes(int64_t n, int64_t R);

@@ -81,7 +81,9 @@ struct JWork {
   T* cs;  // 2 * (m/2): c then s per pair
   int* pq;  // 2 * (m/2): p then q per pair
   int* flag;  // [0]: any rotation this sweep, [1]: any rotation at all
+  unsigned short* blk;  // 2 * nblk: (k, l) of the k <= l pair blocks, filled once per solve
 };
+__host__ __device__ inline int nblocks_of(int m) { return (m / 2) * (m / 2 + 1) / 2; }
 
 // Sweeps of the parallel-order Jacobi on shared-memory A (V accumulates).
 // All threads of the CTA participate.  Returns the number of sweeps run;
@@ -92,6 +94,14 @@ __device__ int jacobi_smem(JWork<T> w, int m, T fro, int max_sweeps, bool* conve
   const T thr_abs = JTol<T>::abs * fro;
   int sweep = 0;
   bool conv = false;
+  const int nblk = nblocks_of(m);
+  for (int k = threadIdx.x; k < half; k += blockDim.x) {
+    int base = k * half - k * (k - 1) / 2;  // blocks before row k of the triangle
+    for (int l = k; l < half; ++l) {
+      w.blk[base + (l - k)] = (unsigned short)k;
+      w.blk[nblk + base + (l - k)] = (unsigned short)l;
+    }
+  }
   if (threadIdx.x == 0) w.flag[1] = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) w.flag[0] = 0;
@@ -111,11 +121,8 @@ __device__ int jacobi_smem(JWork<T> w, int m, T fro, int max_sweeps, bool* conve
       }
       __syncthreads();
       // A <- J^T A J on 2x2 blocks (k <= l), mirrored to keep A exactly symmetric.
-      const int nblk = half * (half + 1) / 2;
       for (int idx = threadIdx.x; idx < nblk; idx += blockDim.x) {
-        int k = 0, rem = idx;
-        while (rem >= half - k) { rem -= half - k; ++k; }
-        int l = k + rem;
+        const int k = w.blk[idx], l = w.blk[nblk + idx];
         T ck = w.cs[k], sk = w.cs[half + k], cl = w.cs[l], sl = w.cs[half + l];
         if (sk == T(0) && sl == T(0)) continue;
         int pk = w.pq[k], qk = w.pq[half + k], pl = w.pq[l], ql = w.pq[half + l];
@@ -178,6 +185,7 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(const double* __restr
   T* cs = V + m * m;
   int* pq = reinterpret_cast<int*>(cs + m);
   int* flag = pq + m;
+  unsigned short* blk = reinterpret_cast<unsigned short*>(flag + 2);
   __shared__ double red[256];
   const double* Sm = S + (size_t)blockIdx.x * n * n;
   double loc = 0.0;
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(const double* __restr
     __syncthreads();
   }
   T fro = (T)sqrt(red[0]);
-  JWork<T> w{A, V, cs, pq, flag};
+  JWork<T> w{A, V, cs, pq, flag, blk};
   bool conv = true;
   if (m >= 2) jacobi_smem<T>(w, m, fro, max_sweeps, &conv);
   if (!conv && threadIdx.x == 0) atomicOr(status, DEV_NOCONV);
@@ -234,6 +242,7 @@ __global__ void __launch_bounds__(256) jacobi_block_kernel(BlockJacobiArgs args,
   T* cs = s3 + JS * JS;
   int* pq = reinterpret_cast<int*>(cs + JS);
   int* flag = pq + JS;
+  unsigned short* blk = reinterpret_cast<unsigned short*>(flag + 2);
   const int m = args.m, mb = args.mb, half = mb / 2;
   const unsigned G = gridDim.x;
   for (int sweep = 0; sweep < args.max_sweeps; ++sweep) {
@@ -248,7 +257,7 @@ __global__ void __launch_bounds__(256) jacobi_block_kernel(BlockJacobiArgs args,
           s1[idx] = (u == v) ? T(1) : T(0);
         }
         __syncthreads();
-        JWork<T> w{s0, s1, cs, pq, flag};
+        JWork<T> w{s0, s1, cs, pq, flag, blk};
         bool conv;
         jacobi_smem<T>(w, JS, fro, args.inner_sweeps, &conv);
         if (threadIdx.x == 0 && flag[1]) atomicOr(args.sweep_flags + sweep, 1);
@@ -348,7 +357,14 @@ __global__ void __launch_bounds__(1024) select_kernel(const T* __restrict__ diag
   __shared__ int order[1024];
   __shared__ double lam[1024];
   __shared__ double red[1024];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = (double)diag[(int64_t)i * dstride];
+  // Sort key: the eigenvalue, with NaN ordered below everything, ties broken by
+  // index.  That is a total order, so the ranks below are a permutation of
+  // 0..n-1 whatever the input holds, and every gathered column stays in range.
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = (double)diag[(int64_t)i * dstride];
+    lam[i] = isnan(v) ? -INFINITY : v;
+    order[i] = i;
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double li = lam[i];
@@ -397,16 +413,18 @@ __global__ void __launch_bounds__(1024) select_kernel(const T* __restrict__ diag
 namespace {
 template <typename T>
 size_t small_smem(int m) {
-  return (size_t)2 * m * m * sizeof(T) + (size_t)m * sizeof(T) + (size_t)(m + 2) * sizeof(int) + 16;
+  return (size_t)2 * m * m * sizeof(T) + (size_t)m * sizeof(T) + (size_t)(m + 2) * sizeof(int) +
+         (size_t)2 * nblocks_of(m) * sizeof(unsigned short) + 16;
 }
 template <typename T>
 bool use_small(int n) {
   int m = n + (n & 1);
-  return small_smem<T>(m) <= 200 * 1024;
+  return small_smem<T>(m) <= 220 * 1024;
 }
 template <typename T>
 size_t block_smem() {
-  return (size_t)4 * JS * JS * sizeof(T) + JS * sizeof(T) + (JS + 2) * sizeof(int) + 16;
+  return (size_t)4 * JS * JS * sizeof(T) + JS * sizeof(T) + (JS + 2) * sizeof(int) +
+         (size_t)2 * nblocks_of(JS) * sizeof(unsigned short) + 16;
 }
 template <typename T>
 size_t eig_bytes_t(int64_t n) {
@@ -507,27 +525,487 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
 }
 }  // namespace
 
+// ------------------------------------------------- Rayleigh-Ritz subspace path
+// Only the R leading eigenvectors are needed (Alg. 2: "R_n leading
+// eigenvectors of S").  For m = R + p well below n, block subspace iteration
+// (float32 products of S with an n x m block, shifted CholeskyQR3)
+// followed by a Rayleigh-Ritz projection B = Q^T S Q reduces the eigenproblem
+// to m x m.  The projection is then diagonalised by the same one-CTA
+// parallel-order Jacobi as above.  The iteration restarts from the Ritz vectors
+// until the predicted error after the float64 refinement,
+//   (theta_m / theta_R) * max_{j<R} ||S q_j - theta_j q_j|| / (theta_R - theta_m),
+// drops below RR_TARGET.  That is a Davis-Kahan bound on the angle between
+// q_R and the leading space, times the contraction of the refinement's
+// subspace step.  When theta_m / theta_R > RR_SLOW_RATIO (the R-th eigenvalue
+// sits in a cluster, so subspace iteration would crawl) or RR_MAXIT
+// iterations pass, the full Jacobi runs instead.
+constexpr int RR_MAXIT = 20;
+constexpr double RR_TARGET = 1e-6;
+constexpr double RR_SLOW_RATIO = 0.5;
+
+int rr_width(int64_t n, int64_t R) {
+  int64_t p = std::max<int64_t>(8, std::min<int64_t>(R, 32));
+  return (int)std::min<int64_t>(std::min<int64_t>(n, R + p), 156);
+}
+
+__global__ void rand_fill_kernel(float* __restrict__ Q, int64_t count, uint64_t seed) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  Q[i] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+}
+
+// C (M x N) = A (M x K) * op(B), op(B) = B (K x N) or B^T with B N x K.  float32,
+// column-major, one thread per output, four partial sums.
+__global__ void gemm_f32_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t M, int64_t K,
+                                int64_t N, int transB, float* __restrict__ C) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= M * N) return;
+  int64_t i = o % M, j = o / M;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int64_t t = 0;
+  if (!transB) {
+    for (; t + 3 < K; t += 4) {
+      s0 = fmaf(A[i + M * t], B[t + K * j], s0);
+      s1 = fmaf(A[i + M * (t + 1)], B[t + 1 + K * j], s1);
+      s2 = fmaf(A[i + M * (t + 2)], B[t + 2 + K * j], s2);
+      s3 = fmaf(A[i + M * (t + 3)], B[t + 3 + K * j], s3);
+    }
+    for (; t < K; ++t) s0 = fmaf(A[i + M * t], B[t + K * j], s0);
+  } else {
+    for (; t + 3 < K; t += 4) {
+      s0 = fmaf(A[i + M * t], B[j + N * t], s0);
+      s1 = fmaf(A[i + M * (t + 1)], B[j + N * (t + 1)], s1);
+      s2 = fmaf(A[i + M * (t + 2)], B[j + N * (t + 2)], s2);
+      s3 = fmaf(A[i + M * (t + 3)], B[j + N * (t + 3)], s3);
+    }
+    for (; t < K; ++t) s0 = fmaf(A[i + M * t], B[j + N * t], s0);
+  }
+  C[o] = (s0 + s1) + (s2 + s3);
+}
+
+// C (M x N, float64) = A^T B with A K x M and B K x N float32 (partial sums in float32).
+__global__ void gemm_f32_tn_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t K, int64_t M,
+                                   int64_t N, double* __restrict__ C) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= M * N) return;
+  int64_t i = o % M, j = o / M;
+  const float* a = A + K * i;
+  const float* b = B + K * j;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int64_t t = 0;
+  for (; t + 3 < K; t += 4) {
+    s0 = fmaf(a[t], b[t], s0);
+    s1 = fmaf(a[t + 1], b[t + 1], s1);
+    s2 = fmaf(a[t + 2], b[t + 2], s2);
+    s3 = fmaf(a[t + 3], b[t + 3], s3);
+  }
+  for (; t < K; ++t) s0 = fmaf(a[t], b[t], s0);
+  C[o] = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
+}
+
+// Normalise each column of Y (n x m) to unit length; one warp per column.
+__global__ void colnorm_f32_kernel(float* __restrict__ Y, int64_t n, int64_t m) {
+  const int64_t col = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (col >= m) return;
+  float* y = Y + n * col;
+  double s = 0.0;
+  for (int64_t i = lane; i < n; i += 32) s += (double)y[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  float inv = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f;
+  for (int64_t i = lane; i < n; i += 32) y[i] *= inv;
+}
+
+// One CTA: Cholesky of G + shift * max(diag G) * I (G m x m SPD, float64 in,
+// float32 work) and the inverse of its lower factor, Linv (m x m column-major
+// float32).  A pivot at or below a tiny floor (rank-deficient block) is raised
+// to the floor, so the factor stays finite.
+__global__ void __launch_bounds__(256) chol_inv_f32_kernel(const double* __restrict__ G, int m, float shift,
+                                                           float* __restrict__ Linv) {
+  extern __shared__ float sm[];
+  float* L = sm;  // m x m, column-major
+  float* Li = sm + m * m;
+  __shared__ float dscale;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) L[idx] = (float)G[idx];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float d = 0.f;
+    for (int j = 0; j < m; ++j) d = fmaxf(d, L[j + m * j]);
+    for (int j = 0; j < m; ++j) L[j + m * j] += shift * d;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float d = 0.f;
+    for (int j = 0; j < m; ++j) d = fmaxf(d, L[j + m * j]);
+    dscale = d;
+  }
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (threadIdx.x == 0) {
+      float d = L[j + m * j];
+      float floor_v = 1e-12f * dscale + 1e-30f;
+      L[j + m * j] = sqrtf(d > floor_v ? d : floor_v);
+    }
+    __syncthreads();
+    float ljj = L[j + m * j];
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i + m * j] /= ljj;
+    __syncthreads();
+    int rem = m - j - 1;
+    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+      int i = j + 1 + idx % rem, k = j + 1 + idx / rem;
+      if (i >= k) L[i + m * k] = fmaf(-L[i + m * j], L[k + m * j], L[i + m * k]);
+    }
+    __syncthreads();
+  }
+  // Columns of Linv by forward substitution, one thread per column.
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      if (i < k) { Li[i + m * k] = 0.f; continue; }
+      float acc = (i == k) ? 1.f : 0.f;
+      for (int t = k; t < i; ++t) acc = fmaf(-L[i + m * t], Li[t + m * k], acc);
+      Li[i + m * k] = acc / L[i + m * i];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Linv[idx] = Li[idx];
+}
+
+// res[0] = max_{j<R} ||Z[:, j] - theta_j Q[:, j]|| / theta_0.  One CTA.
+__global__ void __launch_bounds__(256) ritz_residual_kernel(const float* __restrict__ Z, const float* __restrict__ Q,
+                                                            const double* __restrict__ theta, int64_t n, int64_t R,
+                                                            double* __restrict__ res) {
+  __shared__ double red[256];
+  __shared__ double worst;
+  if (threadIdx.x == 0) worst = 0.0;
+  __syncthreads();
+  for (int64_t j = 0; j < R; ++j) {
+    double s = 0.0;
+    const double th = theta[j];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      double d = (double)Z[i + n * j] - th * Q[i + n * j];
+      s += d * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) worst = fmax(worst, sqrt(red[0]));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) res[0] = worst / fmax(fabs(theta[0]), 1e-300);
+}
+
+__global__ void f32_to_f64_kernel2(const float* __restrict__ s, double* __restrict__ d, int64_t count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) d[i] = (double)s[i];
+}
+
+namespace {
+struct RRBufs {
+  float *Sf, *Q, *Y, *Z, *Wf, *Linv, *Vb, *diag;
+  double *G, *W64, *theta, *res;
+};
+size_t rr_bytes(int64_t n, int m) {
+  size_t nm = (size_t)n * m, mm = (size_t)m * m;
+  return sizeof(float) * ((size_t)n * n + 4 * nm + 2 * mm + m) + sizeof(double) * (2 * mm + m + 8) + 16 * 256;
+}
+// One CholeskyQR pass: Q = Y chol(Y^T Y + shift I)^{-T} after normalising the
+// columns of Y (in place).
+int cholqr_pass_f32(float* Y, float* Q, int64_t n, int m, float shift, RRBufs& b, cudaStream_t st) {
+  colnorm_f32_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Y, n, m);
+  ATK_LAUNCHED();
+  gemm_f32_tn_kernel<<<(unsigned)ceil_div((int64_t)m * m, 256), 256, 0, st>>>(Y, Y, n, m, m, b.G);
+  ATK_LAUNCHED();
+  size_t sm = (size_t)2 * m * m * sizeof(float);
+  ATK_CUDA(cudaFuncSetAttribute(chol_inv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  chol_inv_f32_kernel<<<1, 256, sm, st>>>(b.G, m, shift, b.Linv);
+  ATK_LAUNCHED();
+  gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(Y, b.Linv, n, m, m, 1, Q);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+// Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Zhang, Yamamoto, SISC 2020):
+// the shifted first pass cannot break down, and it leaves a basis with modest
+// condition number.  The two plain passes then make it orthonormal to
+// float32 accuracy.  Y and T are overwritten; the result is in Q.
+int cholqr3_f32(float* Y, float* T, float* Q, int64_t n, int m, RRBufs& b, cudaStream_t st) {
+  ATK_TRY(cholqr_pass_f32(Y, T, n, m, 1e-5f, b, st));
+  ATK_TRY(cholqr_pass_f32(T, Y, n, m, 0.f, b, st));
+  ATK_TRY(cholqr_pass_f32(Y, Q, n, m, 0.f, b, st));
+  return ATK_OK;
+}
+}  // namespace
+
+// Leading Ritz block of S by subspace iteration + Rayleigh-Ritz + Jacobi.
+// On success writes Qblk (n x m float64, m = rr_width(n, R), Ritz vectors in
+// descending Ritz-value order, orthonormal to float32 accuracy) and returns
+// ATK_OK; returns ATK_ENOCONV if the residual test never passed.
+int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, int* dev_status, char* scratch,
+           size_t scratch_bytes, cudaStream_t st) {
+  const int m = rr_width(n, R);
+  Arena ar{scratch, scratch_bytes, 0};
+  RRBufs b;
+  size_t nm = (size_t)n * m, mm = (size_t)m * m;
+  b.Sf = (float*)ar.take(sizeof(float) * n * n);
+  b.Q = (float*)ar.take(sizeof(float) * nm);
+  b.Y = (float*)ar.take(sizeof(float) * nm);
+  b.Z = (float*)ar.take(sizeof(float) * nm);
+  b.Wf = (float*)ar.take(sizeof(float) * nm);
+  b.Linv = (float*)ar.take(sizeof(float) * mm);
+  b.Vb = (float*)ar.take(sizeof(float) * mm);
+  b.diag = (float*)ar.take(sizeof(float) * m);
+  b.G = (double*)ar.take(sizeof(double) * mm);
+  b.W64 = (double*)ar.take(sizeof(double) * mm);
+  b.theta = (double*)ar.take(sizeof(double) * m);
+  b.res = (double*)ar.take(sizeof(double) * 8);
+  if (!b.res) { set_error("rr: scratch too small"); return ATK_EINVAL; }
+  ATK_TRY(f64_to_f32(S, b.Sf, n * n, st));
+  rand_fill_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, st>>>(b.Y, (int64_t)nm, 0x5EEDULL + (uint64_t)n);
+  ATK_LAUNCHED();
+  ATK_TRY(cholqr3_f32(b.Y, b.Z, b.Q, n, m, b, st));
+  const int mp = m + (m & 1);
+  const size_t jsm = small_smem<float>(mp);
+  ATK_CUDA(cudaFuncSetAttribute(jacobi_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
+  for (int it = 0; it < RR_MAXIT; ++it) {
+    // Subspace step: Q <- orth(S Q).
+    gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Sf, b.Q, n, n, m, 0, b.Y);
+    ATK_LAUNCHED();
+    ATK_TRY(cholqr3_f32(b.Y, b.Z, b.Q, n, m, b, st));
+    if (it < 2) continue;  // a few plain steps before the first projection
+    // Rayleigh-Ritz: Z = S Q, B = Q^T Z, B = W diag(theta) W^T.
+    gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Sf, b.Q, n, n, m, 0, b.Z);
+    ATK_LAUNCHED();
+    gemm_f32_tn_kernel<<<(unsigned)ceil_div((int64_t)mm, 256), 256, 0, st>>>(b.Q, b.Z, n, m, m, b.G);
+    ATK_LAUNCHED();
+    jacobi_small_kernel<float><<<1, 256, jsm, st>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
+    ATK_LAUNCHED();
+    select_kernel<float><<<1, 1024, 0, st>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
+    ATK_LAUNCHED();
+    ATK_TRY(f64_to_f32(b.W64, b.Linv, (int64_t)mm, st));
+    // Ritz vectors Q W (sorted by descending theta) and S Q W = Z W.
+    gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Q, b.Linv, n, m, m, 0, b.Y);
+    ATK_LAUNCHED();
+    gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Z, b.Linv, n, m, m, 0, b.Wf);
+    ATK_LAUNCHED();
+    ritz_residual_kernel<<<1, 256, 0, st>>>(b.Wf, b.Y, b.theta, n, R, b.res);
+    ATK_LAUNCHED();
+    std::swap(b.Q, b.Y);
+    double hres[4] = {0.0, 0.0, 0.0, 0.0};
+    ATK_CUDA(cudaMemcpyAsync(hres, b.res, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ATK_CUDA(cudaMemcpyAsync(hres + 1, b.theta, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ATK_CUDA(cudaMemcpyAsync(hres + 2, b.theta + (R - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+    ATK_CUDA(cudaMemcpyAsync(hres + 3, b.theta + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+    ATK_CUDA(cudaStreamSynchronize(st));
+    const double res = hres[0] * hres[1], thR = hres[2], thm = fmax(hres[3], 0.0);
+    if (!(res == res) || !(thR == thR) || res > 1e300) return ATK_ENOCONV;  // non-finite: full Jacobi
+    if (!(thR > 0.0) || thm > RR_SLOW_RATIO * thR) return ATK_ENOCONV;     // clustered: full Jacobi
+    const double predicted = (thm / thR) * res / (thR - thm);
+    if (predicted <= RR_TARGET) {
+      f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Q, Qblk, n * (int64_t)m);
+      ATK_LAUNCHED();
+      return ATK_OK;
+    }
+  }
+  return ATK_ENOCONV;
+}
+
+// ----------------------------------------------------- float64 refinement
+__global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n,
+                                      int64_t R, const double* __restrict__ norms, double rel,
+                                      double* __restrict__ W);
+__global__ void colnorms_f64_kernel(const double* __restrict__ Z, int64_t n, int64_t R, double* __restrict__ norms);
+__global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R);
+
+// W = I + X for the k x k symmetric float64 matrix B: for every pair p < q,
+// the Jacobi rotation that zeroes b_pq in its own 2 x 2 problem, to first order
+// (W_pq = s, W_qp = -s).  Pairs whose angle would be large (a nearly
+// degenerate pair, |b_pq| > |b_pp - b_qq| / 10) are left alone; rotations
+// inside such a cluster do not change the subspaces this refinement serves.
+__global__ void simrot_kernel(const double* __restrict__ B, int64_t k, double* __restrict__ W) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= k * k) return;
+  int64_t i = o % k, j = o / k;
+  if (i == j) { W[o] = 1.0; return; }
+  int64_t p = i < j ? i : j, q = i < j ? j : i;
+  double bpp = B[p + k * p], bqq = B[q + k * q], bpq = B[p + k * q];
+  double s = 0.0;
+  if (bpq != 0.0 && fabs(bpq) * 10.0 <= fabs(bqq - bpp)) {
+    double tau = (bqq - bpp) / (2.0 * bpq);
+    double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    s = t / sqrt(1.0 + t * t);
+  }
+  // column p of the rotated basis gains -s * (old column q); column q gains +s * (old column p)
+  W[o] = (i == p) ? s : -s;  // (row p, col q) = +s ; (row q, col p) = -s
+}
+
+// order[0..k) = indices of diag(B) sorted descending (NaN lowest, ties by
+// index), lam[r] = B[order[r], order[r]] for r < R, disc = trace(S) - sum lam.
+// One CTA, k <= 1024.
+__global__ void __launch_bounds__(256) order_diag_kernel(const double* __restrict__ B, int k, int R,
+                                                         const double* __restrict__ S, int64_t n,
+                                                         int* __restrict__ order, double* __restrict__ lam_out,
+                                                         double* __restrict__ disc_out) {
+  __shared__ double key[1024];
+  __shared__ int ord[1024];
+  __shared__ double red[256];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double v = B[i + (int64_t)k * i];
+    key[i] = isnan(v) ? -INFINITY : v;
+    ord[i] = i;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double li = key[i];
+    int rank = 0;
+    for (int j = 0; j < k; ++j) rank += (key[j] > li) || (key[j] == li && j < i);
+    ord[rank] = i;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < k; r += blockDim.x) order[r] = ord[r];
+  double part = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) part += S[i + n * i];
+  red[threadIdx.x] = part;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double kept = 0.0;
+    for (int r = 0; r < R; ++r) {
+      double l = B[ord[r] + (int64_t)k * ord[r]];
+      kept += l;
+      if (lam_out) lam_out[r] = l;
+    }
+    if (disc_out) *disc_out = red[0] - kept;
+  }
+}
+
+// U[:, r] = QW[:, order[r]] for r < R (n x R float64).
+__global__ void gather_cols_kernel(const double* __restrict__ QW, const int* __restrict__ order, int64_t n, int64_t R,
+                                   double* __restrict__ U) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n * R) return;
+  int64_t i = o % n, r = o / n;
+  U[o] = QW[i + n * order[r]];
+}
+
+__global__ void identity_kernel(double* __restrict__ W, int64_t k) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < k * k) W[o] = (o % k == o / k) ? 1.0 : 0.0;
+}
+
+constexpr int REFINE_ROTATION_STEPS = 3;
+
+size_t refine_bytes(int64_t n, int64_t k) {
+  return sizeof(double) * (size_t)(2 * n * k + 5 * k * k + k + 8) + sizeof(int) * (size_t)k +
+         smallla_scratch_bytes(std::max(n, k), k) + 4096;
+}
+
+// Float64 refinement of an approximate leading block Qb (n x k, columns
+// roughly the leading eigenvectors of S in descending order), then the kept
+// R vectors.  Steps:
+//  1. one subspace-iteration step, Qb <- orth(S Qb): normalise the columns,
+//     then two Newton-Schulz polar steps.  Components outside the leading
+//     k-space shrink by lambda_{k+1}/lambda_j.
+//  2. Rayleigh-Ritz in float64: B = Qb^T S Qb.  The Ritz block is nearly
+//     diagonal; REFINE_ROTATION_STEPS simultaneous Jacobi steps (W from
+//     simrot_kernel, orthonormalised by two polar steps, B <- W^T B W) take
+//     the off-diagonal entries to float64 level.
+//  3. U = (Qb W)[:, top R of diag(B)], one more polar step and the sign rule.
+//     The kept eigenvalues are diag(B), the float64 Rayleigh quotients, and the
+//     discarded energy is trace(S) minus their sum.
+int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, double* U64, double* lambda_out,
+               double* discarded_out, char* scratch, size_t scratch_bytes, cudaStream_t st) {
+  Arena ar{scratch, scratch_bytes, 0};
+  double* Z = (double*)ar.take(sizeof(double) * n * k);
+  double* QW = (double*)ar.take(sizeof(double) * n * k);
+  double* B = (double*)ar.take(sizeof(double) * k * k);
+  double* W = (double*)ar.take(sizeof(double) * k * k);
+  double* Wt = (double*)ar.take(sizeof(double) * k * k);
+  double* T = (double*)ar.take(sizeof(double) * k * k);
+  double* T2 = (double*)ar.take(sizeof(double) * k * k);
+  double* norms = (double*)ar.take(sizeof(double) * (k + 8));
+  int* order = (int*)ar.take(sizeof(int) * k);
+  double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
+  if (!pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
+  const unsigned gk = (unsigned)ceil_div(k * k, 256);
+  // 1. subspace step
+  ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
+  colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, n, k, norms);
+  ATK_LAUNCHED();
+  normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, 1e-5, Qb);
+  ATK_LAUNCHED();
+  ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
+  ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
+  // 2. Rayleigh-Ritz and simultaneous rotations
+  ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
+  ATK_TRY(gemm_tn_f64(Qb, Z, n, k, B, pol, st));
+  identity_kernel<<<gk, 256, 0, st>>>(Wt, k);
+  ATK_LAUNCHED();
+  for (int step = 0; step < REFINE_ROTATION_STEPS && k > 1; ++step) {
+    simrot_kernel<<<gk, 256, 0, st>>>(B, k, W);
+    ATK_LAUNCHED();
+    ATK_TRY(polar_step_f64(W, k, k, pol, st));
+    ATK_TRY(polar_step_f64(W, k, k, pol, st));
+    ATK_TRY(gemm_f64(B, W, k, k, k, T, st));
+    ATK_TRY(gemm_tn_f64(W, T, k, k, B, pol, st));
+    ATK_TRY(gemm_f64(Wt, W, k, k, k, T2, st));
+    std::swap(Wt, T2);
+  }
+  // 3. kept vectors
+  order_diag_kernel<<<1, 256, 0, st>>>(B, (int)k, (int)R, S, n, order, lambda_out, discarded_out);
+  ATK_LAUNCHED();
+  ATK_TRY(gemm_f64(Qb, Wt, n, k, k, QW, st));
+  gather_cols_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(QW, order, n, R, U64);
+  ATK_LAUNCHED();
+  ATK_TRY(polar_step_f64(U64, n, R, pol, st));
+  sign_fix_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(U64, n, R);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+
 size_t eig_scratch_bytes(int64_t n, int arith) {
   size_t jac = arith == ATK_EIG_ROT_FP64 ? eig_bytes_t<double>(n) : eig_bytes_t<float>(n);
   // refinement: Z (n x R) + the float64 small-LA scratch, for R up to n
   size_t ref = (size_t)n * std::min<int64_t>(n, 128) * 8 + smallla_scratch_bytes(n, std::min<int64_t>(n, 128)) + 1024;
-  return std::max(jac, ref);
+  size_t rr = rr_bytes(n, 156);
+  const int64_t kmax = std::min<int64_t>(n, 156);
+  // the Ritz block is carved first and outlives the solver that fills it
+  return (size_t)n * kmax * 8 + 512 + std::max(std::max(jac, ref), std::max(rr, refine_bytes(n, kmax)));
 }
 
-// W[:, r] = Z[:, r] / ||Z[:, r]|| when that norm is above thr, else U[:, r]
-// (a kept eigenvalue at the level of rounding: keep the Jacobi vector).
-// One warp per column.
-__global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n,
-                                      int64_t R, const double* __restrict__ scale, double rel,
-                                      double* __restrict__ W) {
+// norms[r] = ||Z[:, r]||; one warp per column.
+__global__ void colnorms_f64_kernel(const double* __restrict__ Z, int64_t n, int64_t R, double* __restrict__ norms) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   if (warp >= R) return;
-  const double thr = rel * *scale;
   const double* z = Z + (int64_t)warp * n;
   double s = 0.0;
   for (int64_t i = lane; i < n; i += 32) s += z[i] * z[i];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  double nz = sqrt(s);
+  if (lane == 0) norms[warp] = sqrt(s);
+}
+
+// W[:, r] = Z[:, r] / ||Z[:, r]|| when that norm is above rel * max_r ||Z[:, r]||,
+// else U[:, r].  A column whose image under S is at rounding level lies in the
+// numerical null space.  Normalising S u would turn rounding noise into a copy
+// of a leading direction, so such a column keeps its vector.  One warp per column.
+__global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n,
+                                      int64_t R, const double* __restrict__ norms, double rel,
+                                      double* __restrict__ W) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (warp >= R) return;
+  double mx = 0.0;
+  for (int64_t r = 0; r < R; ++r) mx = fmax(mx, norms[r]);
+  const double thr = rel * mx;
+  const double* z = Z + (int64_t)warp * n;
+  double nz = norms[warp];
   double* w = W + (int64_t)warp * n;
   if (nz > thr) {
     for (int64_t i = lane; i < n; i += 32) w[i] = z[i] / nz;
@@ -559,60 +1037,43 @@ __global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R) {
     for (int64_t i = lane; i < n; i += 32) u[i] = -u[i];
 }
 
-__global__ void max_abs_diag_kernel(const double* __restrict__ S, int64_t n, double* out) {
-  __shared__ double red[256];
-  double m = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(S[i + n * i]));
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = red[0];
-}
-
 // Eigen-decomposition + selection + float64 polar orthonormalisation.
 // U64_out (n x R float64) is the orthonormalised basis; U_out its float32 copy.
-int eig_top(const double* S, int64_t n, int64_t R, int arith, int max_sweeps, float* U_out, double* U64_out,
-            double* lambda_out, double* discarded_out, int* dev_status, char* scratch, size_t scratch_bytes,
-            cudaStream_t st) {
+int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, float* U_out,
+            double* U64_out, double* lambda_out, double* discarded_out, int* dev_status, char* scratch,
+            size_t scratch_bytes, cudaStream_t st) {
   if (n <= 0 || R <= 0 || R > n || n > 1024) { set_error("eig: need 1 <= R <= n <= 1024"); return ATK_EUNSUPPORTED; }
-  int s = arith == ATK_EIG_ROT_FP64
-              ? eig_top_t<double>(S, n, R, max_sweeps, U64_out, lambda_out, discarded_out, dev_status, scratch,
-                                  scratch_bytes, st)
-              : eig_top_t<float>(S, n, R, max_sweeps, U64_out, lambda_out, discarded_out, dev_status, scratch,
-                                 scratch_bytes, st);
-  if (s != ATK_OK) return s;
+  const int m = rr_width(n, R);
+  const bool rr = arith == ATK_EIG_ROT_FP32 && m >= R + 8 &&
+                  ((method == ATK_EIG_AUTO && 2 * m <= n) || (method == ATK_EIG_SUBSPACE && m < n));
   Arena ar{scratch, scratch_bytes, 0};
-  double* Z = (double*)ar.take(sizeof(double) * n * R);
-  double* pol = (double*)ar.take(smallla_scratch_bytes(n, R));
-  if (!Z || !pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
-  if (arith != ATK_EIG_ROT_FP64) {
-    // Float rotations have a backward error of a few hundred eps_32 ||S||, so
-    // the selected vectors carry out-of-subspace components at that level.
-    // One float64 subspace-iteration step, Z = S U with columns renormalised,
-    // shrinks them by lambda_{R+1} / lambda_R.  The vectors stay in eigenvalue
-    // order because S U ~ U diag(lambda) with lambda > 0.
-    ATK_TRY(gemm_f64(S, U64_out, n, n, R, Z, st));
-    double* dmax = pol;
-    max_abs_diag_kernel<<<1, 256, 0, st>>>(S, n, dmax);
-    ATK_LAUNCHED();
-    normalize_cols_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(Z, U64_out, n, R, dmax, 1e-7, U64_out);
-    ATK_LAUNCHED();
+  const int64_t kmax = rr ? m : R;
+  double* Qb = (double*)ar.take(sizeof(double) * n * kmax);
+  if (!Qb) { set_error("eig: scratch too small"); return ATK_EINVAL; }
+  char* rest = scratch + ar.used;
+  const size_t rest_bytes = scratch_bytes - ar.used;
+  int s = ATK_ENOCONV;
+  int64_t k = R;
+  if (rr) {
+    s = rr_top(S, n, R, max_sweeps, Qb, dev_status, rest, rest_bytes, st);
+    if (s != ATK_OK && s != ATK_ENOCONV) return s;
+    if (s == ATK_OK) {
+      k = m;
+      if (lambda_out && n > R) {
+        // Only the kept eigenvalues exist on this path; the tail is marked NaN.
+        ATK_CUDA(cudaMemsetAsync(lambda_out + R, 0xFF, sizeof(double) * (n - R), st));
+      }
+    }
   }
-  // Accumulated rotations (and the refinement) leave U orthonormal only to
-  // working precision; two float64 Newton-Schulz polar steps restore it
-  // without reordering the columns.
-  ATK_TRY(polar_step_f64(U64_out, n, R, pol, st));
-  ATK_TRY(polar_step_f64(U64_out, n, R, pol, st));
-  sign_fix_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(U64_out, n, R);
-  ATK_LAUNCHED();
-  // The kept eigenvalues become float64 Rayleigh quotients of the polished
-  // vectors (error ~ ||S|| * subspace error^2), and the discarded energy is
-  // trace(S) minus their sum, so neither inherits the rounding of the
-  // rotations.  The tail of lambda_out keeps the rotated diagonal.
-  ATK_TRY(rayleigh_f64(S, U64_out, n, R, Z, lambda_out, discarded_out, st));
+  if (s != ATK_OK) {
+    // Full Jacobi: the R leading vectors (and all eigenvalues) of the whole Gram.
+    s = arith == ATK_EIG_ROT_FP64
+            ? eig_top_t<double>(S, n, R, max_sweeps, Qb, lambda_out, nullptr, dev_status, rest, rest_bytes, st)
+            : eig_top_t<float>(S, n, R, max_sweeps, Qb, lambda_out, nullptr, dev_status, rest, rest_bytes, st);
+    if (s != ATK_OK) return s;
+    k = R;
+  }
+  ATK_TRY(refine_f64(S, n, Qb, k, R, U64_out, lambda_out, discarded_out, rest, rest_bytes, st));
   if (U_out) ATK_TRY(f64_to_f32(U64_out, U_out, n * R, st));
   return ATK_OK;
 }

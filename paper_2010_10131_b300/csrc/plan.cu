@@ -118,7 +118,7 @@ struct atucker_plan_s {
   int precision = ATK_FP32, als_sweeps = 5;
   uint64_t seed = 0;
   cudaStream_t st = nullptr;
-  int eig_arith = ATK_EIG_ROT_FP32, sync = 0, max_sweeps = 40;
+  int eig_arith = ATK_EIG_ROT_FP32, eig_method = ATK_EIG_AUTO, sync = 0, max_sweeps = 40;
   // device workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -308,6 +308,10 @@ int atucker_plan_set_option(atucker_plan_t p, int key, int64_t value) {
     case ATK_OPT_SYNC:
       p->sync = value ? 1 : 0;
       return ATK_OK;
+    case ATK_OPT_EIG_METHOD:
+      if (value < ATK_EIG_AUTO || value > ATK_EIG_SUBSPACE) break;
+      p->eig_method = (int)value;
+      return ATK_OK;
     case ATK_OPT_TIMING:
       p->timing = value ? 1 : 0;
       p->recs.clear();
@@ -378,8 +382,8 @@ int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* fa
         p->gram_launches++;
       }
       ATK_TRY(mark(PH_GRAM_REDUCE));
-      ATK_TRY(eig_top(p->S, v.n, R, p->eig_arith, p->max_sweeps, U32, p->U64, nullptr, disc, p->dev_status,
-                      p->scratch, p->scratch_bytes, st));
+      ATK_TRY(eig_top(p->S, v.n, R, p->eig_arith, p->eig_method, p->max_sweeps, U32, p->U64, nullptr, disc,
+                      p->dev_status, p->scratch, p->scratch_bytes, st));
       ATK_TRY(mark(PH_EIG));
       ATK_TRY(ttm_f32(Y, v, U32, R, out, st));
       ATK_TRY(mark(PH_TTM));
@@ -523,10 +527,13 @@ int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* 
   return ttm_f32(y, v, U, R, out, (cudaStream_t)stream);
 }
 
-int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, float* U_out, double* lambda_out,
-                double* discarded_out, void* stream) {
+int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, int eig_method, float* U_out,
+                double* lambda_out, double* discarded_out, void* stream) {
   if (!S || !U_out) { set_error("null argument"); return ATK_EINVAL; }
-  if (n < 1 || R < 1 || R > n || n > 1024) { set_error("need 1 <= R <= n <= 1024"); return ATK_EUNSUPPORTED; }
+  if (n < 1 || R < 1 || R > n || n > 1024 || R > 128) {
+    set_error("need 1 <= R <= n <= 1024 and R <= 128");
+    return ATK_EUNSUPPORTED;
+  }
   if (eig_arith != ATK_EIG_ROT_FP32 && eig_arith != ATK_EIG_ROT_FP64) { set_error("bad eig_arith"); return ATK_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
   StreamScratch sc(st);
@@ -538,7 +545,9 @@ int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, float* U_o
   double* U64 = (double*)ar.take((size_t)n * R * 8);
   char* scratch = (char*)ar.take(sb);
   ATK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-  ATK_TRY(eig_top(S, n, R, eig_arith, 40, U_out, U64, lambda_out, discarded_out, status, scratch, sb, st));
+  if (eig_method < ATK_EIG_AUTO || eig_method > ATK_EIG_SUBSPACE) { set_error("bad eig_method"); return ATK_EINVAL; }
+  ATK_TRY(eig_top(S, n, R, eig_arith, eig_method, 40, U_out, U64, lambda_out, discarded_out, status, scratch, sb,
+                  st));
   return read_status(status, st);
 }
 
