@@ -183,6 +183,27 @@ const char* atucker_version(void);
 int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precision, double* S_out,
                  void* stream);
 
+/* Gram matrix as atucker_gram, without allocating any device memory.  The
+ * paper has no counterpart: this entry point serves callers that cannot
+ * allocate GPU memory at call time.  Examples: a service that reserved its
+ * whole memory budget up front, a process whose free device memory is already
+ * held by a framework's caching allocator, or a hook that must not re-enter
+ * the CUDA allocator.
+ *   - The split-K partial tiles live in one fixed 16 MiB device array inside
+ *     the library (float32).  Every GPU that loads the library holds it until
+ *     the process exits.
+ *   - Limit: n <= 2048 (one split's partial tiles must fit); larger n returns
+ *     ATK_EUNSUPPORTED.  Larger J runs in fewer, longer splits than
+ *     atucker_gram when the array is the bound.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other streams,
+ *     other threads) race and corrupt each other's results.  Nothing in the
+ *     array needs to start at zero; each call writes every tile it reads.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+int atucker_gram_noalloc(const float* y, int64_t lo, int64_t n, int64_t hi, double* S_out, void* stream);
+
 /* Truncating TTM Y' = Y x_n U^T (Eq. 2 with the matrix U^T; Alg. 2, EIG branch).
  * U: n x R float32 column-major.  out: lo x R x hi float32 column-major. */
 int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* U, int64_t R, int precision,

@@ -54,6 +54,7 @@ _SIGS = {
     "atucker_last_error": (ctypes.c_char_p, []),
     "atucker_version": (ctypes.c_char_p, []),
     "atucker_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
+    "atucker_gram_noalloc": (_i32, [_vp, _i64, _i64, _i64, _vp, _vp]),
     "atucker_ttm": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _i32, _vp, _vp]),
     "atucker_eig": (_i32, [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _vp, _vp]),
     "atucker_als_mode": (_i32, [_vp, _i64, _i64, _i64, _i64, _vp, _u64, _i32, _i32, _i32, _vp, _vp, _vp]),

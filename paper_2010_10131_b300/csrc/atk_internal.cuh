@@ -120,6 +120,9 @@ size_t gram_scratch_bytes(const View& v);
 // `mid` (nullable) is recorded between the partial-tile kernel and the reduction.
 int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st,
              cudaEvent_t mid = nullptr);
+// As gram_f32, with the number of split-K partials capped to fit scratch_bytes.
+int gram_f32_fixed_scratch(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes,
+                           cudaStream_t st);
 int ttm_f32(const float* y, const View& v, const float* U, int64_t R, float* out, cudaStream_t st);
 // C (n x R, float64) = sum_c Y(c, i) P(c, r); P is a (lo, R, hi) tensor.
 size_t cross_scratch_bytes(const View& v, int64_t R);

@@ -448,6 +448,41 @@ int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t sc
   return ATK_OK;
 }
 
+// Same kernels as gram_f32, with the split count capped so that the partial
+// tiles fit in `scratch_bytes` (callers whose scratch is a fixed block).
+// Fewer splits mean longer float32 chains per partial sum; the float64
+// reduction across splits is unchanged.
+int gram_f32_fixed_scratch(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes,
+                           cudaStream_t st) {
+  if (v.n <= 0) return ATK_OK;
+  if (v.J() == 0) {
+    ATK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * v.n * v.n, st));
+    return ATK_OK;
+  }
+  const int bm = gram_bm(v.n);
+  const int T = (int)ceil_div(v.n, bm);
+  const int nt = T * (T + 1) / 2;
+  const size_t per_split = (size_t)nt * bm * bm * sizeof(float);
+  const int64_t fit = (int64_t)(scratch_bytes / per_split);
+  if (fit < 1) {
+    set_error("gram: the partial tiles of one split do not fit in the fixed scratch");
+    return ATK_EUNSUPPORTED;
+  }
+  SplitPlan sp = choose_split(v.J(), nt);
+  if (sp.nsplit > fit) {
+    sp.kc = ceil_div(ceil_div(v.J(), fit), TK) * TK;
+    sp.nsplit = (int)ceil_div(v.J(), sp.kc);
+  }
+  dim3 grid(nt, sp.nsplit);
+  if (bm == 128) gram_ci_kernel<128, 8><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
+  else if (bm == 64) gram_ci_kernel<64, 4><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
+  else gram_ci_kernel<32, 2><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
+  ATK_LAUNCHED();
+  reduce_sym_kernel<<<(unsigned)ceil_div(v.n * v.n, 256), 256, 0, st>>>(scratch, sp.nsplit, nt, T, bm, v.n, S);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+
 size_t cross_scratch_bytes(const View& v, int64_t R) {
   int bn = cross_bn(R);
   int TI = (int)ceil_div(v.n, 128), TR = (int)ceil_div(R, bn);
