@@ -176,7 +176,7 @@ __device__ int jacobi_smem(JWork<T> w, int m, T fro, int max_sweeps, bool* conve
 // One matrix per CTA (blockIdx.x), padded to m = n rounded up to even.
 // Writes diag (n) and V (n x n, row-major, column j = eigenvector j) to global.
 template <typename T>
-__global__ void __launch_bounds__(256) jacobi_small_kernel(const double* __restrict__ S, int n, int m, int max_sweeps,
+__global__ void __launch_bounds__(1024) jacobi_small_kernel(const double* __restrict__ S, int n, int m, int max_sweeps,
                                                            T* __restrict__ diag_out, T* __restrict__ V_out,
                                                            int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(const double* __restr
   int* pq = reinterpret_cast<int*>(cs + m);
   int* flag = pq + m;
   unsigned short* blk = reinterpret_cast<unsigned short*>(flag + 2);
-  __shared__ double red[256];
+  __shared__ double red[1024];
   const double* Sm = S + (size_t)blockIdx.x * n * n;
   double loc = 0.0;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(const double* __restr
   }
   red[threadIdx.x] = loc;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
@@ -527,24 +527,30 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
 
 // ------------------------------------------------- Rayleigh-Ritz subspace path
 // Only the R leading eigenvectors are needed (Alg. 2: "R_n leading
-// eigenvectors of S").  For m = R + p well below n, block subspace iteration
-// (float32 products of S with an n x m block, shifted CholeskyQR3)
-// followed by a Rayleigh-Ritz projection B = Q^T S Q reduces the eigenproblem
-// to m x m.  The projection is then diagonalised by the same one-CTA
-// parallel-order Jacobi as above.  The iteration restarts from the Ritz vectors
-// until the predicted error after the float64 refinement,
-//   (theta_m / theta_R) * max_{j<R} ||S q_j - theta_j q_j|| / (theta_R - theta_m),
-// drops below RR_TARGET.  That is a Davis-Kahan bound on the angle between
-// q_R and the leading space, times the contraction of the refinement's
-// subspace step.  When theta_m / theta_R > RR_SLOW_RATIO (the R-th eigenvalue
-// sits in a cluster, so subspace iteration would crawl) or RR_MAXIT
-// iterations pass, the full Jacobi runs instead.
-constexpr int RR_MAXIT = 20;
+// eigenvectors of S").  For m = R + p well below n, this path works on an
+// n x m block:
+//  1. two power steps, Q <- orth(S Q), orthonormalised by shifted
+//     CholeskyQR3;
+//  2. a Rayleigh-Ritz projection B = Q^T S Q diagonalised by the same
+//     one-CTA parallel-order Jacobi as above, giving Ritz vectors Q W;
+//  3. further steps restarting from the Ritz vectors (S Q W = Z W is
+//     already at hand, two CholeskyQR passes suffice) until the predicted
+//     error after the float64 refinement,
+//       (theta_m / theta_R) * max_{j<R} ||S q_j - theta_j q_j|| / (theta_R - theta_m),
+//     drops below RR_TARGET.  That is a Davis-Kahan bound on the angle
+//     between q_R and the leading space, times the contraction of the
+//     refinement's subspace step.
+// When theta_m / theta_R > RR_SLOW_RATIO (the R-th eigenvalue sits in a
+// cluster, so subspace iteration would crawl) or RR_MAXIT projections pass,
+// the full Jacobi runs instead.  Every product runs on the contraction engine
+// of fp32_ops.cu: the n x m block is the mode-2 view (lo = n, I = m, hi = 1)
+// of an n x m column-major matrix.
+constexpr int RR_MAXIT = 16;
 constexpr double RR_TARGET = 1e-6;
 constexpr double RR_SLOW_RATIO = 0.5;
 
 int rr_width(int64_t n, int64_t R) {
-  int64_t p = std::max<int64_t>(8, std::min<int64_t>(R, 32));
+  int64_t p = std::max<int64_t>(8, std::min<int64_t>(16, R / 2));
   return (int)std::min<int64_t>(std::min<int64_t>(n, R + p), 156);
 }
 
@@ -556,55 +562,6 @@ __global__ void rand_fill_kernel(float* __restrict__ Q, int64_t count, uint64_t 
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   z ^= z >> 31;
   Q[i] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
-}
-
-// C (M x N) = A (M x K) * op(B), op(B) = B (K x N) or B^T with B N x K.  float32,
-// column-major, one thread per output, four partial sums.
-__global__ void gemm_f32_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t M, int64_t K,
-                                int64_t N, int transB, float* __restrict__ C) {
-  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= M * N) return;
-  int64_t i = o % M, j = o / M;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  int64_t t = 0;
-  if (!transB) {
-    for (; t + 3 < K; t += 4) {
-      s0 = fmaf(A[i + M * t], B[t + K * j], s0);
-      s1 = fmaf(A[i + M * (t + 1)], B[t + 1 + K * j], s1);
-      s2 = fmaf(A[i + M * (t + 2)], B[t + 2 + K * j], s2);
-      s3 = fmaf(A[i + M * (t + 3)], B[t + 3 + K * j], s3);
-    }
-    for (; t < K; ++t) s0 = fmaf(A[i + M * t], B[t + K * j], s0);
-  } else {
-    for (; t + 3 < K; t += 4) {
-      s0 = fmaf(A[i + M * t], B[j + N * t], s0);
-      s1 = fmaf(A[i + M * (t + 1)], B[j + N * (t + 1)], s1);
-      s2 = fmaf(A[i + M * (t + 2)], B[j + N * (t + 2)], s2);
-      s3 = fmaf(A[i + M * (t + 3)], B[j + N * (t + 3)], s3);
-    }
-    for (; t < K; ++t) s0 = fmaf(A[i + M * t], B[j + N * t], s0);
-  }
-  C[o] = (s0 + s1) + (s2 + s3);
-}
-
-// C (M x N, float64) = A^T B with A K x M and B K x N float32 (partial sums in float32).
-__global__ void gemm_f32_tn_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t K, int64_t M,
-                                   int64_t N, double* __restrict__ C) {
-  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= M * N) return;
-  int64_t i = o % M, j = o / M;
-  const float* a = A + K * i;
-  const float* b = B + K * j;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  int64_t t = 0;
-  for (; t + 3 < K; t += 4) {
-    s0 = fmaf(a[t], b[t], s0);
-    s1 = fmaf(a[t + 1], b[t + 1], s1);
-    s2 = fmaf(a[t + 2], b[t + 2], s2);
-    s3 = fmaf(a[t + 3], b[t + 3], s3);
-  }
-  for (; t < K; ++t) s0 = fmaf(a[t], b[t], s0);
-  C[o] = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
 }
 
 // Normalise each column of Y (n x m) to unit length; one warp per column.
@@ -620,85 +577,90 @@ __global__ void colnorm_f32_kernel(float* __restrict__ Y, int64_t n, int64_t m) 
   for (int64_t i = lane; i < n; i += 32) y[i] *= inv;
 }
 
-// One CTA: Cholesky of G + shift * max(diag G) * I (G m x m SPD, float64 in,
-// float32 work) and the inverse of its lower factor, Linv (m x m column-major
-// float32).  A pivot at or below a tiny floor (rank-deficient block) is raised
-// to the floor, so the factor stays finite.
-__global__ void __launch_bounds__(256) chol_inv_f32_kernel(const double* __restrict__ G, int m, float shift,
-                                                           float* __restrict__ Linv) {
+// One CTA: Cholesky L L^T = G + shift * max(diag G) * I (G m x m SPD, float64
+// in, float32 work in shared memory), then LinvT = (L^{-1})^T (m x m
+// column-major float32), so that Q = Y LinvT.  A pivot at or below a tiny
+// floor (rank-deficient block) is raised to the floor, so the factor stays
+// finite.  Two barriers per column for the factorisation, one per row for the
+// inverse.
+__global__ void __launch_bounds__(512) chol_invT_f32_kernel(const double* __restrict__ G, int m, float shift,
+                                                            float* __restrict__ LinvT) {
   extern __shared__ float sm[];
-  float* L = sm;  // m x m, column-major
-  float* Li = sm + m * m;
-  __shared__ float dscale;
+  float* L = sm;          // m x m column-major; lower triangle used
+  float* Li = sm + m * m;  // L^{-1}, column-major, lower
+  __shared__ float dmax, dinv;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) L[idx] = (float)G[idx];
   __syncthreads();
   if (threadIdx.x == 0) {
     float d = 0.f;
     for (int j = 0; j < m; ++j) d = fmaxf(d, L[j + m * j]);
     for (int j = 0; j < m; ++j) L[j + m * j] += shift * d;
+    dmax = d;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float d = 0.f;
-    for (int j = 0; j < m; ++j) d = fmaxf(d, L[j + m * j]);
-    dscale = d;
-  }
-  __syncthreads();
+  const float floor_v = 1e-12f * dmax + 1e-30f;
   for (int j = 0; j < m; ++j) {
+    // pivot j is final here; scale column j and publish 1/l_jj
     if (threadIdx.x == 0) {
       float d = L[j + m * j];
-      float floor_v = 1e-12f * dscale + 1e-30f;
-      L[j + m * j] = sqrtf(d > floor_v ? d : floor_v);
+      float ljj = sqrtf(d > floor_v ? d : floor_v);
+      L[j + m * j] = ljj;
+      dinv = 1.f / ljj;
     }
     __syncthreads();
-    float ljj = L[j + m * j];
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i + m * j] /= ljj;
-    __syncthreads();
-    int rem = m - j - 1;
+    const float inv = dinv;
+    const int rem = m - j - 1;
+    // trailing update with the unscaled column, then the scaled column j
     for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
       int i = j + 1 + idx % rem, k = j + 1 + idx / rem;
-      if (i >= k) L[i + m * k] = fmaf(-L[i + m * j], L[k + m * j], L[i + m * k]);
+      if (i >= k) L[i + m * k] = fmaf(-(L[i + m * j] * inv), L[k + m * j] * inv, L[i + m * k]);
     }
     __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i + m * j] *= inv;
   }
-  // Columns of Linv by forward substitution, one thread per column.
-  for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    for (int i = 0; i < m; ++i) {
-      if (i < k) { Li[i + m * k] = 0.f; continue; }
-      float acc = (i == k) ? 1.f : 0.f;
+  __syncthreads();
+  // L^{-1} row by row: Li[i][k] = -(sum_{k<=t<i} L[i][t] Li[t][k]) / L[i][i], Li[i][i] = 1 / L[i][i].
+  for (int i = 0; i < m; ++i) {
+    for (int k = threadIdx.x; k <= i; k += blockDim.x) {
+      float acc = (k == i) ? 1.f : 0.f;
       for (int t = k; t < i; ++t) acc = fmaf(-L[i + m * t], Li[t + m * k], acc);
       Li[i + m * k] = acc / L[i + m * i];
     }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Linv[idx] = Li[idx];
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    int r = idx % m, c = idx / m;
+    LinvT[idx] = (r <= c) ? Li[c + m * r] : 0.f;  // LinvT[r][c] = Li[c][r]
+  }
 }
 
-// res[0] = max_{j<R} ||Z[:, j] - theta_j Q[:, j]|| / theta_0.  One CTA.
-__global__ void __launch_bounds__(256) ritz_residual_kernel(const float* __restrict__ Z, const float* __restrict__ Q,
-                                                            const double* __restrict__ theta, int64_t n, int64_t R,
-                                                            double* __restrict__ res) {
-  __shared__ double red[256];
-  __shared__ double worst;
-  if (threadIdx.x == 0) worst = 0.0;
-  __syncthreads();
-  for (int64_t j = 0; j < R; ++j) {
-    double s = 0.0;
-    const double th = theta[j];
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      double d = (double)Z[i + n * j] - th * Q[i + n * j];
-      s += d * d;
-    }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int k = 128; k > 0; k >>= 1) {
-      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) worst = fmax(worst, sqrt(red[0]));
-    __syncthreads();
+// res[j] = ||Z[:, j] - theta_j Q[:, j]|| for j < R; one warp per column.
+__global__ void ritz_residual_kernel(const float* __restrict__ Z, const float* __restrict__ Q,
+                                     const double* __restrict__ theta, int64_t n, int64_t R,
+                                     double* __restrict__ res) {
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (j >= R) return;
+  const double th = theta[j];
+  double s = 0.0;
+  for (int64_t i = lane; i < n; i += 32) {
+    double d = (double)Z[i + n * j] - th * Q[i + n * j];
+    s += d * d;
   }
-  if (threadIdx.x == 0) res[0] = worst / fmax(fabs(theta[0]), 1e-300);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) res[j] = sqrt(s);
+}
+
+// out[0] = max_j res[j], out[1] = theta[0], out[2] = theta[R-1], out[3] = theta[m-1].
+__global__ void ritz_summary_kernel(const double* __restrict__ res, const double* __restrict__ theta, int R, int m,
+                                    double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double w = 0.0;
+  for (int j = 0; j < R; ++j) w = fmax(w, res[j]);
+  out[0] = w;
+  out[1] = theta[0];
+  out[2] = theta[R - 1];
+  out[3] = theta[m - 1];
 }
 
 __global__ void f32_to_f64_kernel2(const float* __restrict__ s, double* __restrict__ d, int64_t count) {
@@ -708,26 +670,32 @@ __global__ void f32_to_f64_kernel2(const float* __restrict__ s, double* __restri
 
 namespace {
 struct RRBufs {
-  float *Sf, *Q, *Y, *Z, *Wf, *Linv, *Vb, *diag;
-  double *G, *W64, *theta, *res;
+  float *Sf, *Q, *Y, *Z, *T, *LinvT, *Vb, *diag, *Wf;
+  double *G, *W64, *theta, *res, *summary;
+  float* part;  // split-K partials of the m x m products
+  size_t part_bytes;
 };
+size_t rr_part_bytes(int64_t n, int m) {
+  View v{n, m, 1};
+  return std::max(gram_scratch_bytes(v), cross_scratch_bytes(v, m));
+}
 size_t rr_bytes(int64_t n, int m) {
   size_t nm = (size_t)n * m, mm = (size_t)m * m;
-  return sizeof(float) * ((size_t)n * n + 4 * nm + 2 * mm + m) + sizeof(double) * (2 * mm + m + 8) + 16 * 256;
+  return sizeof(float) * ((size_t)n * n + 4 * nm + 3 * mm + m) + sizeof(double) * (2 * mm + 2 * m + 8) +
+         rr_part_bytes(n, m) + 16 * 256;
 }
 // One CholeskyQR pass: Q = Y chol(Y^T Y + shift I)^{-T} after normalising the
 // columns of Y (in place).
 int cholqr_pass_f32(float* Y, float* Q, int64_t n, int m, float shift, RRBufs& b, cudaStream_t st) {
+  const View v{n, m, 1};
   colnorm_f32_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Y, n, m);
   ATK_LAUNCHED();
-  gemm_f32_tn_kernel<<<(unsigned)ceil_div((int64_t)m * m, 256), 256, 0, st>>>(Y, Y, n, m, m, b.G);
-  ATK_LAUNCHED();
+  ATK_TRY(gram_f32(Y, v, b.G, b.part, b.part_bytes, st));
   size_t sm = (size_t)2 * m * m * sizeof(float);
-  ATK_CUDA(cudaFuncSetAttribute(chol_inv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  chol_inv_f32_kernel<<<1, 256, sm, st>>>(b.G, m, shift, b.Linv);
+  ATK_CUDA(cudaFuncSetAttribute(chol_invT_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  chol_invT_f32_kernel<<<1, 512, sm, st>>>(b.G, m, shift, b.LinvT);
   ATK_LAUNCHED();
-  gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(Y, b.Linv, n, m, m, 1, Q);
-  ATK_LAUNCHED();
+  ATK_TRY(ttm_f32(Y, v, b.LinvT, m, Q, st));
   return ATK_OK;
 }
 // Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Zhang, Yamamoto, SISC 2020):
@@ -745,7 +713,7 @@ int cholqr3_f32(float* Y, float* T, float* Q, int64_t n, int m, RRBufs& b, cudaS
 // Leading Ritz block of S by subspace iteration + Rayleigh-Ritz + Jacobi.
 // On success writes Qblk (n x m float64, m = rr_width(n, R), Ritz vectors in
 // descending Ritz-value order, orthonormal to float32 accuracy) and returns
-// ATK_OK; returns ATK_ENOCONV if the residual test never passed.
+// ATK_OK; returns ATK_ENOCONV to request the full Jacobi.
 int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, int* dev_status, char* scratch,
            size_t scratch_bytes, cudaStream_t st) {
   const int m = rr_width(n, R);
@@ -756,61 +724,63 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   b.Q = (float*)ar.take(sizeof(float) * nm);
   b.Y = (float*)ar.take(sizeof(float) * nm);
   b.Z = (float*)ar.take(sizeof(float) * nm);
-  b.Wf = (float*)ar.take(sizeof(float) * nm);
-  b.Linv = (float*)ar.take(sizeof(float) * mm);
+  b.T = (float*)ar.take(sizeof(float) * nm);
+  b.LinvT = (float*)ar.take(sizeof(float) * mm);
   b.Vb = (float*)ar.take(sizeof(float) * mm);
+  b.Wf = (float*)ar.take(sizeof(float) * mm);
   b.diag = (float*)ar.take(sizeof(float) * m);
   b.G = (double*)ar.take(sizeof(double) * mm);
   b.W64 = (double*)ar.take(sizeof(double) * mm);
   b.theta = (double*)ar.take(sizeof(double) * m);
-  b.res = (double*)ar.take(sizeof(double) * 8);
-  if (!b.res) { set_error("rr: scratch too small"); return ATK_EINVAL; }
+  b.res = (double*)ar.take(sizeof(double) * m);
+  b.summary = (double*)ar.take(sizeof(double) * 8);
+  b.part_bytes = rr_part_bytes(n, m);
+  b.part = (float*)ar.take(b.part_bytes);
+  if (!b.part) { set_error("rr: scratch too small"); return ATK_EINVAL; }
+  const View sv{n, n, 1}, qv{n, m, 1};
   ATK_TRY(f64_to_f32(S, b.Sf, n * n, st));
-  rand_fill_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, st>>>(b.Y, (int64_t)nm, 0x5EEDULL + (uint64_t)n);
+  rand_fill_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, st>>>(b.Q, (int64_t)nm, 0x5EEDULL + (uint64_t)n);
   ATK_LAUNCHED();
-  ATK_TRY(cholqr3_f32(b.Y, b.Z, b.Q, n, m, b, st));
+  // Two power steps from the random block.
+  for (int s = 0; s < 2; ++s) {
+    ATK_TRY(ttm_f32(b.Sf, sv, b.Q, m, b.Y, st));  // Y = S Q
+    ATK_TRY(cholqr3_f32(b.Y, b.T, b.Q, n, m, b, st));
+  }
   const int mp = m + (m & 1);
   const size_t jsm = small_smem<float>(mp);
   ATK_CUDA(cudaFuncSetAttribute(jacobi_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
   for (int it = 0; it < RR_MAXIT; ++it) {
-    // Subspace step: Q <- orth(S Q).
-    gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Sf, b.Q, n, n, m, 0, b.Y);
-    ATK_LAUNCHED();
-    ATK_TRY(cholqr3_f32(b.Y, b.Z, b.Q, n, m, b, st));
-    if (it < 2) continue;  // a few plain steps before the first projection
-    // Rayleigh-Ritz: Z = S Q, B = Q^T Z, B = W diag(theta) W^T.
-    gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Sf, b.Q, n, n, m, 0, b.Z);
-    ATK_LAUNCHED();
-    gemm_f32_tn_kernel<<<(unsigned)ceil_div((int64_t)mm, 256), 256, 0, st>>>(b.Q, b.Z, n, m, m, b.G);
-    ATK_LAUNCHED();
-    jacobi_small_kernel<float><<<1, 256, jsm, st>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
+    // Rayleigh-Ritz: Z = S Q, B = Q^T Z = W diag(theta) W^T.
+    ATK_TRY(ttm_f32(b.Sf, sv, b.Q, m, b.Z, st));
+    ATK_TRY(cross_f32(b.Q, qv, b.Z, m, b.G, b.part, b.part_bytes, st));
+    jacobi_small_kernel<float><<<1, 1024, jsm, st>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
     ATK_LAUNCHED();
     select_kernel<float><<<1, 1024, 0, st>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
     ATK_LAUNCHED();
-    ATK_TRY(f64_to_f32(b.W64, b.Linv, (int64_t)mm, st));
-    // Ritz vectors Q W (sorted by descending theta) and S Q W = Z W.
-    gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Q, b.Linv, n, m, m, 0, b.Y);
+    ATK_TRY(f64_to_f32(b.W64, b.Wf, (int64_t)mm, st));
+    // Ritz vectors Y = Q W (descending theta) and S Q W = Z W.
+    ATK_TRY(ttm_f32(b.Q, qv, b.Wf, m, b.Y, st));
+    ATK_TRY(ttm_f32(b.Z, qv, b.Wf, m, b.T, st));
+    ritz_residual_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(b.T, b.Y, b.theta, n, R, b.res);
     ATK_LAUNCHED();
-    gemm_f32_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Z, b.Linv, n, m, m, 0, b.Wf);
+    ritz_summary_kernel<<<1, 32, 0, st>>>(b.res, b.theta, (int)R, m, b.summary);
     ATK_LAUNCHED();
-    ritz_residual_kernel<<<1, 256, 0, st>>>(b.Wf, b.Y, b.theta, n, R, b.res);
-    ATK_LAUNCHED();
-    std::swap(b.Q, b.Y);
-    double hres[4] = {0.0, 0.0, 0.0, 0.0};
-    ATK_CUDA(cudaMemcpyAsync(hres, b.res, sizeof(double), cudaMemcpyDeviceToHost, st));
-    ATK_CUDA(cudaMemcpyAsync(hres + 1, b.theta, sizeof(double), cudaMemcpyDeviceToHost, st));
-    ATK_CUDA(cudaMemcpyAsync(hres + 2, b.theta + (R - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
-    ATK_CUDA(cudaMemcpyAsync(hres + 3, b.theta + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+    double h[4] = {0.0, 0.0, 0.0, 0.0};
+    ATK_CUDA(cudaMemcpyAsync(h, b.summary, sizeof(h), cudaMemcpyDeviceToHost, st));
     ATK_CUDA(cudaStreamSynchronize(st));
-    const double res = hres[0] * hres[1], thR = hres[2], thm = fmax(hres[3], 0.0);
+    const double res = h[0], thR = h[2], thm = fmax(h[3], 0.0);
     if (!(res == res) || !(thR == thR) || res > 1e300) return ATK_ENOCONV;  // non-finite: full Jacobi
     if (!(thR > 0.0) || thm > RR_SLOW_RATIO * thR) return ATK_ENOCONV;     // clustered: full Jacobi
     const double predicted = (thm / thR) * res / (thR - thm);
     if (predicted <= RR_TARGET) {
-      f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Q, Qblk, n * (int64_t)m);
+      f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Y, Qblk, n * (int64_t)m);
       ATK_LAUNCHED();
       return ATK_OK;
     }
+    // Next step from the Ritz vectors: S (Q W) = Z W is in T; its columns are
+    // nearly orthogonal, so two plain CholeskyQR passes orthonormalise it.
+    ATK_TRY(cholqr_pass_f32(b.T, b.Y, n, m, 0.f, b, st));
+    ATK_TRY(cholqr_pass_f32(b.Y, b.Q, n, m, 0.f, b, st));
   }
   return ATK_ENOCONV;
 }
