@@ -57,13 +57,16 @@ __device__ __forceinline__ void rr_pair(int r, int k, int m, int& p, int& q) {
   }
 }
 
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+
 template <typename T>
 __device__ __forceinline__ void rot_params(T app, T aqq, T apq, T thr_abs, T& c, T& s, bool& rot) {
   T thr = JTol<T>::rel * sqrt(fabs(app * aqq));
   if (fabs(apq) > thr && fabs(apq) > thr_abs) {
     T tau = (aqq - app) / (T(2) * apq);
     T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-    c = T(1) / sqrt(T(1) + t * t);
+    c = rsq(T(1) + t * t);
     s = t * c;
     rot = true;
   } else {
@@ -76,12 +79,13 @@ __device__ __forceinline__ void rot_params(T app, T aqq, T apq, T thr_abs, T& c,
 // Shared-memory working set of one scalar Jacobi solve on an m x m matrix.
 template <typename T>
 struct JWork {
-  T* A;   // m x m, row-major, leading dimension m
-  T* V;   // m x m
+  T* A;   // m x m, row-major, leading dimension ld
+  T* V;   // m x m, leading dimension ld
   T* cs;  // 2 * (m/2): c then s per pair
   int* pq;  // 2 * (m/2): p then q per pair
   int* flag;  // [0]: any rotation this sweep, [1]: any rotation at all
   unsigned short* blk;  // 2 * nblk: (k, l) of the k <= l pair blocks, filled once per solve
+  int ld;               // leading dimension of A and V (m, or m + 1 to spread banks)
 };
 __host__ __device__ inline int nblocks_of(int m) { return (m / 2) * (m / 2 + 1) / 2; }
 
@@ -91,6 +95,7 @@ __host__ __device__ inline int nblocks_of(int m) { return (m / 2) * (m / 2 + 1) 
 template <typename T>
 __device__ int jacobi_smem(JWork<T> w, int m, T fro, int max_sweeps, bool* converged) {
   const int half = m / 2;
+  const int ld = w.ld;
   const T thr_abs = JTol<T>::abs * fro;
   int sweep = 0;
   bool conv = false;
@@ -112,7 +117,7 @@ __device__ int jacobi_smem(JWork<T> w, int m, T fro, int max_sweeps, bool* conve
         rr_pair(r, k, m, p, q);
         T c, s;
         bool rot;
-        rot_params<T>(w.A[p * m + p], w.A[q * m + q], w.A[p * m + q], thr_abs, c, s, rot);
+        rot_params<T>(w.A[p * ld + p], w.A[q * ld + q], w.A[p * ld + q], thr_abs, c, s, rot);
         w.pq[k] = p;
         w.pq[half + k] = q;
         w.cs[k] = c;
@@ -126,35 +131,68 @@ __device__ int jacobi_smem(JWork<T> w, int m, T fro, int max_sweeps, bool* conve
         T ck = w.cs[k], sk = w.cs[half + k], cl = w.cs[l], sl = w.cs[half + l];
         if (sk == T(0) && sl == T(0)) continue;
         int pk = w.pq[k], qk = w.pq[half + k], pl = w.pq[l], ql = w.pq[half + l];
-        T x11 = w.A[pk * m + pl], x12 = w.A[pk * m + ql];
-        T x21 = w.A[qk * m + pl], x22 = w.A[qk * m + ql];
+        T x11 = w.A[pk * ld + pl], x12 = w.A[pk * ld + ql];
+        T x21 = w.A[qk * ld + pl], x22 = w.A[qk * ld + ql];
         T y11 = ck * x11 - sk * x21, y12 = ck * x12 - sk * x22;
         T y21 = sk * x11 + ck * x21, y22 = sk * x12 + ck * x22;
         T z11 = cl * y11 - sl * y12, z12 = sl * y11 + cl * y12;
         T z21 = cl * y21 - sl * y22, z22 = sl * y21 + cl * y22;
         if (k == l) {
           if (sk != T(0)) { z12 = T(0); z21 = T(0); }
-          w.A[pk * m + pk] = z11;
-          w.A[qk * m + qk] = z22;
-          w.A[pk * m + qk] = z12;
-          w.A[qk * m + pk] = z12;
+          w.A[pk * ld + pk] = z11;
+          w.A[qk * ld + qk] = z22;
+          w.A[pk * ld + qk] = z12;
+          w.A[qk * ld + pk] = z12;
         } else {
-          w.A[pk * m + pl] = z11; w.A[pl * m + pk] = z11;
-          w.A[pk * m + ql] = z12; w.A[ql * m + pk] = z12;
-          w.A[qk * m + pl] = z21; w.A[pl * m + qk] = z21;
-          w.A[qk * m + ql] = z22; w.A[ql * m + qk] = z22;
+          w.A[pk * ld + pl] = z11; w.A[pl * ld + pk] = z11;
+          w.A[pk * ld + ql] = z12; w.A[ql * ld + pk] = z12;
+          w.A[qk * ld + pl] = z21; w.A[pl * ld + qk] = z21;
+          w.A[qk * ld + ql] = z22; w.A[ql * ld + qk] = z22;
         }
       }
-      // V <- V J
-      for (int idx = threadIdx.x; idx < m * half; idx += blockDim.x) {
-        int i = idx / half, l = idx % half;
-        T sl = w.cs[half + l];
-        if (sl == T(0)) continue;
-        T cl = w.cs[l];
-        int pl = w.pq[l], ql = w.pq[half + l];
-        T vp = w.V[i * m + pl], vq = w.V[i * m + ql];
-        w.V[i * m + pl] = cl * vp - sl * vq;
-        w.V[i * m + ql] = sl * vp + cl * vq;
+      // V <- V J.  Thread t owns pair l = t % half and the rows i = t / half,
+      // t / half + groups, ...; the pair's rotation stays in registers and four
+      // rows are loaded before any is written, so shared-memory latency overlaps.
+      if ((int)blockDim.x < half) {
+        for (int idx = threadIdx.x; idx < m * half; idx += blockDim.x) {
+          int i = idx / half, l = idx % half;
+          T sl = w.cs[half + l];
+          if (sl == T(0)) continue;
+          T cl = w.cs[l];
+          int pl = w.pq[l], ql = w.pq[half + l];
+          T vp = w.V[i * ld + pl], vq = w.V[i * ld + ql];
+          w.V[i * ld + pl] = cl * vp - sl * vq;
+          w.V[i * ld + ql] = sl * vp + cl * vq;
+        }
+      } else {
+        const int groups = (int)blockDim.x / half;
+        const int l = threadIdx.x % half, g = threadIdx.x / half;
+        const T sl = w.cs[half + l];
+        if (g < groups && sl != T(0)) {
+          const T cl = w.cs[l];
+          const int pl = w.pq[l], ql = w.pq[half + l];
+          int i = g;
+          for (; i + 3 * groups < m; i += 4 * groups) {
+            T vp0 = w.V[i * ld + pl], vq0 = w.V[i * ld + ql];
+            T vp1 = w.V[(i + groups) * ld + pl], vq1 = w.V[(i + groups) * ld + ql];
+            T vp2 = w.V[(i + 2 * groups) * ld + pl], vq2 = w.V[(i + 2 * groups) * ld + ql];
+            T vp3 = w.V[(i + 3 * groups) * ld + pl], vq3 = w.V[(i + 3 * groups) * ld + ql];
+            w.V[i * ld + pl] = cl * vp0 - sl * vq0;
+            w.V[i * ld + ql] = sl * vp0 + cl * vq0;
+            w.V[(i + groups) * ld + pl] = cl * vp1 - sl * vq1;
+            w.V[(i + groups) * ld + ql] = sl * vp1 + cl * vq1;
+            w.V[(i + 2 * groups) * ld + pl] = cl * vp2 - sl * vq2;
+            w.V[(i + 2 * groups) * ld + ql] = sl * vp2 + cl * vq2;
+            w.V[(i + 3 * groups) * ld + pl] = cl * vp3 - sl * vq3;
+            w.V[(i + 3 * groups) * ld + ql] = sl * vp3 + cl * vq3;
+          }
+          for (; i < m; i += groups) {
+            T vp = w.V[i * ld + pl], vq = w.V[i * ld + ql];
+            w.V[i * ld + pl] = cl * vp - sl * vq;
+            w.V[i * ld + ql] = sl * vp + cl * vq;
+          }
+        }
+        // threads beyond groups * half (blockDim not a multiple of half) idle here
       }
       __syncthreads();
     }
@@ -180,9 +218,10 @@ __global__ void __launch_bounds__(1024) jacobi_small_kernel(const double* __rest
                                                            T* __restrict__ diag_out, T* __restrict__ V_out,
                                                            int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = m + 1;
   T* A = reinterpret_cast<T*>(smem_raw);
-  T* V = A + m * m;
-  T* cs = V + m * m;
+  T* V = A + m * ld;
+  T* cs = V + m * ld;
   int* pq = reinterpret_cast<int*>(cs + m);
   int* flag = pq + m;
   unsigned short* blk = reinterpret_cast<unsigned short*>(flag + 2);
@@ -192,8 +231,8 @@ __global__ void __launch_bounds__(1024) jacobi_small_kernel(const double* __rest
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
     int i = idx / m, j = idx % m;
     double v = (i < n && j < n) ? Sm[i + (size_t)n * j] : 0.0;
-    A[idx] = (T)v;
-    V[idx] = (i == j) ? T(1) : T(0);
+    A[i * ld + j] = (T)v;
+    V[i * ld + j] = (i == j) ? T(1) : T(0);
     loc += v * v;
   }
   red[threadIdx.x] = loc;
@@ -203,16 +242,16 @@ __global__ void __launch_bounds__(1024) jacobi_small_kernel(const double* __rest
     __syncthreads();
   }
   T fro = (T)sqrt(red[0]);
-  JWork<T> w{A, V, cs, pq, flag, blk};
+  JWork<T> w{A, V, cs, pq, flag, blk, ld};
   bool conv = true;
   if (m >= 2) jacobi_smem<T>(w, m, fro, max_sweeps, &conv);
   if (!conv && threadIdx.x == 0) atomicOr(status, DEV_NOCONV);
   T* dg = diag_out + (size_t)blockIdx.x * n;
   T* vo = V_out + (size_t)blockIdx.x * n * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = A[i * m + i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = A[i * ld + i];
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     int i = idx / n, j = idx % n;
-    vo[idx] = V[i * m + j];
+    vo[idx] = V[i * ld + j];
   }
 }
 
@@ -257,7 +296,7 @@ __global__ void __launch_bounds__(256) jacobi_block_kernel(BlockJacobiArgs args,
           s1[idx] = (u == v) ? T(1) : T(0);
         }
         __syncthreads();
-        JWork<T> w{s0, s1, cs, pq, flag, blk};
+        JWork<T> w{s0, s1, cs, pq, flag, blk, JS};
         bool conv;
         jacobi_smem<T>(w, JS, fro, args.inner_sweeps, &conv);
         if (threadIdx.x == 0 && flag[1]) atomicOr(args.sweep_flags + sweep, 1);
@@ -413,7 +452,7 @@ __global__ void __launch_bounds__(1024) select_kernel(const T* __restrict__ diag
 namespace {
 template <typename T>
 size_t small_smem(int m) {
-  return (size_t)2 * m * m * sizeof(T) + (size_t)m * sizeof(T) + (size_t)(m + 2) * sizeof(int) +
+  return (size_t)2 * m * (m + 1) * sizeof(T) + (size_t)m * sizeof(T) + (size_t)(m + 2) * sizeof(int) +
          (size_t)2 * nblocks_of(m) * sizeof(unsigned short) + 16;
 }
 template <typename T>
@@ -529,8 +568,8 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
 // Only the R leading eigenvectors are needed (Alg. 2: "R_n leading
 // eigenvectors of S").  For m = R + p well below n, this path works on an
 // n x m block:
-//  1. two power steps, Q <- orth(S Q), orthonormalised by shifted
-//     CholeskyQR3;
+//  1. one power step from a random block, Q <- orth(S Q), orthonormalised by
+//     shifted CholeskyQR3;
 //  2. a Rayleigh-Ritz projection B = Q^T S Q diagonalised by the same
 //     one-CTA parallel-order Jacobi as above, giving Ritz vectors Q W;
 //  3. further steps restarting from the Ritz vectors (S Q W = Z W is
@@ -578,16 +617,12 @@ __global__ void colnorm_f32_kernel(float* __restrict__ Y, int64_t n, int64_t m) 
 }
 
 // One CTA: Cholesky L L^T = G + shift * max(diag G) * I (G m x m SPD, float64
-// in, float32 work in shared memory), then LinvT = (L^{-1})^T (m x m
-// column-major float32), so that Q = Y LinvT.  A pivot at or below a tiny
-// floor (rank-deficient block) is raised to the floor, so the factor stays
-// finite.  Two barriers per column for the factorisation, one per row for the
-// inverse.
-__global__ void __launch_bounds__(512) chol_invT_f32_kernel(const double* __restrict__ G, int m, float shift,
-                                                            float* __restrict__ LinvT) {
-  extern __shared__ float sm[];
-  float* L = sm;          // m x m column-major; lower triangle used
-  float* Li = sm + m * m;  // L^{-1}, column-major, lower
+// in, float32 work in shared memory), L written column-major (lower).  A pivot
+// at or below a tiny floor (rank-deficient block) is raised to the floor, so
+// the factor stays finite.  Two barriers per column.
+__global__ void __launch_bounds__(512) chol_f32_kernel(const double* __restrict__ G, int m, float shift,
+                                                       float* __restrict__ Lout) {
+  extern __shared__ float L[];  // m x m, column-major; lower triangle used
   __shared__ float dmax, dinv;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) L[idx] = (float)G[idx];
   __syncthreads();
@@ -600,7 +635,7 @@ __global__ void __launch_bounds__(512) chol_invT_f32_kernel(const double* __rest
   __syncthreads();
   const float floor_v = 1e-12f * dmax + 1e-30f;
   for (int j = 0; j < m; ++j) {
-    // pivot j is final here; scale column j and publish 1/l_jj
+    // pivot j is final here; publish l_jj and its inverse
     if (threadIdx.x == 0) {
       float d = L[j + m * j];
       float ljj = sqrtf(d > floor_v ? d : floor_v);
@@ -610,7 +645,7 @@ __global__ void __launch_bounds__(512) chol_invT_f32_kernel(const double* __rest
     __syncthreads();
     const float inv = dinv;
     const int rem = m - j - 1;
-    // trailing update with the unscaled column, then the scaled column j
+    // trailing update with the unscaled column, then scale column j
     for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
       int i = j + 1 + idx % rem, k = j + 1 + idx / rem;
       if (i >= k) L[i + m * k] = fmaf(-(L[i + m * j] * inv), L[k + m * j] * inv, L[i + m * k]);
@@ -619,18 +654,40 @@ __global__ void __launch_bounds__(512) chol_invT_f32_kernel(const double* __rest
     for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i + m * j] *= inv;
   }
   __syncthreads();
-  // L^{-1} row by row: Li[i][k] = -(sum_{k<=t<i} L[i][t] Li[t][k]) / L[i][i], Li[i][i] = 1 / L[i][i].
-  for (int i = 0; i < m; ++i) {
-    for (int k = threadIdx.x; k <= i; k += blockDim.x) {
-      float acc = (k == i) ? 1.f : 0.f;
-      for (int t = k; t < i; ++t) acc = fmaf(-L[i + m * t], Li[t + m * k], acc);
-      Li[i + m * k] = acc / L[i + m * i];
-    }
-    __syncthreads();
-  }
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
     int r = idx % m, c = idx / m;
-    LinvT[idx] = (r <= c) ? Li[c + m * r] : 0.f;  // LinvT[r][c] = Li[c][r]
+    Lout[idx] = (r >= c) ? L[idx] : 0.f;
+  }
+}
+
+// Q = Y L^{-T}: row i of Q solves L q = y_i (forward substitution).  One
+// thread per row of Y (n x m column-major); L (m x m, lower) and the thread's
+// partial solution live in shared memory.
+constexpr int TRSM_THREADS = 64;
+__global__ void __launch_bounds__(TRSM_THREADS) trsm_rows_kernel(const float* __restrict__ Y,
+                                                                 const float* __restrict__ Lg, int64_t n, int m,
+                                                                 float* __restrict__ Q) {
+  extern __shared__ float sm[];
+  float* L = sm;                   // m x m
+  float* qs = sm + (size_t)m * m;  // TRSM_THREADS x m, element (t, j) at t + TRSM_THREADS * j
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) L[idx] = Lg[idx];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * TRSM_THREADS + threadIdx.x;
+  if (i >= n) return;
+  float* q = qs + threadIdx.x;
+  for (int j = 0; j < m; ++j) {
+    float a0 = Y[i + n * j], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int t = 0;
+    for (; t + 3 < j; t += 4) {
+      a0 = fmaf(-L[j + m * t], q[TRSM_THREADS * t], a0);
+      a1 = fmaf(-L[j + m * (t + 1)], q[TRSM_THREADS * (t + 1)], a1);
+      a2 = fmaf(-L[j + m * (t + 2)], q[TRSM_THREADS * (t + 2)], a2);
+      a3 = fmaf(-L[j + m * (t + 3)], q[TRSM_THREADS * (t + 3)], a3);
+    }
+    for (; t < j; ++t) a0 = fmaf(-L[j + m * t], q[TRSM_THREADS * t], a0);
+    float qj = ((a0 + a1) + (a2 + a3)) / L[j + m * j];
+    q[TRSM_THREADS * j] = qj;
+    Q[i + n * j] = qj;
   }
 }
 
@@ -670,7 +727,7 @@ __global__ void f32_to_f64_kernel2(const float* __restrict__ s, double* __restri
 
 namespace {
 struct RRBufs {
-  float *Sf, *Q, *Y, *Z, *T, *LinvT, *Vb, *diag, *Wf;
+  float *Sf, *Q, *Y, *Z, *T, *LinvT, *Vb, *diag, *Wf;  // LinvT holds the Cholesky factor L
   double *G, *W64, *theta, *res, *summary;
   float* part;  // split-K partials of the m x m products
   size_t part_bytes;
@@ -684,18 +741,21 @@ size_t rr_bytes(int64_t n, int m) {
   return sizeof(float) * ((size_t)n * n + 4 * nm + 3 * mm + m) + sizeof(double) * (2 * mm + 2 * m + 8) +
          rr_part_bytes(n, m) + 16 * 256;
 }
-// One CholeskyQR pass: Q = Y chol(Y^T Y + shift I)^{-T} after normalising the
-// columns of Y (in place).
+// One CholeskyQR pass: Q = Y L^{-T} with L L^T = Y^T Y + shift I, after
+// normalising the columns of Y (in place).
 int cholqr_pass_f32(float* Y, float* Q, int64_t n, int m, float shift, RRBufs& b, cudaStream_t st) {
   const View v{n, m, 1};
   colnorm_f32_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Y, n, m);
   ATK_LAUNCHED();
   ATK_TRY(gram_f32(Y, v, b.G, b.part, b.part_bytes, st));
-  size_t sm = (size_t)2 * m * m * sizeof(float);
-  ATK_CUDA(cudaFuncSetAttribute(chol_invT_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  chol_invT_f32_kernel<<<1, 512, sm, st>>>(b.G, m, shift, b.LinvT);
+  const size_t sm = (size_t)m * m * sizeof(float);
+  ATK_CUDA(cudaFuncSetAttribute(chol_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  chol_f32_kernel<<<1, 512, sm, st>>>(b.G, m, shift, b.LinvT);
   ATK_LAUNCHED();
-  ATK_TRY(ttm_f32(Y, v, b.LinvT, m, Q, st));
+  const size_t sm2 = sm + (size_t)TRSM_THREADS * m * sizeof(float);
+  ATK_CUDA(cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  trsm_rows_kernel<<<(unsigned)ceil_div(n, TRSM_THREADS), TRSM_THREADS, sm2, st>>>(Y, b.LinvT, n, m, Q);
+  ATK_LAUNCHED();
   return ATK_OK;
 }
 // Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Zhang, Yamamoto, SISC 2020):
@@ -741,11 +801,10 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   ATK_TRY(f64_to_f32(S, b.Sf, n * n, st));
   rand_fill_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, st>>>(b.Q, (int64_t)nm, 0x5EEDULL + (uint64_t)n);
   ATK_LAUNCHED();
-  // Two power steps from the random block.
-  for (int s = 0; s < 2; ++s) {
-    ATK_TRY(ttm_f32(b.Sf, sv, b.Q, m, b.Y, st));  // Y = S Q
-    ATK_TRY(cholqr3_f32(b.Y, b.T, b.Q, n, m, b, st));
-  }
+  // One power step from the random block; the loop below continues from the
+  // Ritz vectors when more are needed.
+  ATK_TRY(ttm_f32(b.Sf, sv, b.Q, m, b.Y, st));  // Y = S Q
+  ATK_TRY(cholqr3_f32(b.Y, b.T, b.Q, n, m, b, st));
   const int mp = m + (m & 1);
   const size_t jsm = small_smem<float>(mp);
   ATK_CUDA(cudaFuncSetAttribute(jacobi_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
@@ -753,7 +812,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
     // Rayleigh-Ritz: Z = S Q, B = Q^T Z = W diag(theta) W^T.
     ATK_TRY(ttm_f32(b.Sf, sv, b.Q, m, b.Z, st));
     ATK_TRY(cross_f32(b.Q, qv, b.Z, m, b.G, b.part, b.part_bytes, st));
-    jacobi_small_kernel<float><<<1, 1024, jsm, st>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
+    jacobi_small_kernel<float><<<1, 512, jsm, st>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
     ATK_LAUNCHED();
     select_kernel<float><<<1, 1024, 0, st>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
     ATK_LAUNCHED();
