@@ -280,6 +280,45 @@ def run_ours(args):
     return 0
 
 
+def run_case(args):
+    """Time one step-level operation on one view: --case gram:LO,N,HI or ttm:LO,N,HI,R.
+
+    Used for kernel profiles: the input is synthetic N(0,1) float32 on the
+    device, the call goes through the C ABI, and the line reports the
+    operation's device time (CUDA events) and its algorithmic rate.
+    """
+    import torch
+    import paper_2010_10131_b300 as atk
+    kind, _, shape = args.case.partition(":")
+    vals = [int(v) for v in shape.split(",")]
+    lo, n, hi = vals[:3]
+    g = torch.Generator(device="cuda").manual_seed(0)
+    y = torch.randn(lo * n * hi, device="cuda", generator=g)
+    if kind == "gram":
+        fn = lambda: atk.gram(y, lo, n, hi)  # noqa: E731
+        flops = float(n) * n * lo * hi  # I_n^2 J_n (Eq. 4)
+    elif kind == "ttm":
+        R = vals[3]
+        U = torch.randn(n, R, device="cuda", generator=g)
+        fn = lambda: atk.ttm(y, lo, n, hi, U)  # noqa: E731
+        flops = 2.0 * n * R * lo * hi
+    else:
+        raise SystemExit(f"unknown case {kind}")
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"case": args.case, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                      "input_gbs": lo * n * hi * 4 / (ms * 1e-3) / 1e9}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,7 +326,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, help="profile one op: gram:LO,N,HI or ttm:LO,N,HI,R")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

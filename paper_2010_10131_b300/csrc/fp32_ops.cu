@@ -32,37 +32,40 @@ constexpr int SPLIT_MAX_K = 8192;
 // into registers, then stores it to shared memory as s[k * (W + PAD) + m].
 
 // A view operand with k = c (the other index) and m = i (mode index): CI role.
+// Index state is 32-bit: every tensor the library accepts has fewer than 2^31
+// elements, so every offset below fits.
 template <int W>
 struct ViewLoaderKC {
   static constexpr int PER = TK * W / NT;
   const float* y;
-  int64_t lo, n, c_end, i0;
+  int lo, n, c_end, i0;
   bool lanes_on_m;  // lo == 1: m (= i) is contiguous
   int km, mm, step;
   float r[PER];
   __device__ void init(const float* y_, int64_t lo_, int64_t n_, int64_t c_end_, int64_t i0_) {
-    y = y_; lo = lo_; n = n_; c_end = c_end_; i0 = i0_;
+    y = y_; lo = (int)lo_; n = (int)n_; c_end = (int)c_end_; i0 = (int)i0_;
     lanes_on_m = (lo == 1);
     int t = threadIdx.x;
     if (lanes_on_m) { mm = t % W; km = t / W; step = NT / W; }
     else { km = t % TK; mm = t / TK; step = NT / TK; }
   }
-  __device__ void fetch(int64_t c0) {
+  __device__ void fetch(int64_t c0_) {
+    const int c0 = (int)c0_;
     if (lanes_on_m) {
-      const int64_t i = i0 + mm;
+      const int i = i0 + mm;
 #pragma unroll
       for (int e = 0; e < PER; ++e) {
-        int64_t c = c0 + km + e * step;
-        r[e] = (c < c_end && i < n) ? __ldg(y + i + n * c) : 0.f;
+        int c = c0 + km + e * step;
+        r[e] = (c < c_end && i < n) ? __ldg(y + (i + n * c)) : 0.f;
       }
     } else {
-      int64_t c = c0 + km;
+      int c = c0 + km;
       bool cv = c < c_end;
-      int64_t a = cv ? c % lo : 0, b = cv ? c / lo : 0;
-      const float* base = y + a + lo * n * b;
+      int a = cv ? c % lo : 0, b = cv ? c / lo : 0;
+      const float* base = y + (a + lo * n * b);
 #pragma unroll
       for (int e = 0; e < PER; ++e) {
-        int64_t i = i0 + mm + e * step;
+        int i = i0 + mm + e * step;
         r[e] = (cv && i < n) ? __ldg(base + lo * i) : 0.f;
       }
     }
@@ -83,36 +86,37 @@ template <int W>
 struct ViewLoaderKI {
   static constexpr int PER = TK * W / NT;
   const float* y;
-  int64_t lo, n, J, c0, cbase_off;
+  int lo, n, J, c0, cbase_off;
   bool lanes_on_k;  // lo == 1: k (= i) is contiguous
   bool cvalid;
   int km, mm, step;
   float r[PER];
   __device__ void init(const float* y_, int64_t lo_, int64_t n_, int64_t J_, int64_t c0_) {
-    y = y_; lo = lo_; n = n_; J = J_; c0 = c0_;
+    y = y_; lo = (int)lo_; n = (int)n_; J = (int)J_; c0 = (int)c0_;
     lanes_on_k = (lo == 1);
     int t = threadIdx.x;
     if (lanes_on_k) { km = t % TK; mm = t / TK; step = NT / TK; }
     else {
       mm = t % W; km = t / W; step = NT / W;
-      int64_t c = c0 + mm;
+      int c = c0 + mm;
       cvalid = c < J;
       cbase_off = cvalid ? (c % lo) + lo * n * (c / lo) : 0;
     }
   }
-  __device__ void fetch(int64_t i0) {
+  __device__ void fetch(int64_t i0_) {
+    const int i0 = (int)i0_;
     if (lanes_on_k) {
-      int64_t i = i0 + km;
+      int i = i0 + km;
 #pragma unroll
       for (int e = 0; e < PER; ++e) {
-        int64_t c = c0 + mm + e * step;
-        r[e] = (i < n && c < J) ? __ldg(y + i + n * c) : 0.f;
+        int c = c0 + mm + e * step;
+        r[e] = (i < n && c < J) ? __ldg(y + (i + n * c)) : 0.f;
       }
     } else {
 #pragma unroll
       for (int e = 0; e < PER; ++e) {
-        int64_t i = i0 + km + e * step;
-        r[e] = (cvalid && i < n) ? __ldg(y + cbase_off + lo * i) : 0.f;
+        int i = i0 + km + e * step;
+        r[e] = (cvalid && i < n) ? __ldg(y + (cbase_off + lo * i)) : 0.f;
       }
     }
   }
@@ -211,60 +215,77 @@ struct Block {
   }
 };
 
-// Upper-triangle tile enumeration of a T x T tile grid (row-major).
-__host__ __device__ inline void tri_tile(int id, int T, int& ti, int& tj) {
-  ti = 0;
-  while (id >= T - ti) { id -= T - ti; ++ti; }
-  tj = ti + id;
-}
-
 // ------------------------------------------------------------- CI kernels
-// Gram: C = sum_c Y(c, :)^T Y(c, :), upper-triangle tiles only; partial tile
-// (row-major BM x BN, float32) per (tile, split).
-template <int BM, int TM>
+// Gram: C = sum_c Y(c, :)^T Y(c, :), upper-triangle tiles only; one partial
+// tile (row-major BM x BM, float32) per (tile, split), indexed by the tile's
+// row-major position in the upper triangle.  Diagonal and off-diagonal tiles
+// are separate launches (DIAG): a diagonal tile loads one operand and uses it
+// twice, and neither instantiation carries the other's registers.
+template <int BM, int TM, bool DIAG>
 __global__ void __launch_bounds__(NT, 2)
 gram_ci_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, int T, int64_t kc,
                float* __restrict__ part) {
-  __shared__ __align__(16) float sA[2][TK * (BM + PAD)];
-  __shared__ __align__(16) float sB[2][TK * (BM + PAD)];
-  int tile = blockIdx.x, split = blockIdx.y;
+  constexpr int SA = TK * (BM + PAD);
+  __shared__ __align__(16) float sA[2 * SA];
+  __shared__ __align__(16) float sB[DIAG ? 1 : 2 * SA];
+  const int split = blockIdx.y;
   int ti, tj;
-  tri_tile(tile, T, ti, tj);
-  const bool diag = ti == tj;
+  if (DIAG) {
+    ti = tj = blockIdx.x;
+  } else {
+    // blockIdx.x enumerates the strict upper triangle row by row
+    int id = blockIdx.x;
+    ti = 0;
+    while (id >= T - 1 - ti) { id -= T - 1 - ti; ++ti; }
+    tj = ti + 1 + id;
+  }
+  const int tile = ti * T - ti * (ti - 1) / 2 + (tj - ti);
   const int64_t J = lo * hi;
   const int64_t cb = (int64_t)split * kc, ce = min(J, cb + kc);
   ViewLoaderKC<BM> la, lb;
   la.init(y, lo, n, ce, (int64_t)ti * BM);
-  lb.init(y, lo, n, ce, (int64_t)tj * BM);
+  if (!DIAG) lb.init(y, lo, n, ce, (int64_t)tj * BM);
   Block<BM, BM, TM, TM> blk;
   blk.init();
   const int64_t ntile = cb < ce ? (ce - cb + TK - 1) / TK : 0;
   if (ntile > 0) {
     la.fetch(cb);
-    if (!diag) lb.fetch(cb);
-    la.store(sA[0]);
-    if (!diag) lb.store(sB[0]);
+    la.store(sA);
+    if (!DIAG) {
+      lb.fetch(cb);
+      lb.store(sB);
+    }
     __syncthreads();
     for (int64_t t = 0; t < ntile; ++t) {
       const int buf = t & 1;
       if (t + 1 < ntile) {
         la.fetch(cb + (t + 1) * TK);
-        if (!diag) lb.fetch(cb + (t + 1) * TK);
+        if (!DIAG) lb.fetch(cb + (t + 1) * TK);
       }
-      blk.mma(sA[buf], diag ? sA[buf] : sB[buf]);
+      if (DIAG) blk.mma(sA + buf * SA, sA + buf * SA);
+      else blk.mma(sA + buf * SA, sB + buf * SA);
       if (t + 1 < ntile) {
-        la.store(sA[buf ^ 1]);
-        if (!diag) lb.store(sB[buf ^ 1]);
+        la.store(sA + (buf ^ 1) * SA);
+        if (!DIAG) lb.store(sB + (buf ^ 1) * SA);
       }
       __syncthreads();
     }
   }
-  float* out = part + ((int64_t)split * gridDim.x + tile) * (BM * BM);
+  const int ntiles = T * (T + 1) / 2;
+  float* out = part + ((int64_t)split * ntiles + tile) * (BM * BM);
 #pragma unroll
   for (int u = 0; u < TM; ++u)
 #pragma unroll
     for (int v = 0; v < TM; ++v)
       out[Block<BM, BM, TM, TM>::row_of(blk.ty, u) * BM + Block<BM, BM, TM, TM>::col_of(blk.tx, v)] = blk.acc[u][v];
+}
+
+template <int BM, int TM>
+static void launch_gram_tiles(const float* y, const View& v, int T, int ns_d, int64_t kc_d, int ns_o, int64_t kc_o,
+                              float* part, cudaStream_t st) {
+  gram_ci_kernel<BM, TM, true><<<dim3(T, ns_d), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_d, part);
+  if (T > 1)
+    gram_ci_kernel<BM, TM, false><<<dim3(T * (T - 1) / 2, ns_o), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_o, part);
 }
 
 // Cross product C (n x R) = sum_c Y(c, i) P(c, r), P a (lo, R, hi) tensor.
@@ -315,9 +336,10 @@ cross_ci_kernel(const float* __restrict__ y, const float* __restrict__ p, int64_
 }
 
 // Sum the split-K partial tiles in float64, in split order (deterministic).
-// sym: C is n x n from upper-triangle tiles (T x T grid of BM tiles).
-__global__ void reduce_sym_kernel(const float* __restrict__ part, int nsplit, int ntiles, int T, int BM, int64_t n,
-                                  double* __restrict__ C) {
+// sym: C is n x n from upper-triangle tiles (T x T grid of BM tiles); diagonal
+// tiles have ns_d splits, off-diagonal tiles ns_o.
+__global__ void reduce_sym_kernel(const float* __restrict__ part, int ns_d, int ns_o, int ntiles, int T, int BM,
+                                  int64_t n, double* __restrict__ C) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   int64_t i = idx / n, j = idx % n;  // lanes along j: contiguous within a tile row
@@ -325,6 +347,7 @@ __global__ void reduce_sym_kernel(const float* __restrict__ part, int nsplit, in
   int ti = (int)(i / BM), tj = (int)(j / BM);
   int id = ti * T - ti * (ti - 1) / 2 + (tj - ti);
   int64_t o = (i - (int64_t)ti * BM) * BM + (j - (int64_t)tj * BM);
+  const int nsplit = ti == tj ? ns_d : ns_o;
   double s = 0.0;
   for (int sp = 0; sp < nsplit; ++sp) s += (double)part[((int64_t)sp * ntiles + id) * BM * BM + o];
   C[i + n * j] = s;
@@ -399,11 +422,14 @@ struct SplitPlan {
   int nsplit;
   int64_t kc;
 };
+// Split count for a CI launch of `ntiles` output tiles: at least enough splits
+// to keep every float32 partial sum within SPLIT_MAX_K terms, then as many as
+// fill the needed waves of (2 CTAs per SM) slots without a partial tail wave.
 SplitPlan choose_split(int64_t J, int ntiles) {
   const int slots = 2 * num_sms();
-  int64_t need = ceil_div(J, SPLIT_MAX_K) * ntiles;  // splits required for accuracy
-  int64_t waves = std::max<int64_t>(1, ceil_div(need, slots));
-  int64_t nsplit = std::max<int64_t>(1, ceil_div(waves * slots, ntiles));
+  const int64_t min_split = ceil_div(J, SPLIT_MAX_K);
+  const int64_t waves = std::max<int64_t>(1, ceil_div(min_split * ntiles, slots));
+  int64_t nsplit = std::max<int64_t>(min_split, (waves * slots) / ntiles);
   nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, ceil_div(J, TK)));
   int64_t kc = ceil_div(ceil_div(J, nsplit), TK) * TK;
   nsplit = ceil_div(J, kc);
@@ -413,12 +439,24 @@ int gram_bm(int64_t n) { return n > 64 ? 128 : (n > 32 ? 64 : 32); }
 int cross_bn(int64_t R) { return R > 64 ? 128 : (R > 32 ? 64 : (R > 16 ? 32 : 16)); }
 }  // namespace
 
+// Split plans of the two Gram launches (diagonal tiles, off-diagonal tiles).
+struct GramPlan {
+  int bm, T, nt;
+  SplitPlan d, o;
+};
+static GramPlan gram_plan(const View& v) {
+  GramPlan g;
+  g.bm = gram_bm(v.n);
+  g.T = (int)ceil_div(v.n, g.bm);
+  g.nt = g.T * (g.T + 1) / 2;
+  g.d = choose_split(v.J(), g.T);
+  g.o = g.T > 1 ? choose_split(v.J(), g.T * (g.T - 1) / 2) : g.d;
+  return g;
+}
+
 size_t gram_scratch_bytes(const View& v) {
-  int bm = gram_bm(v.n);
-  int T = (int)ceil_div(v.n, bm);
-  int nt = T * (T + 1) / 2;
-  SplitPlan sp = choose_split(v.J(), nt);
-  return (size_t)sp.nsplit * nt * bm * bm * sizeof(float);
+  GramPlan g = gram_plan(v);
+  return (size_t)std::max(g.d.nsplit, g.o.nsplit) * g.nt * g.bm * g.bm * sizeof(float);
 }
 
 int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st,
@@ -428,22 +466,20 @@ int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t sc
     ATK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * v.n * v.n, st));
     return ATK_OK;
   }
-  int bm = gram_bm(v.n);
-  int T = (int)ceil_div(v.n, bm);
-  int nt = T * (T + 1) / 2;
-  SplitPlan sp = choose_split(v.J(), nt);
-  if ((size_t)sp.nsplit * nt * bm * bm * sizeof(float) > scratch_bytes) {
+  GramPlan g = gram_plan(v);
+  if (gram_scratch_bytes(v) > scratch_bytes) {
     set_error("gram_f32: scratch too small");
     return ATK_EINVAL;
   }
-  dim3 grid(nt, sp.nsplit);
-  if (bm == 128) gram_ci_kernel<128, 8><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
-  else if (bm == 64) gram_ci_kernel<64, 4><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
-  else gram_ci_kernel<32, 2><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
+  if (g.bm == 128) launch_gram_tiles<128, 8>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
+  else if (g.bm == 64) launch_gram_tiles<64, 4>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
+  else launch_gram_tiles<32, 2>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
   ATK_LAUNCHED();
+  if (g.T > 1) count_launch();
   if (mid) ATK_CUDA(cudaEventRecord(mid, st));
   int64_t total = v.n * v.n;
-  reduce_sym_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(scratch, sp.nsplit, nt, T, bm, v.n, S);
+  reduce_sym_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(scratch, g.d.nsplit, g.o.nsplit, g.nt, g.T, g.bm,
+                                                                     v.n, S);
   ATK_LAUNCHED();
   return ATK_OK;
 }
@@ -459,26 +495,26 @@ int gram_f32_fixed_scratch(const float* y, const View& v, double* S, float* scra
     ATK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * v.n * v.n, st));
     return ATK_OK;
   }
-  const int bm = gram_bm(v.n);
-  const int T = (int)ceil_div(v.n, bm);
-  const int nt = T * (T + 1) / 2;
-  const size_t per_split = (size_t)nt * bm * bm * sizeof(float);
+  GramPlan g = gram_plan(v);
+  const size_t per_split = (size_t)g.nt * g.bm * g.bm * sizeof(float);
   const int64_t fit = (int64_t)(scratch_bytes / per_split);
   if (fit < 1) {
     set_error("gram: the partial tiles of one split do not fit in the fixed scratch");
     return ATK_EUNSUPPORTED;
   }
-  SplitPlan sp = choose_split(v.J(), nt);
-  if (sp.nsplit > fit) {
-    sp.kc = ceil_div(ceil_div(v.J(), fit), TK) * TK;
-    sp.nsplit = (int)ceil_div(v.J(), sp.kc);
+  for (SplitPlan* sp : {&g.d, &g.o}) {
+    if (sp->nsplit > fit) {
+      sp->kc = ceil_div(ceil_div(v.J(), fit), TK) * TK;
+      sp->nsplit = (int)ceil_div(v.J(), sp->kc);
+    }
   }
-  dim3 grid(nt, sp.nsplit);
-  if (bm == 128) gram_ci_kernel<128, 8><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
-  else if (bm == 64) gram_ci_kernel<64, 4><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
-  else gram_ci_kernel<32, 2><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, T, sp.kc, scratch);
+  if (g.bm == 128) launch_gram_tiles<128, 8>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
+  else if (g.bm == 64) launch_gram_tiles<64, 4>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
+  else launch_gram_tiles<32, 2>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
   ATK_LAUNCHED();
-  reduce_sym_kernel<<<(unsigned)ceil_div(v.n * v.n, 256), 256, 0, st>>>(scratch, sp.nsplit, nt, T, bm, v.n, S);
+  if (g.T > 1) count_launch();
+  reduce_sym_kernel<<<(unsigned)ceil_div(v.n * v.n, 256), 256, 0, st>>>(scratch, g.d.nsplit, g.o.nsplit, g.nt, g.T,
+                                                                         g.bm, v.n, S);
   ATK_LAUNCHED();
   return ATK_OK;
 }
