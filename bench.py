@@ -39,6 +39,7 @@ UNIT = "GB/s"
 TENSORS = [((640, 640, 640), (64, 64, 64)), ((128, 128, 128, 128), (16, 16, 16, 16))]
 WORKLOAD = "plain FP32 st-HOSVD (EIG every mode): 640^3 R64 + 128^4 R16, random Tucker + 1e-3 noise"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+GRAM_TRAFFIC_RATIO = 1.02  # DRAM bytes / input bytes per Gram launch, from the ncu capture in profiles/
 CPU_SAMPLE = ((640, 640, 8), (64, 64, 8))       # cpu_baseline: a 640 x 640 x 8 slab of the workload
 REF_SAMPLE = ((640, 160, 8), (64, 64, 8))       # reference arm: one such slab sample per step
 
@@ -222,6 +223,19 @@ def run_ours(args):
     value = in_bytes * ws / (ms * 1e-3) / 1e9
 
     # Dominant kernel: the Gram partial-tile kernel (float32 CUDA cores).
+    # DRAM traffic per Gram call, scaled from one ncu capture of a smaller view
+    # (profiles/gram_ci_fp32_640x80000.md): each launch reads its input once
+    # (measured traffic / input bytes = 1.02), and a call makes two launches
+    # (diagonal and off-diagonal tiles) when the Gram has more than 128 rows.
+    calls, traffic_bytes = 0, 0.0
+    for d, r in TENSORS:
+        cur = list(d)
+        for nmode in range(len(d)):
+            size = float(np.prod(cur)) * 4
+            launches = 1 if cur[nmode] <= 128 else 2
+            traffic_bytes += GRAM_TRAFFIC_RATIO * size * launches
+            calls += 1
+            cur[nmode] = r[nmode]
     gram_ms = sum(t["gram"] for t in tims)
     flops = sum(gram_flops(d, r, [0] * len(d)) for d, r in TENSORS) * args.steps
     achieved = flops / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None
@@ -260,7 +274,9 @@ def run_ours(args):
                        "precision": "FP32 CUDA cores", "l2": "inputs (1.05 GB, 1.07 GB) larger than L2; no flush"},
             "roofline": {"bound": "alu", "kernel": "gram_ci_kernel (float32 FMA)",
                          "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": (achieved / FP32_ALU_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                         "frac": (achieved / FP32_ALU_PEAK_TFLOPS) if achieved else None,
+                         "traffic": traffic_bytes / calls, "traffic_unit": "bytes per Gram call",
+                         "traffic_source": "scaled from ncu dram bytes of gram:1,640,80000 (ratio 1.02 x input)",
                          "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
                          "flops_per_step": flops / max(args.steps, 1),
                          "ms_per_step": gram_ms / max(args.steps, 1)},
