@@ -54,8 +54,17 @@ typedef enum { ATK_EIG = 0, ATK_ALS = 1 } atucker_solver;
 
 /* Arithmetic for the bulk Gram / TTM / ALS contractions.
  * ATK_FP32 is plain float32 on the CUDA cores, accumulated in float32 and
- * reduced in float64 across split-K partials. */
-typedef enum { ATK_FP32 = 0 } atucker_precision;
+ * reduced in float64 across split-K partials.  The tensor-core forms
+ * (tcgen05, float32 accumulation in tensor memory, the same float64 split-K
+ * reduction) apply to the Gram of EIG modes:
+ *   ATK_TF32     operands rounded to TF32 (round to nearest)
+ *   ATK_BF16     operands rounded to BF16
+ *   ATK_BF16X3   x = hi + lo (both BF16); hi hi^T + hi lo^T + lo hi^T
+ *   ATK_FP8E4M3  each mode-n row i scaled by the power of two
+ *                s_i = 2^floor(log2(448 / max |row i|)), rounded to e4m3; the
+ *                product is divided by s_i s_j exactly afterwards
+ * The eigensolver, TTM, ALS and orthonormalisation are unchanged. */
+typedef enum { ATK_FP32 = 0, ATK_TF32 = 1, ATK_BF16 = 2, ATK_BF16X3 = 3, ATK_FP8E4M3 = 4 } atucker_precision;
 
 /* Arithmetic of the Jacobi rotations in the eigensolver.  Either way, the
  * Gram arrives in float64, and eigenvalue sums and the final

@@ -15,7 +15,7 @@ import re
 
 __all__ = [
     "lib", "abi_symbols", "AtuckerError", "Plan", "sthosvd", "gram", "ttm", "eig", "als_mode",
-    "EIG", "ALS", "FP32", "EIG_ROT_FP32", "EIG_ROT_FP64",
+    "EIG", "ALS", "FP32", "TF32", "BF16", "BF16X3", "FP8E4M3", "EIG_ROT_FP32", "EIG_ROT_FP64",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -25,7 +25,7 @@ HEADER = os.path.join(_ROOT, "include", "atucker.h")
 
 OK, EINVAL, ERANK, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 EIG, ALS = 0, 1
-FP32 = 0
+FP32, TF32, BF16, BF16X3, FP8E4M3 = 0, 1, 2, 3, 4
 EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
 OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD = 1, 2, 3, 4, 5
 EIG_AUTO, EIG_FULL_JACOBI, EIG_SUBSPACE = 0, 1, 2
@@ -214,12 +214,13 @@ class Plan:
 
 
 def sthosvd(x, dims, ranks, mode_order=None, solver=None, als_sweeps: int = 5, seed: int = 0,
-            eig_arith: int | None = None, with_discarded: bool = False, eig_method: int | None = None):
+            eig_arith: int | None = None, with_discarded: bool = False, eig_method: int | None = None,
+            precision: int = FP32):
     """Decompose the column-major tensor x (flat CUDA float32).
 
     Returns (core_flat, [U^(n)], discarded or None)."""
     torch = _torch()
-    p = Plan(dims, ranks, mode_order, solver, FP32, als_sweeps, seed, eig_arith=eig_arith, eig_method=eig_method)
+    p = Plan(dims, ranks, mode_order, solver, precision, als_sweeps, seed, eig_arith=eig_arith, eig_method=eig_method)
     disc = torch.zeros(len(dims), device=x.device, dtype=torch.float64) if with_discarded else None
     core, fac = p.run(x, discarded=disc)
     p.sync()

@@ -129,6 +129,12 @@ size_t cross_scratch_bytes(const View& v, int64_t R);
 int cross_f32(const float* y, const View& v, const float* P, int64_t R, double* C, float* scratch,
               size_t scratch_bytes, cudaStream_t st);
 
+// Tensor-core Gram (tc_ops.cu): precision is ATK_TF32, ATK_BF16, ATK_BF16X3 or
+// ATK_FP8E4M3.  Bounded waits report DEV_TIMEOUT through *status.
+size_t tc_gram_scratch_bytes(const View& v, int precision);
+int tc_gram(const float* y, const View& v, int precision, double* S, float* scratch, size_t scratch_bytes,
+            int* status, cudaStream_t st);
+
 // Jacobi eigensolver (jacobi.cu).
 size_t eig_scratch_bytes(int64_t n, int arith);
 // method: ATK_EIG_AUTO (Rayleigh-Ritz when R + p <= n/2, else full Jacobi),

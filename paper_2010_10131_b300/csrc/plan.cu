@@ -201,6 +201,7 @@ static int plan_alloc(atucker_plan_s* p) {
     if (p->solver[n] == ATK_EIG) {
       s_elems = std::max(s_elems, (size_t)(v.n * v.n));
       scratch = std::max(scratch, gram_scratch_bytes(v));
+      if (p->precision != ATK_FP32) scratch = std::max(scratch, tc_gram_scratch_bytes(v, p->precision));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP64));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP32));
       scratch = std::max(scratch, smallla_scratch_bytes(v.n, R));
@@ -272,7 +273,7 @@ int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, co
   if (!plan) { set_error("plan is null"); return ATK_EINVAL; }
   *plan = nullptr;
   ATK_TRY(validate(order, dims, ranks, mode_order, solver_per_mode));
-  if (precision != ATK_FP32) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  if (precision < ATK_FP32 || precision > ATK_FP8E4M3) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
   atucker_plan_s* p = new atucker_plan_s();
   p->order = order;
   int64_t off = 0;
@@ -375,7 +376,12 @@ int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* fa
     if (p->solver[n] == ATK_EIG) {
       // S = Y_(n) Y_(n)^T; U = leading eigenvectors; Y' = Y x_n U^T.
       cudaEvent_t mid = tm ? p->ev() : nullptr;
-      ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid));
+      if (p->precision == ATK_FP32) {
+        ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid));
+      } else {
+        ATK_TRY(tc_gram(Y, v, p->precision, p->S, (float*)p->scratch, p->scratch_bytes, p->dev_status, st));
+        if (mid) ATK_CUDA(cudaEventRecord(mid, st));
+      }
       if (tm) {
         p->recs.push_back({PH_GRAM, e_prev, mid});
         e_prev = mid;
@@ -507,14 +513,22 @@ static int read_status(int* dev, cudaStream_t st) {
 int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precision, double* S_out, void* stream) {
   if (!y || !S_out) { set_error("null argument"); return ATK_EINVAL; }
   ATK_TRY(check_view(lo, n, hi));
-  if (precision != ATK_FP32) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  if (precision < ATK_FP32 || precision > ATK_FP8E4M3) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
   if (n > 4096) { set_error("Gram needs n <= 4096"); return ATK_EUNSUPPORTED; }
   cudaStream_t st = (cudaStream_t)stream;
   View v{lo, n, hi};
   StreamScratch sc(st);
-  size_t bytes = gram_scratch_bytes(v);
+  if (precision == ATK_FP32) {
+    size_t bytes = gram_scratch_bytes(v);
+    ATK_TRY(sc.alloc(bytes));
+    return gram_f32(y, v, S_out, (float*)sc.ptr, bytes, st);
+  }
+  size_t bytes = tc_gram_scratch_bytes(v, precision) + 256;
   ATK_TRY(sc.alloc(bytes));
-  return gram_f32(y, v, S_out, (float*)sc.ptr, bytes, st);
+  int* status = (int*)((char*)sc.ptr + bytes - 256);
+  ATK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  ATK_TRY(tc_gram(y, v, precision, S_out, (float*)sc.ptr, bytes - 256, status, st));
+  return read_status(status, st);
 }
 
 int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* U, int64_t R, int precision,
