@@ -139,6 +139,16 @@ def cpu_oracle_sample(sample, reps=1):
     return x.nbytes, times
 
 
+def relerr_identity(x_np, core_t):
+    """||X - X_hat|| / ||X|| from ||X||^2 - ||G||^2 (exact for EIG modes with orthonormal factors)."""
+    nx2 = 0.0
+    for chunk in np.array_split(x_np, 64):
+        c = chunk.astype(np.float64)
+        nx2 += float(np.dot(c, c))
+    g = core_t.detach().cpu().numpy().astype(np.float64)
+    return float(np.sqrt(max(nx2 - float(np.dot(g, g)), 0.0) / nx2))
+
+
 def run_reference(args):
     rank, ws, _ = dist_env()
     if rank != 0:
@@ -179,9 +189,10 @@ def run_ours(args):
     import synth
     atk.lib()
     stream = torch.cuda.current_stream()
-    plans, xs, hosts = [], [], []
+    plans, xs, hosts, xnps = [], [], [], []
     for dims, ranks in TENSORS:
         x, _, _ = synth.random_tucker(dims, ranks, seed=rank)
+        xnps.append(x)
         xt = torch.from_numpy(x).cuda()
         p = atk.Plan(dims, ranks, solver=[0] * len(dims), stream=stream)
         core = torch.empty(p.core_numel, device="cuda")
@@ -243,6 +254,37 @@ def run_ours(args):
               ("gram", "gram_reduce", "eig", "ttm", "als", "norms", "total")}
     launches = int(sum(t["launches"] for t in tims))
 
+    # Mixed precision on the same tensors: the tensor-core Gram forms, timed
+    # like the plain step, each compared by relative error with the plain output.
+    mixed = None
+    if not args.no_mixed:
+        rel_plain = [relerr_identity(xn, core) for xn, (_, core, _) in zip(xnps, plans)]
+        mixed = {"relerr_plain": rel_plain, "forms": {}}
+        for name, prec in (("BF16X3", atk.BF16X3), ("TF32", atk.TF32), ("BF16", atk.BF16)):
+            mplans = []
+            for (dims, ranks), x in zip(TENSORS, xs):
+                mp = atk.Plan(dims, ranks, solver=[0] * len(dims), precision=prec, stream=stream)
+                mplans.append((mp, torch.empty(mp.core_numel, device="cuda"),
+                               torch.empty(mp.factors_numel, device="cuda")))
+            for _ in range(args.warmup):
+                for (mp, c, f), x in zip(mplans, xs):
+                    mp.run(x, c, f)
+            torch.cuda.synchronize()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            for _ in range(args.steps):
+                for (mp, c, f), x in zip(mplans, xs):
+                    mp.run(x, c, f)
+            m1.record(stream)
+            torch.cuda.synchronize()
+            mms = m0.elapsed_time(m1) / max(args.steps, 1)
+            rel = [relerr_identity(xn, c) for xn, (_, c, _) in zip(xnps, mplans)]
+            mixed["forms"][name] = {"ms_per_step": mms, "value": in_bytes / (mms * 1e-3) / 1e9,
+                                    "speedup_vs_plain": ms / mms, "relerr": rel,
+                                    "max_relerr_delta_vs_plain": max(abs(a - b) for a, b in zip(rel, rel_plain))}
+            for mp, _, _ in mplans:
+                mp.close()
+
     # End to end through the C ABI with host buffers (copies inside the timed region).
     cores_h = [torch.empty(p.core_numel).pin_memory() for p, _, _ in plans]
     facs_h = [torch.empty(p.factors_numel).pin_memory() for p, _, _ in plans]
@@ -281,6 +323,7 @@ def run_ours(args):
                          "flops_per_step": flops / max(args.steps, 1),
                          "ms_per_step": gram_ms / max(args.steps, 1)},
             "phases_ms_per_step": phases,
+            "mixed": mixed,
             "e2e": {"value": in_bytes / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -305,13 +348,14 @@ def run_case(args):
     """
     import torch
     import paper_2010_10131_b300 as atk
+    prec = args.precision
     kind, _, shape = args.case.partition(":")
     vals = [int(v) for v in shape.split(",")]
     lo, n, hi = vals[:3]
     g = torch.Generator(device="cuda").manual_seed(0)
     y = torch.randn(lo * n * hi, device="cuda", generator=g)
     if kind == "gram":
-        fn = lambda: atk.gram(y, lo, n, hi)  # noqa: E731
+        fn = lambda: atk.gram(y, lo, n, hi, precision=prec)  # noqa: E731
         flops = float(n) * n * lo * hi  # I_n^2 J_n (Eq. 4)
     elif kind == "ttm":
         R = vals[3]
@@ -330,7 +374,7 @@ def run_case(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    print(json.dumps({"case": args.case, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+    print(json.dumps({"case": args.case, "precision": prec, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
                       "input_gbs": lo * n * hi * 4 / (ms * 1e-3) / 1e9}), flush=True)
     return 0
 
@@ -343,6 +387,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, help="profile one op: gram:LO,N,HI or ttm:LO,N,HI,R")
+    ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 TF32, 2 BF16, 3 3xBF16, 4 FP8-e4m3 (--case)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
