@@ -7,23 +7,34 @@
 //   BF16    operands rounded to BF16, kind::f16
 //   BF16X3  x = hi + lo with hi = bf16(x), lo = bf16(x - hi);
 //           hi hi^T + hi lo^T + lo hi^T, three kind::f16 MMAs per step
-//   FP8E4M3 each mode-n row i is scaled by s_i = 2^floor(log2(448 / max_c |y_ic|))
-//           (a power of two, from a row-max pre-pass), rounded to e4m3,
+//   FP8E4M3 each mode-n row i is scaled by s_i = 2^(8 - e_i), where
+//           max_c |y_ic| lies in [2^(e_i - 1), 2^e_i) (a row-max pre-pass),
+//           so every scaled value is below 256 < 448; rounded to e4m3,
 //           kind::f8f6f4; the reduction multiplies S_ij by 1 / (s_i s_j) exactly.
 // Every form accumulates in float32 in tensor memory (TMEM).  Split-K partial
 // tiles are summed in float64 in a fixed order, as in the float32 path.
 //
-// One CTA computes one 128 x 128 tile (rows ti, columns tj of the upper
-// triangle) over a range of the other index c.  Stage t of a 4-slot
-// shared-memory ring holds KC = 32 values of c for the tile's 128 + 128 rows,
-// converted and stored K-major in the no-swizzle canonical layout: 8-row x
-// 16-byte core matrices, adjacent along K (LBO = 128 B), 8-row groups SBO
-// apart.  All 256 threads stage operands, with the next stage prefetched into
-// registers.  Thread 0 issues the MMAs of a stage and commits them to that
-// slot's mbarrier.  Before a slot is refilled, its previous MMAs must have
-// completed.  Every mbarrier wait is bounded: on timeout the CTA records
-// DEV_TIMEOUT, waits once more (bounded) for its MMAs, frees its TMEM and
-// returns.
+// Two kernels per Gram:
+//  1. pack: one pass over the view converts it into the MMA operand format and
+//     writes it in "blocks" of 128 rows x 128 bytes of K (16 KB per array),
+//     already in the tcgen05 K-major no-swizzle canonical layout: 8-row x
+//     16-byte core matrices, adjacent along K (LBO = 128 B), 8-row groups
+//     1024 B apart (SBO).  Rows beyond n and c beyond J are zero.  The
+//     transpose needed when the rows are the contiguous index (lo == 1) goes
+//     through shared memory, so both the reads and the writes are coalesced.
+//  2. gram: one CTA per (upper-triangle 128 x 128 tile, range of blocks).  One
+//     thread streams the A and B blocks with cp.async.bulk into a 3-slot ring
+//     (completion counted on the slot's "full" mbarrier); one thread issues the
+//     MMAs of a slot and commits them to its "empty" mbarrier; after the last
+//     slot a final commit releases the four epilogue warps, which move the
+//     accumulator from TMEM to the split's partial tile.  The tiles of one
+//     range run side by side (tile index fastest in the grid), so each block
+//     is read from HBM about once and re-read by its other tiles from L2.
+// Every mbarrier wait is bounded (a time limit on %globaltimer).  A loop that
+// gives up raises the CTA's abort flag and the device status DEV_TIMEOUT; the
+// producer then waits (bounded) for its copies in flight, the MMA thread
+// commits and waits (bounded) for its MMAs, and the CTA frees its TMEM and
+// returns with a zero partial.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -35,11 +46,15 @@ namespace atk {
 
 namespace tc {
 
-constexpr int BM = 128;       // tile rows = cols = MMA M = N
-constexpr int KC = 32;        // c values per stage
-constexpr int STAGES = 4;
-constexpr int THREADS = 256;
-constexpr long long WAIT_LIMIT = 50000000LL;
+constexpr int BM = 128;              // tile rows = cols = MMA M = N
+constexpr int KP = 128;              // c values per pack tile
+constexpr int ARRAY_BYTES = 16384;   // one block array: 128 rows x 128 bytes
+constexpr int STAGES = 3;            // ring slots of the gram kernel
+constexpr int GRAM_THREADS = 128;    // warp 0: producer + epilogue, warp 1: MMA + epilogue, 2-3: epilogue
+constexpr int PACK_THREADS = 256;
+constexpr int PACK_LD = KP + 1;      // shared-memory row pitch (floats) of the pack tile
+constexpr int SPLIT_MAX_TERMS = 8192;  // c values per float32 partial sum
+constexpr unsigned long long WAIT_NS = 2000000000ULL;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -49,14 +64,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// Byte offset of (row, kbyte) in the K-major no-swizzle canonical layout.
-__device__ __forceinline__ uint32_t koff(int row, int kbyte, uint32_t sbo) {
-  return (uint32_t)((row >> 3) * sbo + (kbyte >> 4) * 128 + (row & 7) * 16 + (kbyte & 15));
-}
-
 template <int P>
 struct Form;
-// Element bytes, bytes of one stage row, arrays per operand (hi[/lo]), MMA format code.
+// ES: element bytes; ARR: arrays per block (hi [, lo]); FMT: MMA operand format
+// code; KIND: 0 kind::f16, 1 kind::tf32, 2 kind::f8f6f4.
 template <>
 struct Form<ATK_TF32> {
   static constexpr int ES = 4, ARR = 1, FMT = 2, KIND = 1;
@@ -75,13 +86,11 @@ struct Form<ATK_FP8E4M3> {
 };
 
 template <int P>
-struct Stage {
-  static constexpr int ROWB = KC * Form<P>::ES;           // bytes of one row of one array
-  static constexpr uint32_t SBO = (ROWB / 16) * 128;      // bytes per 8-row group
-  static constexpr int ARRB = BM * ROWB;                  // bytes of one array (128 rows)
-  static constexpr int OPB = ARRB * Form<P>::ARR;         // one operand (hi [+ lo])
-  static constexpr int BYTES = 2 * OPB;                   // A and B
-  static constexpr int KSTEPS = ROWB / 32;                // MMAs (32 B of K each) per array pair
+struct Blk {
+  static constexpr int KB = 128 / Form<P>::ES;          // c values per block
+  static constexpr int PER_TILE = KP / KB;              // blocks per pack tile
+  static constexpr int BYTES = ARRAY_BYTES * Form<P>::ARR;
+  static constexpr int W = 16 / Form<P>::ES;            // values per 16-byte piece
 };
 
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc, int kind) {
@@ -99,127 +108,201 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
                  "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t done;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done)
-                 : "r"(bar), "r"(parity));
-    if (done) return true;
-  }
-  return false;
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-// Convert one float32 value into the stage arrays at byte offset `o`.
-template <int P>
-__device__ __forceinline__ void put(unsigned char* hi, unsigned char* lo, uint32_t o, float x) {
-  if (P == ATK_TF32) {
-    uint32_t t;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-    *reinterpret_cast<uint32_t*>(hi + o) = t;
-  } else if (P == ATK_BF16) {
-    *reinterpret_cast<__nv_bfloat16*>(hi + o) = __float2bfloat16_rn(x);
-  } else if (P == ATK_BF16X3) {
-    __nv_bfloat16 h = __float2bfloat16_rn(x);
-    *reinterpret_cast<__nv_bfloat16*>(hi + o) = h;
-    *reinterpret_cast<__nv_bfloat16*>(lo + o) = __float2bfloat16_rn(x - __bfloat162float(h));
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(done)
+               : "r"(bar), "r"(parity));
+  return done != 0;
+}
+
+// Wait for the phase of parity `parity` to complete.  Gives up after WAIT_NS,
+// or at once when `abort` is set (pass nullptr for a wait that must not be cut
+// short, such as a drain of work in flight).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (abort && *abort) return false;
+    if ((it & 63) == 0 && gtime() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void arrive_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Pack
+
+// Load the 128 (rows i0..) x 128 (c from c0) float32 tile of the view into
+// shared memory as sm[k * PACK_LD + r], zero outside the view.  Rows are the
+// contiguous index when lo == 1 (threads run along i), c is otherwise (threads
+// run along c, which is a within one b).
+__device__ __forceinline__ void load_tile(const float* __restrict__ y, int lo, int n, int64_t J, int i0, int64_t c0,
+                                          float* sm) {
+  const int t = threadIdx.x;
+  if (lo == 1) {
+    const int r = t % BM, kk = t / BM;
+    const int i = i0 + r;
+#pragma unroll 16
+    for (int e = 0; e < KP / 2; ++e) {
+      const int k = kk + 2 * e;
+      const int64_t c = c0 + k;
+      sm[k * PACK_LD + r] = (i < n && c < J) ? __ldg(y + ((int64_t)i + (int64_t)n * c)) : 0.f;
+    }
   } else {
-    *reinterpret_cast<__nv_fp8_e4m3*>(hi + o) = __nv_fp8_e4m3(x);
+    const int k = t % KP, r0 = t / KP;
+    const int64_t c = c0 + k;
+    const bool cv = c < J;
+    const int64_t a = cv ? c % lo : 0, b = cv ? c / lo : 0;
+    const float* base = y + (a + (int64_t)lo * n * b);
+#pragma unroll 16
+    for (int e = 0; e < BM / 2; ++e) {
+      const int r = r0 + 2 * e;
+      const int i = i0 + r;
+      sm[k * PACK_LD + r] = (cv && i < n) ? __ldg(base + (int64_t)lo * i) : 0.f;
+    }
   }
 }
 
-// Registers of one stage: 2 operands x 128 rows x KC values over 256 threads.
-// lo == 1 (rows contiguous): thread t owns row t % 128 and 16 consecutive c.
-// lo > 1  (c contiguous):    thread t owns c = t % 32 and 16 rows.
-struct StageRegs {
-  float a[16], b[16];
+// FP8 row scale from the row max: 2^(8 - e) with max in [2^(e-1), 2^e).
+__device__ __forceinline__ float fp8_row_scale(float m) {
+  if (!(m > 0.f)) return 1.f;
+  int e;
+  frexpf(m, &e);
+  e = min(max(8 - e, -126), 127);
+  return ldexpf(1.f, e);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <int P>
+__global__ void __launch_bounds__(PACK_THREADS) tc_pack_kernel(const float* __restrict__ y, int lo, int n, int64_t J,
+                                                               int64_t nkb, const float* __restrict__ rmax,
+                                                               unsigned char* __restrict__ out) {
+  using B = Blk<P>;
+  extern __shared__ float sm[];
+  const int ti = blockIdx.y;
+  const int64_t c0 = (int64_t)blockIdx.x * KP;
+  load_tile(y, lo, n, J, ti * BM, c0, sm);
+  __syncthreads();
+  // Pieces: 16 bytes = W consecutive c of one row.  Piece pp of a block array
+  // sits at byte 16 pp: 8-row group g = pp / 64, core matrix along K cm =
+  // (pp / 8) % 8, row within the group pp % 8.
+  constexpr int PIECES = B::PER_TILE * 1024;
+  for (int p = threadIdx.x; p < PIECES; p += PACK_THREADS) {
+    const int bk = p / 1024, pp = p % 1024;
+    const int row = (pp / 64) * 8 + (pp % 8);
+    const int k0 = bk * B::KB + ((pp / 8) % 8) * B::W;
+    const float* src = sm + k0 * PACK_LD + row;
+    unsigned char* dst = out + ((int64_t)ti * nkb + (int64_t)blockIdx.x * B::PER_TILE + bk) * B::BYTES + 16 * pp;
+    if (P == ATK_TF32) {
+      uint4 v;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v.x) : "f"(src[0]));
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v.y) : "f"(src[PACK_LD]));
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v.z) : "f"(src[2 * PACK_LD]));
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v.w) : "f"(src[3 * PACK_LD]));
+      *reinterpret_cast<uint4*>(dst) = v;
+    } else if (P == ATK_BF16 || P == ATK_BF16X3) {
+      float x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = src[j * PACK_LD];
+      uint4 h;
+      h.x = pack_bf16x2(x[0], x[1]);
+      h.y = pack_bf16x2(x[2], x[3]);
+      h.z = pack_bf16x2(x[4], x[5]);
+      h.w = pack_bf16x2(x[6], x[7]);
+      *reinterpret_cast<uint4*>(dst) = h;
+      if (P == ATK_BF16X3) {
+        const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+        uint32_t lw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float h0 = __uint_as_float(hw[q] << 16), h1 = __uint_as_float(hw[q] & 0xFFFF0000u);
+          lw[q] = pack_bf16x2(x[2 * q] - h0, x[2 * q + 1] - h1);
+        }
+        *reinterpret_cast<uint4*>(dst + ARRAY_BYTES) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+    } else {
+      const float s = fp8_row_scale(ti * BM + row < n ? rmax[ti * BM + row] : 0.f);
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_fp8x2_storage_t lo2 = __nv_cvt_float2_to_fp8x2(
+            make_float2(src[(4 * q) * PACK_LD] * s, src[(4 * q + 1) * PACK_LD] * s), __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8x2_storage_t hi2 = __nv_cvt_float2_to_fp8x2(
+            make_float2(src[(4 * q + 2) * PACK_LD] * s, src[(4 * q + 3) * PACK_LD] * s), __NV_SATFINITE, __NV_E4M3);
+        w[q] = (uint32_t)lo2 | ((uint32_t)hi2 << 16);
+      }
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// Row maxima of |y| for the FP8 scales: the same tiles as the pack, one
+// atomicMax per row and tile (non-negative floats order like their bits).
+__global__ void __launch_bounds__(PACK_THREADS) tc_rowmax_kernel(const float* __restrict__ y, int lo, int n,
+                                                                 int64_t J, int* __restrict__ rmax_bits) {
+  extern __shared__ float sm[];
+  const int i0 = blockIdx.y * BM;
+  load_tile(y, lo, n, J, i0, (int64_t)blockIdx.x * KP, sm);
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < BM && i0 + r < n) {
+    float m = 0.f;
+    for (int k = 0; k < KP; ++k) m = fmaxf(m, fabsf(sm[k * PACK_LD + r]));
+    atomicMax(rmax_bits + i0 + r, __float_as_int(m));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram
+
+template <int P>
+struct Ring {
+  static constexpr int SLOT = 2 * Blk<P>::BYTES;  // A and B blocks
+  static constexpr int BYTES = STAGES * SLOT;
 };
 
-template <bool TWO>
-__device__ __forceinline__ void fetch_stage(const float* __restrict__ y, int lo, int n, int c_end, int i0a, int i0b,
-                                            int c0, const float* __restrict__ rscale, StageRegs& r) {
-  const int t = threadIdx.x;
-  if (lo == 1) {
-    const int row = t % BM, kg = (t / BM) * 16;
-    const int ia = i0a + row, ib = i0b + row;
-    const float sa = (rscale && ia < n) ? rscale[ia] : 1.f;
-    const float sb = (rscale && ib < n) ? rscale[ib] : 1.f;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int c = c0 + kg + e;
-      const bool cv = c < c_end;
-      r.a[e] = (cv && ia < n) ? __ldg(y + (ia + n * c)) * sa : 0.f;
-      if (TWO) r.b[e] = (cv && ib < n) ? __ldg(y + (ib + n * c)) * sb : 0.f;
-    }
-  } else {
-    const int kk = t % KC, rg = t / KC;  // rg in [0, 8)
-    const int c = c0 + kk;
-    const bool cv = c < c_end;
-    const int ca = cv ? c % lo : 0, cb = cv ? c / lo : 0;
-    const float* base = y + (ca + lo * n * cb);
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int row = rg + 8 * e;
-      const int ia = i0a + row, ib = i0b + row;
-      r.a[e] = (cv && ia < n) ? __ldg(base + lo * ia) * (rscale ? rscale[ia] : 1.f) : 0.f;
-      if (TWO) r.b[e] = (cv && ib < n) ? __ldg(base + lo * ib) * (rscale ? rscale[ib] : 1.f) : 0.f;
-    }
-  }
-}
-
-template <int P, bool TWO>
-__device__ __forceinline__ void store_stage(unsigned char* st, int lo, const StageRegs& r) {
-  using SG = Stage<P>;
-  constexpr int ES = Form<P>::ES;
-  unsigned char* ahi = st;
-  unsigned char* alo = st + SG::ARRB;
-  unsigned char* bhi = st + SG::OPB;
-  unsigned char* blo = st + SG::OPB + SG::ARRB;
-  const int t = threadIdx.x;
-  if (lo == 1) {
-    const int row = t % BM, kg = (t / BM) * 16;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const uint32_t o = koff(row, (kg + e) * ES, SG::SBO);
-      put<P>(ahi, alo, o, r.a[e]);
-      if (TWO) put<P>(bhi, blo, o, r.b[e]);
-    }
-  } else {
-    const int kk = t % KC, rg = t / KC;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const uint32_t o = koff(rg + 8 * e, kk * ES, SG::SBO);
-      put<P>(ahi, alo, o, r.a[e]);
-      if (TWO) put<P>(bhi, blo, o, r.b[e]);
-    }
-  }
-}
-
-// One Gram tile (ti, tj) over c in [split * kc, min(J, (split + 1) * kc)).
-template <int P, bool DIAG>
-__global__ void __launch_bounds__(THREADS) tc_gram_kernel(const float* __restrict__ y, int lo, int n, int hi, int T,
-                                                          int kc, const float* __restrict__ rscale,
-                                                          float* __restrict__ part, int* __restrict__ status) {
-  using SG = Stage<P>;
+// Tile blockIdx.x (row-major upper triangle of the T x T tile grid) over
+// blocks [split * kbps, min(nkb, (split + 1) * kbps)).
+template <int P>
+__global__ void __launch_bounds__(GRAM_THREADS) tc_gram_kernel(const unsigned char* __restrict__ packed, int T,
+                                                               int64_t nkb, int kbps, float* __restrict__ part,
+                                                               int* __restrict__ status) {
+  using B = Blk<P>;
+  using RG = Ring<P>;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t bars[STAGES];
-  __shared__ int failed;
-  const int tid = threadIdx.x, warp = tid / 32;
-  const int split = blockIdx.y;
-  int ti, tj;
-  if (DIAG) {
-    ti = tj = blockIdx.x;
-  } else {
-    int id = blockIdx.x;
-    ti = 0;
-    while (id >= T - 1 - ti) { id -= T - 1 - ti; ++ti; }
-    tj = ti + 1 + id;
-  }
-  const int tile = ti * T - ti * (ti - 1) / 2 + (tj - ti);
-  const int J = lo * hi;
-  const int cb = split * kc, ce = min(J, cb + kc);
-  const int nst = cb < ce ? (ce - cb + KC - 1) / KC : 0;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int tile = blockIdx.x, split = blockIdx.y;
+  int ti = 0, id = tile;
+  while (id >= T - ti) { id -= T - ti; ++ti; }
+  const int tj = ti + id;
+  const bool diag = ti == tj;
+  const int64_t kb0 = (int64_t)split * kbps;
+  const int64_t kend = kb0 + kbps < nkb ? kb0 + kbps : nkb;
+  const int nst = kend > kb0 ? (int)(kend - kb0) : 0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -227,87 +310,104 @@ __global__ void __launch_bounds__(THREADS) tc_gram_kernel(const float* __restric
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    failed = 0;
-    for (int s = 0; s < STAGES; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[s])), "r"(1));
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(1));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  constexpr uint32_t idesc = (1u << 4) | ((uint32_t)Form<P>::FMT << 7) | ((uint32_t)Form<P>::FMT << 10) |
-                             ((uint32_t)(BM >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-  const int i0a = ti * BM, i0b = tj * BM;
+  const uint32_t sbase = smem_u32(smem);
+  bool ok = true;
 
-  StageRegs regs;
-  int last = -1;  // last stage whose MMAs were committed
-  if (nst > 0) fetch_stage<!DIAG>(y, lo, n, ce, i0a, i0b, cb, rscale, regs);
-  for (int s = 0; s < nst; ++s) {
-    const int slot = s % STAGES;
-    unsigned char* st = smem + slot * SG::BYTES;
-    if (s >= STAGES) {
-      // the MMAs that last read this slot (stage s - STAGES) must be done
-      if (!mbar_wait(smem_u32(&bars[slot]), (uint32_t)(((s / STAGES) - 1) & 1))) failed = 1;
-      __syncthreads();
-      if (failed) break;
+  if (warp == 0 && lane == 0) {
+    // Producer.
+    const unsigned char* pa = packed + ((int64_t)ti * nkb + kb0) * B::BYTES;
+    const unsigned char* pb = packed + ((int64_t)tj * nkb + kb0) * B::BYTES;
+    const uint32_t bytes = diag ? B::BYTES : 2 * B::BYTES;
+    int issued = 0;
+    for (int s = 0; s < nst; ++s) {
+      const int slot = s % STAGES;
+      if (s >= STAGES && !mbar_wait(smem_u32(&empty[slot]), (uint32_t)(((s / STAGES) - 1) & 1), &abort_flag)) {
+        ok = false;
+        break;
+      }
+      const uint32_t dst = sbase + slot * RG::SLOT, bar = smem_u32(&full[slot]);
+      arrive_expect(bar, bytes);
+      bulk_load(dst, pa + (int64_t)s * B::BYTES, B::BYTES, bar);
+      if (!diag) bulk_load(dst + B::BYTES, pb + (int64_t)s * B::BYTES, B::BYTES, bar);
+      issued = s + 1;
     }
-    store_stage<P, !DIAG>(st, lo, regs);
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (s + 1 < nst) fetch_stage<!DIAG>(y, lo, n, ce, i0a, i0b, cb + (s + 1) * KC, rscale, regs);
-    if (tid == 0) {
+    // Drain: the last copy issued into each slot has landed.
+    for (int s = issued > STAGES ? issued - STAGES : 0; s < issued; ++s)
+      if (!mbar_wait(smem_u32(&full[s % STAGES]), (uint32_t)((s / STAGES) & 1), nullptr)) ok = false;
+    if (!ok) abort_flag = 1;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer.
+    constexpr uint32_t idesc = (1u << 4) | ((uint32_t)Form<P>::FMT << 7) | ((uint32_t)Form<P>::FMT << 10) |
+                               ((uint32_t)(BM >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    for (int s = 0; s < nst; ++s) {
+      const int slot = s % STAGES;
+      if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)((s / STAGES) & 1), &abort_flag)) {
+        ok = false;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(st), b0 = DIAG ? a0 : smem_u32(st + SG::OPB);
+      const uint32_t a0 = sbase + slot * RG::SLOT, b0 = diag ? a0 : a0 + B::BYTES;
 #pragma unroll
-      for (int j = 0; j < SG::KSTEPS; ++j) {
+      for (int j = 0; j < 4; ++j) {  // 4 MMAs of 32 bytes of K each per 128-byte array row
         const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
         const uint32_t off = j * 256;
-        mma(tmem, sdesc(a0 + off, 128, SG::SBO), sdesc(b0 + off, 128, SG::SBO), idesc, acc, Form<P>::KIND);
+        mma(tmem, sdesc(a0 + off, 128, 1024), sdesc(b0 + off, 128, 1024), idesc, acc, Form<P>::KIND);
         if (P == ATK_BF16X3) {
-          const uint32_t al = a0 + SG::ARRB, bl = b0 + SG::ARRB;
-          mma(tmem, sdesc(a0 + off, 128, SG::SBO), sdesc(bl + off, 128, SG::SBO), idesc, 1u, 0);
-          mma(tmem, sdesc(al + off, 128, SG::SBO), sdesc(b0 + off, 128, SG::SBO), idesc, 1u, 0);
+          const uint32_t al = a0 + ARRAY_BYTES, bl = b0 + ARRAY_BYTES;
+          mma(tmem, sdesc(a0 + off, 128, 1024), sdesc(bl + off, 128, 1024), idesc, 1u, 0);
+          mma(tmem, sdesc(al + off, 128, 1024), sdesc(b0 + off, 128, 1024), idesc, 1u, 0);
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&bars[slot])));
+          smem_u32(&empty[slot])));
     }
-    last = s;
+    if (!ok) abort_flag = 1;
+    // A commit tracks every MMA this thread issued before it.
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(&done)));
   }
-  // Wait for the last committed stage; a commit covers every MMA the thread
-  // issued before it, so this drains all of them.
-  bool ok = !failed;
-  if (last >= 0) {
-    bool done = mbar_wait(smem_u32(&bars[last % STAGES]), (uint32_t)((last / STAGES) & 1));
-    if (!done) done = mbar_wait(smem_u32(&bars[last % STAGES]), (uint32_t)((last / STAGES) & 1));
-    ok = ok && done;
-  }
-  if (!ok && tid == 0) atomicOr(status, DEV_TIMEOUT);
+  __syncwarp();
+  // Epilogue: every thread waits for the final commit (never cut short).
+  if (!mbar_wait(smem_u32(&done), 0u, nullptr)) ok = false;
+  if (!ok) abort_flag = 1;
   asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  const bool failed = abort_flag != 0;
+  const bool good = !failed && nst > 0;
+  if (failed && tid == 0) atomicOr(status, DEV_TIMEOUT);
   const int ntiles = T * (T + 1) / 2;
-  float* out = part + ((size_t)split * ntiles + tile) * (BM * BM);
-  // Epilogue: warp w reads lanes 32 (w % 4) .. +31, columns 64 (w / 4) .. +63.
-  const int q = warp % 4, h = warp / 4;
-  const int row = 32 * q + (tid % 32);
-#pragma unroll
-  for (int c0 = 0; c0 < 64; c0 += 16) {
+  float* out = part + ((int64_t)split * ntiles + tile) * (BM * BM);
+  const int row = 32 * warp + lane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BM; c0 += 16) {
     uint32_t r[16];
-    const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h + c0);
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;");
-    float4* o4 = reinterpret_cast<float4*>(out + (size_t)row * BM + 64 * h + c0);
+    float4* o4 = reinterpret_cast<float4*>(out + (int64_t)row * BM + c0);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       float4 f;
-      f.x = (ok && last >= 0) ? __uint_as_float(r[4 * v + 0]) : 0.f;
-      f.y = (ok && last >= 0) ? __uint_as_float(r[4 * v + 1]) : 0.f;
-      f.z = (ok && last >= 0) ? __uint_as_float(r[4 * v + 2]) : 0.f;
-      f.w = (ok && last >= 0) ? __uint_as_float(r[4 * v + 3]) : 0.f;
+      f.x = good ? __uint_as_float(r[4 * v + 0]) : 0.f;
+      f.y = good ? __uint_as_float(r[4 * v + 1]) : 0.f;
+      f.z = good ? __uint_as_float(r[4 * v + 2]) : 0.f;
+      f.w = good ? __uint_as_float(r[4 * v + 3]) : 0.f;
       o4[v] = f;
     }
   }
@@ -316,33 +416,10 @@ __global__ void __launch_bounds__(THREADS) tc_gram_kernel(const float* __restric
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BM));
 }
 
-// Row scales for FP8: s_i = 2^floor(log2(448 / max_c |y_ic|)) (1 for an all-zero row).
-// One CTA per row i; the view's c runs over (a, b) pairs.
-__global__ void rowscale_kernel(const float* __restrict__ y, int lo, int n, int hi, float* __restrict__ scale) {
-  __shared__ float red[256];
-  const int i = blockIdx.x;
-  float m = 0.f;
-  const int J = lo * hi;
-  for (int c = threadIdx.x; c < J; c += blockDim.x) {
-    const int a = c % lo, b = c / lo;
-    m = fmaxf(m, fabsf(y[a + lo * (i + n * b)]));
-  }
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    float mx = red[0];
-    scale[i] = mx > 0.f ? exp2f(floorf(log2f(448.f / mx))) : 1.f;
-  }
-}
-
-// Float64 reduction of the split partials (diagonal tiles ns_d splits,
-// off-diagonal ns_o), with the optional FP8 row scales undone exactly.
-__global__ void tc_reduce_sym_kernel(const float* __restrict__ part, int ns_d, int ns_o, int ntiles, int T, int n,
-                                     const float* __restrict__ rscale, double* __restrict__ C) {
+// Float64 reduction of the split partials, with the optional FP8 row scales
+// (from the row maxima) undone exactly.
+__global__ void tc_reduce_sym_kernel(const float* __restrict__ part, int ns, int ntiles, int T, int n,
+                                     const float* __restrict__ rmax, double* __restrict__ C) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * n) return;
   const int i = (int)(idx / n), j = (int)(idx % n);
@@ -350,68 +427,62 @@ __global__ void tc_reduce_sym_kernel(const float* __restrict__ part, int ns_d, i
   const int ti = i / BM, tj = j / BM;
   const int id = ti * T - ti * (ti - 1) / 2 + (tj - ti);
   const int64_t o = (int64_t)(i - ti * BM) * BM + (j - tj * BM);
-  const int ns = ti == tj ? ns_d : ns_o;
   double s = 0.0;
   for (int sp = 0; sp < ns; ++sp) s += (double)part[((int64_t)sp * ntiles + id) * BM * BM + o];
-  if (rscale) s /= (double)rscale[i] * (double)rscale[j];
+  if (rmax) s /= (double)fp8_row_scale(rmax[i]) * (double)fp8_row_scale(rmax[j]);
   C[i + (int64_t)n * j] = s;
   C[j + (int64_t)n * i] = s;
 }
 
-struct TcSplit {
-  int nsplit, kc;
-};
-TcSplit tc_split(int64_t J, int ntiles, int slots) {
-  // Each partial sum stays within 8192 terms of float32 accumulation, and the
-  // launch fills whole waves.
-  const int64_t min_split = ceil_div(J, 8192);
-  const int64_t waves = std::max<int64_t>(1, ceil_div(min_split * ntiles, slots));
-  int64_t ns = std::max<int64_t>(min_split, (waves * slots) / ntiles);
-  ns = std::min<int64_t>(ns, std::max<int64_t>(1, ceil_div(J, KC)));
-  int64_t kc = ceil_div(ceil_div(J, ns), KC) * KC;
-  ns = ceil_div(J, kc);
-  return {(int)std::max<int64_t>(1, ns), (int)kc};
-}
-
 template <int P>
-int stage_bytes() {
-  return STAGES * Stage<P>::BYTES;
-}
-
-template <int P>
-int slots_per_sm() {
-  int per = 0;
-  // Requested shared memory also caps residency at 4 CTAs (TMEM: 4 x 128 columns).
-  size_t sm = std::max<size_t>((size_t)stage_bytes<P>(), 57 * 1024);
-  cudaFuncSetAttribute(tc_gram_kernel<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(tc_gram_kernel<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tc_gram_kernel<P, false>, THREADS, sm);
-  return std::max(1, std::min(per, 4));
+int gram_ctas_per_sm() {
+  static int per = -1;  // depends only on the kernel and the device
+  if (per < 0) {
+    cudaFuncSetAttribute(tc_gram_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Ring<P>::BYTES);
+    cudaFuncSetAttribute(tc_pack_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(KP * PACK_LD * sizeof(float)));
+    int v = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, tc_gram_kernel<P>, GRAM_THREADS, Ring<P>::BYTES);
+    per = std::max(1, std::min(v, 4));  // TMEM: 4 x 128 columns
+  }
+  return per;
 }
 
 struct TcPlan {
   int T, nt;
-  TcSplit d, o;
-  size_t smem;
+  int64_t nkp, nkb;  // pack tiles and blocks along c
+  int ns, kbps;      // splits and blocks per split
+  size_t part_bytes, packed_bytes;
 };
 
 template <int P>
 TcPlan tc_plan(const View& v) {
+  using B = Blk<P>;
   TcPlan g;
   g.T = (int)ceil_div(v.n, BM);
   g.nt = g.T * (g.T + 1) / 2;
-  const int slots = slots_per_sm<P>() * num_sms();
-  g.d = tc_split(v.J(), g.T, slots);
-  g.o = g.T > 1 ? tc_split(v.J(), g.T * (g.T - 1) / 2, slots) : g.d;
-  g.smem = std::max<size_t>((size_t)stage_bytes<P>(), 57 * 1024);
+  g.nkp = ceil_div(v.J(), KP);
+  g.nkb = g.nkp * B::PER_TILE;
+  // Each partial sum stays within SPLIT_MAX_TERMS values of c, and the launch
+  // fills whole waves of resident CTAs.
+  const int64_t slots = (int64_t)gram_ctas_per_sm<P>() * num_sms();
+  const int64_t max_kb = SPLIT_MAX_TERMS / B::KB;
+  const int64_t min_split = ceil_div(g.nkb, max_kb);
+  const int64_t waves = std::max<int64_t>(1, ceil_div(min_split * g.nt, slots));
+  int64_t ns = std::max<int64_t>(min_split, (waves * slots) / g.nt);
+  ns = std::min<int64_t>(ns, g.nkb);
+  const int64_t kbps = ceil_div(g.nkb, ns);
+  g.kbps = (int)kbps;
+  g.ns = (int)ceil_div(g.nkb, kbps);
+  g.part_bytes = (size_t)g.ns * g.nt * BM * BM * sizeof(float);
+  g.packed_bytes = (size_t)g.T * g.nkb * B::BYTES;
   return g;
 }
 
 template <int P>
 size_t tc_scratch_t(const View& v) {
   TcPlan g = tc_plan<P>(v);
-  return (size_t)std::max(g.d.nsplit, g.o.nsplit) * g.nt * BM * BM * sizeof(float) + (size_t)v.n * sizeof(float) +
-         256;
+  return g.part_bytes + g.packed_bytes + (size_t)v.n * sizeof(float) + 3 * 256;
 }
 
 template <int P>
@@ -422,23 +493,27 @@ int tc_gram_t(const float* y, const View& v, double* S, float* scratch, size_t s
     set_error("tc_gram: scratch too small");
     return ATK_EINVAL;
   }
-  float* part = scratch;
-  float* rscale = nullptr;
+  Arena ar{reinterpret_cast<char*>(scratch), scratch_bytes, 0};
+  float* part = reinterpret_cast<float*>(ar.take(g.part_bytes));
+  unsigned char* packed = reinterpret_cast<unsigned char*>(ar.take(g.packed_bytes));
+  float* rmax = nullptr;
+  const size_t pack_smem = (size_t)KP * PACK_LD * sizeof(float);
+  const dim3 pgrid((unsigned)g.nkp, (unsigned)g.T);
   if (P == ATK_FP8E4M3) {
-    rscale = scratch + (size_t)std::max(g.d.nsplit, g.o.nsplit) * g.nt * BM * BM;
-    rowscale_kernel<<<(unsigned)v.n, 256, 0, st>>>(y, (int)v.lo, (int)v.n, (int)v.hi, rscale);
+    rmax = reinterpret_cast<float*>(ar.take((size_t)v.n * sizeof(float)));
+    ATK_CUDA(cudaMemsetAsync(rmax, 0, (size_t)v.n * sizeof(float), st));
+    cudaFuncSetAttribute(tc_rowmax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pack_smem);
+    tc_rowmax_kernel<<<pgrid, PACK_THREADS, pack_smem, st>>>(y, (int)v.lo, (int)v.n, v.J(),
+                                                            reinterpret_cast<int*>(rmax));
     ATK_LAUNCHED();
   }
-  tc_gram_kernel<P, true><<<dim3(g.T, g.d.nsplit), THREADS, g.smem, st>>>(y, (int)v.lo, (int)v.n, (int)v.hi, g.T,
-                                                                            g.d.kc, rscale, part, status);
+  tc_pack_kernel<P><<<pgrid, PACK_THREADS, pack_smem, st>>>(y, (int)v.lo, (int)v.n, v.J(), g.nkb, rmax, packed);
   ATK_LAUNCHED();
-  if (g.T > 1) {
-    tc_gram_kernel<P, false><<<dim3(g.T * (g.T - 1) / 2, g.o.nsplit), THREADS, g.smem, st>>>(
-        y, (int)v.lo, (int)v.n, (int)v.hi, g.T, g.o.kc, rscale, part, status);
-    ATK_LAUNCHED();
-  }
-  tc_reduce_sym_kernel<<<(unsigned)ceil_div(v.n * v.n, 256), 256, 0, st>>>(part, g.d.nsplit, g.o.nsplit, g.nt, g.T,
-                                                                            (int)v.n, rscale, S);
+  tc_gram_kernel<P><<<dim3(g.nt, g.ns), GRAM_THREADS, Ring<P>::BYTES, st>>>(packed, g.T, g.nkb, g.kbps, part,
+                                                                            status);
+  ATK_LAUNCHED();
+  tc_reduce_sym_kernel<<<(unsigned)ceil_div(v.n * v.n, 256), 256, 0, st>>>(part, g.ns, g.nt, g.T, (int)v.n, rmax,
+                                                                          S);
   ATK_LAUNCHED();
   return ATK_OK;
 }
