@@ -62,6 +62,23 @@ long long launch_count();
 // Device status word bits (written by kernels, read by atucker_plan_sync).
 enum : int { DEV_NOCONV = 1, DEV_TIMEOUT = 2, DEV_CHOL = 4 };
 
+// ------------------------------------------------------------ float-float sum
+// Fixed-order sum of float32 terms carried as an unevaluated pair hi + lo
+// (Knuth's TwoSum makes each hi update exact; lo collects the errors).  The
+// relative error is about (terms) * 2^-48, far below the float32 partials'
+// own rounding, and it runs on the float32 pipe: B300's float64 pipe issues
+// about two operations per clock per SM.  Converted to float64 once.
+struct FFSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = hi + v;
+    const float bp = t - hi;
+    lo += (hi - (t - bp)) + (v - bp);
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // ------------------------------------------------------------ grid barrier
 // Sense-reversing barrier across the CTAs of a cooperative launch.  Every wait
 // is bounded: after `limit` polls the CTA sets DEV_TIMEOUT in *status and

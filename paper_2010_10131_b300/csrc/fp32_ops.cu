@@ -14,8 +14,9 @@
 // the stride view.  Lanes run along whichever index is contiguous in memory:
 // i when lo == 1, c otherwise.  So no unfolding is ever materialised.
 // CI outputs are split over c (split-K) into float32 partial tiles.  A second
-// kernel sums them in float64 in a fixed order, so results are deterministic
-// and no float32 sum runs longer than one split (<= 8192 terms).
+// kernel sums them in a fixed order as float-float pairs (about 48 bits),
+// rounded once to float64, so results are deterministic and no plain float32
+// sum runs longer than one split (<= 8192 terms).
 #include <algorithm>
 
 #include "atk_internal.cuh"
@@ -335,7 +336,8 @@ cross_ci_kernel(const float* __restrict__ y, const float* __restrict__ p, int64_
           blk.acc[u][v];
 }
 
-// Sum the split-K partial tiles in float64, in split order (deterministic).
+// Sum the split-K partial tiles in split order (deterministic), as a
+// float-float pair rounded once to float64.
 // sym: C is n x n from upper-triangle tiles (T x T grid of BM tiles); diagonal
 // tiles have ns_d splits, off-diagonal tiles ns_o.
 __global__ void reduce_sym_kernel(const float* __restrict__ part, int ns_d, int ns_o, int ntiles, int T, int BM,
@@ -348,8 +350,9 @@ __global__ void reduce_sym_kernel(const float* __restrict__ part, int ns_d, int 
   int id = ti * T - ti * (ti - 1) / 2 + (tj - ti);
   int64_t o = (i - (int64_t)ti * BM) * BM + (j - (int64_t)tj * BM);
   const int nsplit = ti == tj ? ns_d : ns_o;
-  double s = 0.0;
-  for (int sp = 0; sp < nsplit; ++sp) s += (double)part[((int64_t)sp * ntiles + id) * BM * BM + o];
+  FFSum acc;
+  for (int sp = 0; sp < nsplit; ++sp) acc.add(part[((int64_t)sp * ntiles + id) * BM * BM + o]);
+  const double s = acc.value();
   C[i + n * j] = s;
   C[j + n * i] = s;
 }
@@ -362,9 +365,9 @@ __global__ void reduce_cross_kernel(const float* __restrict__ part, int nsplit, 
   int ti = (int)(i / BM), tr = (int)(r / BN);
   int id = ti * TR + tr;
   int64_t o = (i - (int64_t)ti * BM) * BN + (r - (int64_t)tr * BN);
-  double s = 0.0;
-  for (int sp = 0; sp < nsplit; ++sp) s += (double)part[((int64_t)sp * ntiles + id) * BM * BN + o];
-  C[i + n * r] = s;
+  FFSum acc;
+  for (int sp = 0; sp < nsplit; ++sp) acc.add(part[((int64_t)sp * ntiles + id) * BM * BN + o]);
+  C[i + n * r] = acc.value();
 }
 
 // ------------------------------------------------------------- CO kernel

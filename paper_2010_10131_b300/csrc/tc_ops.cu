@@ -12,7 +12,7 @@
 //           so every scaled value is below 256 < 448; rounded to e4m3,
 //           kind::f8f6f4; the reduction multiplies S_ij by 1 / (s_i s_j) exactly.
 // Every form accumulates in float32 in tensor memory (TMEM).  Split-K partial
-// tiles are summed in float64 in a fixed order, as in the float32 path.
+// tiles are summed in a fixed order as float-float pairs, as in the float32 path.
 //
 // Two kernels per Gram:
 //  1. pack: one pass over the view converts it into the MMA operand format and
@@ -47,12 +47,13 @@ namespace atk {
 namespace tc {
 
 constexpr int BM = 128;              // tile rows = cols = MMA M = N
-constexpr int KP = 128;              // c values per pack tile
+constexpr int KP = 64;               // c values per pack tile
+constexpr int CPAD = 128;            // the packed c extent is a multiple of this (one FP8 block)
 constexpr int ARRAY_BYTES = 16384;   // one block array: 128 rows x 128 bytes
 constexpr int STAGES = 3;            // ring slots of the gram kernel
 constexpr int GRAM_THREADS = 128;    // warp 0: producer + epilogue, warp 1: MMA + epilogue, 2-3: epilogue
 constexpr int PACK_THREADS = 256;
-constexpr int PACK_LD = KP + 1;      // shared-memory row pitch (floats) of the pack tile
+constexpr int PACK_LD = BM + 1;      // shared-memory pitch (floats) between the tile's c values
 constexpr int SPLIT_MAX_TERMS = 8192;  // c values per float32 partial sum
 constexpr unsigned long long WAIT_NS = 2000000000ULL;  // 2 s per wait
 
@@ -88,7 +89,6 @@ struct Form<ATK_FP8E4M3> {
 template <int P>
 struct Blk {
   static constexpr int KB = 128 / Form<P>::ES;          // c values per block
-  static constexpr int PER_TILE = KP / KB;              // blocks per pack tile
   static constexpr int BYTES = ARRAY_BYTES * Form<P>::ARR;
   static constexpr int W = 16 / Form<P>::ES;            // values per 16-byte piece
 };
@@ -149,7 +149,7 @@ __device__ __forceinline__ void arrive_expect(uint32_t bar, uint32_t bytes) {
 // ---------------------------------------------------------------------------
 // Pack
 
-// Load the 128 (rows i0..) x 128 (c from c0) float32 tile of the view into
+// Load the 128 (rows i0..) x KP (c from c0) float32 tile of the view into
 // shared memory as sm[k * PACK_LD + r], zero outside the view.  Rows are the
 // contiguous index when lo == 1 (threads run along i), c is otherwise (threads
 // run along c, which is a within one b).
@@ -159,9 +159,9 @@ __device__ __forceinline__ void load_tile(const float* __restrict__ y, int lo, i
   if (lo == 1) {
     const int r = t % BM, kk = t / BM;
     const int i = i0 + r;
-#pragma unroll 16
-    for (int e = 0; e < KP / 2; ++e) {
-      const int k = kk + 2 * e;
+#pragma unroll
+    for (int e = 0; e < KP * BM / PACK_THREADS; ++e) {
+      const int k = kk + (PACK_THREADS / BM) * e;
       const int64_t c = c0 + k;
       sm[k * PACK_LD + r] = (i < n && c < J) ? __ldg(y + ((int64_t)i + (int64_t)n * c)) : 0.f;
     }
@@ -171,9 +171,9 @@ __device__ __forceinline__ void load_tile(const float* __restrict__ y, int lo, i
     const bool cv = c < J;
     const int64_t a = cv ? c % lo : 0, b = cv ? c / lo : 0;
     const float* base = y + (a + (int64_t)lo * n * b);
-#pragma unroll 16
-    for (int e = 0; e < BM / 2; ++e) {
-      const int r = r0 + 2 * e;
+#pragma unroll
+    for (int e = 0; e < KP * BM / PACK_THREADS; ++e) {
+      const int r = r0 + (PACK_THREADS / KP) * e;
       const int i = i0 + r;
       sm[k * PACK_LD + r] = (cv && i < n) ? __ldg(base + (int64_t)lo * i) : 0.f;
     }
@@ -204,16 +204,22 @@ __global__ void __launch_bounds__(PACK_THREADS) tc_pack_kernel(const float* __re
   const int64_t c0 = (int64_t)blockIdx.x * KP;
   load_tile(y, lo, n, J, ti * BM, c0, sm);
   __syncthreads();
-  // Pieces: 16 bytes = W consecutive c of one row.  Piece pp of a block array
-  // sits at byte 16 pp: 8-row group g = pp / 64, core matrix along K cm =
-  // (pp / 8) % 8, row within the group pp % 8.
-  constexpr int PIECES = B::PER_TILE * 1024;
-  for (int p = threadIdx.x; p < PIECES; p += PACK_THREADS) {
-    const int bk = p / 1024, pp = p % 1024;
-    const int row = (pp / 64) * 8 + (pp % 8);
-    const int k0 = bk * B::KB + ((pp / 8) % 8) * B::W;
-    const float* src = sm + k0 * PACK_LD + row;
-    unsigned char* dst = out + ((int64_t)ti * nkb + (int64_t)blockIdx.x * B::PER_TILE + bk) * B::BYTES + 16 * pp;
+  // Pieces: 16 bytes = W consecutive c of one row.  In a block array, the
+  // piece of row 8 g + r8 and core-matrix column cm (c values W cm .. W cm +
+  // W - 1 of the block) sits at byte 1024 g + 128 cm + 16 r8.  Consecutive
+  // threads take consecutive r8, then piece columns, then g, so each warp
+  // writes whole 128-byte runs.
+  constexpr int PCOLS = KP / B::W;  // piece columns per tile row
+  const int64_t pcol0 = c0 / B::W;  // first piece column of the tile along c
+#pragma unroll
+  for (int it = 0; it < BM * PCOLS / PACK_THREADS; ++it) {
+    const int q = threadIdx.x + it * PACK_THREADS;
+    const int r8 = q % 8, lp = (q / 8) % PCOLS, g = q / (8 * PCOLS);
+    const int row = 8 * g + r8;
+    const int64_t pc = pcol0 + lp;
+    const float* src = sm + (lp * B::W) * PACK_LD + row;
+    unsigned char* dst =
+        out + ((int64_t)ti * nkb + pc / 8) * B::BYTES + 1024 * g + 128 * (int)(pc % 8) + 16 * r8;
     if (P == ATK_TF32) {
       uint4 v;
       asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v.x) : "f"(src[0]));
@@ -416,19 +422,34 @@ __global__ void __launch_bounds__(GRAM_THREADS) tc_gram_kernel(const unsigned ch
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BM));
 }
 
-// Float64 reduction of the split partials, with the optional FP8 row scales
-// (from the row maxima) undone exactly.
-__global__ void tc_reduce_sym_kernel(const float* __restrict__ part, int ns, int ntiles, int T, int n,
-                                     const float* __restrict__ rmax, double* __restrict__ C) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * n) return;
-  const int i = (int)(idx / n), j = (int)(idx % n);
-  if (i > j) return;
-  const int ti = i / BM, tj = j / BM;
-  const int id = ti * T - ti * (ti - 1) / 2 + (tj - ti);
-  const int64_t o = (int64_t)(i - ti * BM) * BM + (j - tj * BM);
-  double s = 0.0;
-  for (int sp = 0; sp < ns; ++sp) s += (double)part[((int64_t)sp * ntiles + id) * BM * BM + o];
+// Fixed-order float-float reduction of the split partials, with the optional FP8 row scales
+// (from the row maxima) undone exactly.  Block (tile, chunk): one thread per
+// entry of the upper-triangle tile, reading the partials coalesced.
+constexpr int RED_THREADS = 256;
+__global__ void __launch_bounds__(RED_THREADS) tc_reduce_sym_kernel(const float* __restrict__ part, int ns, int T,
+                                                                    int n, const float* __restrict__ rmax,
+                                                                    double* __restrict__ C) {
+  const int tile = blockIdx.x, ntiles = T * (T + 1) / 2;
+  int ti = 0, id = tile;
+  while (id >= T - ti) { id -= T - ti; ++ti; }
+  const int tj = ti + id;
+  const int o = blockIdx.y * RED_THREADS + threadIdx.x;
+  const int i = ti * BM + o / BM, j = tj * BM + o % BM;
+  if (i >= n || j >= n || i > j) return;
+  const float* p = part + (int64_t)tile * BM * BM + o;
+  const int64_t stride = (int64_t)ntiles * BM * BM;
+  FFSum acc;
+  int sp = 0;
+  for (; sp + 4 <= ns; sp += 4) {
+    const float v0 = p[sp * stride], v1 = p[(sp + 1) * stride], v2 = p[(sp + 2) * stride],
+                v3 = p[(sp + 3) * stride];
+    acc.add(v0);
+    acc.add(v1);
+    acc.add(v2);
+    acc.add(v3);
+  }
+  for (; sp < ns; ++sp) acc.add(p[sp * stride]);
+  double s = acc.value();
   if (rmax) s /= (double)fp8_row_scale(rmax[i]) * (double)fp8_row_scale(rmax[j]);
   C[i + (int64_t)n * j] = s;
   C[j + (int64_t)n * i] = s;
@@ -461,8 +482,9 @@ TcPlan tc_plan(const View& v) {
   TcPlan g;
   g.T = (int)ceil_div(v.n, BM);
   g.nt = g.T * (g.T + 1) / 2;
-  g.nkp = ceil_div(v.J(), KP);
-  g.nkb = g.nkp * B::PER_TILE;
+  const int64_t jp = ceil_div(v.J(), CPAD) * CPAD;
+  g.nkp = jp / KP;
+  g.nkb = jp / B::KB;
   // Each partial sum stays within SPLIT_MAX_TERMS values of c, and the launch
   // fills whole waves of resident CTAs.
   const int64_t slots = (int64_t)gram_ctas_per_sm<P>() * num_sms();
@@ -512,8 +534,8 @@ int tc_gram_t(const float* y, const View& v, double* S, float* scratch, size_t s
   tc_gram_kernel<P><<<dim3(g.nt, g.ns), GRAM_THREADS, Ring<P>::BYTES, st>>>(packed, g.T, g.nkb, g.kbps, part,
                                                                             status);
   ATK_LAUNCHED();
-  tc_reduce_sym_kernel<<<(unsigned)ceil_div(v.n * v.n, 256), 256, 0, st>>>(part, g.ns, g.nt, g.T, (int)v.n, rmax,
-                                                                          S);
+  tc_reduce_sym_kernel<<<dim3(g.nt, BM * BM / RED_THREADS), RED_THREADS, 0, st>>>(part, g.ns, g.T, (int)v.n, rmax,
+                                                                                  S);
   ATK_LAUNCHED();
   return ATK_OK;
 }
