@@ -340,7 +340,7 @@ def run_ours(args):
 
 
 def run_case(args):
-    """Time one step-level operation on one view: --case gram:LO,N,HI or ttm:LO,N,HI,R.
+    """Time one step-level operation: --case gram:LO,N,HI, ttm:LO,N,HI,R or eig:N,R[,METHOD].
 
     Used for kernel profiles: the input is synthetic N(0,1) float32 on the
     device, the call goes through the C ABI, and the line reports the
@@ -350,11 +350,39 @@ def run_case(args):
     import paper_2010_10131_b300 as atk
     prec = args.precision
     kind, _, shape = args.case.partition(":")
+    if kind == "batched":
+        out = run_batched(args, count=int(shape) if shape else 4096)
+        print(json.dumps({"case": args.case, **out}), flush=True)
+        return 0
     vals = [int(v) for v in shape.split(",")]
-    lo, n, hi = vals[:3]
     g = torch.Generator(device="cuda").manual_seed(0)
-    y = torch.randn(lo * n * hi, device="cuda", generator=g)
-    if kind == "gram":
+    if kind == "eig":
+        # S = Q diag(lambda) Q^T: R signal eigenvalues in [1, 10] over a noise
+        # floor 1e-6 (the spectrum of a rank-R Tucker tensor's Gram plus 1e-3 noise).
+        n, R = vals[0], vals[1]
+        method = vals[2] if len(vals) > 2 else atk.EIG_AUTO
+        q, _ = torch.linalg.qr(torch.randn(n, n, device="cuda", dtype=torch.float64, generator=g))
+        lam = torch.cat([1 + 9 * torch.rand(R, device="cuda", dtype=torch.float64, generator=g),
+                         1e-6 * (1 + torch.rand(n - R, device="cuda", dtype=torch.float64, generator=g))])
+        S = ((q * lam) @ q.t()).contiguous()
+        U = torch.empty(n * R, device="cuda", dtype=torch.float32)
+        lamo = torch.empty(n, device="cuda", dtype=torch.float64)
+        disc = torch.empty(1, device="cuda", dtype=torch.float64)
+        L = atk.lib()
+        stream = torch.cuda.current_stream().cuda_stream
+
+        def fn():
+            st = L.atucker_eig(S.data_ptr(), n, R, atk.EIG_ROT_FP32, method, U.data_ptr(), lamo.data_ptr(),
+                               disc.data_ptr(), stream)
+            if st != 0:
+                raise SystemExit(f"atucker_eig failed: {st}")
+        flops, lo, hi = 2.0 * n * n * R, 1, n  # one S Q product as the unit of work
+    else:
+        lo, n, hi = vals[:3]
+        y = torch.randn(lo * n * hi, device="cuda", generator=g)
+    if kind == "eig":
+        pass
+    elif kind == "gram":
         fn = lambda: atk.gram(y, lo, n, hi, precision=prec)  # noqa: E731
         flops = float(n) * n * lo * hi  # I_n^2 J_n (Eq. 4)
     elif kind == "ttm":
@@ -379,6 +407,68 @@ def run_case(args):
     return 0
 
 
+def batched_inputs(count: int, seed: int = 0):
+    """The batched workload: `count` random-Tucker order-3 tensors (synth recipe)."""
+    import synth
+    shapes = synth.batched_shapes(count=count, seed=seed)
+    return shapes, [synth.batched_tensor(shapes, t, seed=seed) for t in range(count)]
+
+
+def run_batched(args, count: int = 4096, serial_sample: int = 256):
+    """Time the batched form: one tuned, graph-replayed persistent launch over
+    `count` small tensors, against the single-tensor plan path called one
+    tensor at a time (plans created beforehand) on the first `serial_sample`
+    tensors, scaled to the whole batch.  Returns a dict for the JSON line."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    t0 = time.time()
+    shapes, xs_np = batched_inputs(count)
+    gen_s = time.time() - t0
+    in_bytes = sum(x.nbytes for x in xs_np)
+    xs = [torch.from_numpy(x).cuda() for x in xs_np]
+    b = atk.Batch([s[0] for s in shapes], [s[1] for s in shapes])
+    cores, facs = b.outputs()
+    tune_ms = b.tune(xs, cores, facs, reps=2)
+    variant = b.variant
+    for _ in range(max(args.warmup, 1)):
+        b.run(xs, cores, facs, sync=False)
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(args.steps, 1)
+    e0.record()
+    for _ in range(steps):
+        b.run(xs, cores, facs, sync=False)
+    e1.record()
+    b.sync()
+    ms = e0.elapsed_time(e1) / steps
+    b.close()
+    # One at a time: the regular plan per tensor, created outside the timed region.
+    k = min(serial_sample, count)
+    plans = [atk.Plan(shapes[t][0], shapes[t][1], solver=[0, 0, 0]) for t in range(k)]
+    outs = [(torch.empty(int(np.prod(shapes[t][1])), device="cuda"),
+             torch.empty(sum(d * r for d, r in zip(*shapes[t])), device="cuda")) for t in range(k)]
+    for t in range(k):
+        plans[t].run(xs[t], outs[t][0], outs[t][1])
+    torch.cuda.synchronize()
+    e0.record()
+    for t in range(k):
+        plans[t].run(xs[t], outs[t][0], outs[t][1])
+    e1.record()
+    torch.cuda.synchronize()
+    serial_ms = e0.elapsed_time(e1) * count / k
+    for pl in plans:
+        pl.close()
+    return {
+        "workload": f"{count} order-3 tensors, dims uniform in [16, 96], ranks uniform in [4, 16] "
+                    "(feasibility-clamped), random Tucker + 1e-3 noise, EIG every mode",
+        "input_bytes": in_bytes, "ms": ms, "gbs": in_bytes / (ms * 1e-3) / 1e9,
+        "tensors_per_s": count / (ms * 1e-3), "variant": variant,
+        "variants": [{"threads": th, "chunk": kc, "ms": m} for (th, kc), m in zip(atk.Batch.variants(), tune_ms)],
+        "one_at_a_time_ms": serial_ms, "one_at_a_time_sample": f"first {k} of {count} tensors, scaled",
+        "speedup_vs_one_at_a_time": serial_ms / ms, "graph": True, "generate_s": gen_s,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,7 +476,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default=None, help="profile one op: gram:LO,N,HI or ttm:LO,N,HI,R")
+    ap.add_argument("--case", default=None, help="profile one op: gram:LO,N,HI, ttm:LO,N,HI,R, eig:N,R[,METHOD] or batched[:COUNT]")
     ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 TF32, 2 BF16, 3 3xBF16, 4 FP8-e4m3 (--case)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     args = ap.parse_args()

@@ -247,6 +247,63 @@ int atucker_als_mode(const float* y, int64_t lo, int64_t n, int64_t hi, int64_t 
                      uint64_t seed, int mode, int sweeps, int precision, float* U_out, float* core_out,
                      void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many small order-3 tensors in one persistent launch.
+ *
+ * Alg. 2 runs on every tensor with the EIG solver in every mode and mode
+ * order 1, 2, 3, exactly as atucker_sthosvd would, except that the Jacobi
+ * eigenvectors are used as computed in float32 (no float64 refinement step)
+ * and no discarded energies are returned.  Each CTA of one persistent kernel
+ * takes whole tensors from a device work counter, largest first, so a whole
+ * batch is one launch; it is captured once in a CUDA graph (pointer-table
+ * upload, counter reset, kernel) and replayed by atucker_batch_run.
+ *
+ * Limits: every dimension in [1, 96], every rank in [1, min(dim, 32)], and
+ * Tucker-feasible ranks (R_n <= product of the other two ranks), else
+ * ATK_EUNSUPPORTED / ATK_ERANK at creation.
+ * ------------------------------------------------------------------------ */
+typedef struct atucker_batch_s* atucker_batch_t;
+
+enum atucker_batch_option {
+  ATK_BATCH_OPT_VARIANT = 1,            /* launch variant index (see atucker_batch_variants); set by tuning */
+  ATK_BATCH_OPT_GRAPH = 2,              /* 1 (default): replay a CUDA graph; 0: plain launches */
+  ATK_BATCH_OPT_SYNC = 3,               /* 1: atucker_batch_run waits and returns the device status */
+  ATK_BATCH_OPT_JACOBI_MAX_SWEEPS = 4   /* sweep cap of the Jacobi eigensolver (default 40) */
+};
+
+/* Create a batch of `count` tensors.  dims3 and ranks3 are host arrays of
+ * 3 * count values: tensor t has dims (dims3[3t], dims3[3t+1], dims3[3t+2])
+ * and ranks likewise.  The batch owns its device workspace (one block of
+ * R1 d2 d3 + R1 R2 d3 floats per resident CTA) and runs on `stream`. */
+int atucker_batch_create(atucker_batch_t* batch, int count, const int64_t* dims3, const int64_t* ranks3,
+                         void* stream);
+int atucker_batch_set_option(atucker_batch_t batch, int option, int64_t value);
+
+/* Decompose the batch.  xs, cores and factors are HOST arrays of `count`
+ * device pointers: tensor t is read from xs[t] (d1 x d2 x d3 float32,
+ * column-major, not modified), its core is written to cores[t] (R1 x R2 x R3)
+ * and its factors to factors[t] (U1 | U2 | U3, each d_n x R_n column-major,
+ * concatenated).  The pointer tables are copied at the call.  Asynchronous on
+ * the batch's stream unless ATK_BATCH_OPT_SYNC is set; a later call waits for
+ * the previous one to finish reading its tables. */
+int atucker_batch_run(atucker_batch_t batch, const float* const* xs, float* const* cores, float* const* factors);
+
+/* Wait for the last run; returns ATK_ENOCONV if any Jacobi reached its sweep
+ * cap, ATK_ETIMEOUT for a timed-out wait, else ATK_OK. */
+int atucker_batch_sync(atucker_batch_t batch);
+
+/* Autotuner: run every launch variant on this batch (one warm-up and `reps`
+ * timed runs each, CUDA events on the batch's stream), keep the fastest.
+ * ms_out (nullable) receives the mean time of each variant. */
+int atucker_batch_tune(atucker_batch_t batch, const float* const* xs, float* const* cores, float* const* factors,
+                       int reps, float* ms_out);
+int atucker_batch_get_variant(atucker_batch_t batch, int* variant_out);
+
+/* The launch variants: count, and per variant threads per CTA and c values per
+ * staged Gram chunk (each array sized by the count; nullable). */
+int atucker_batch_variants(int* count_out, int* threads_out, int* chunk_out);
+void atucker_batch_destroy(atucker_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ import os
 import re
 
 __all__ = [
-    "lib", "abi_symbols", "AtuckerError", "Plan", "sthosvd", "gram", "ttm", "eig", "als_mode",
+    "lib", "abi_symbols", "AtuckerError", "Plan", "Batch", "sthosvd", "gram", "ttm", "eig", "als_mode",
     "EIG", "ALS", "FP32", "TF32", "BF16", "BF16X3", "FP8E4M3", "EIG_ROT_FP32", "EIG_ROT_FP64",
 ]
 
@@ -29,6 +29,7 @@ FP32, TF32, BF16, BF16X3, FP8E4M3 = 0, 1, 2, 3, 4
 EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
 OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD = 1, 2, 3, 4, 5
 EIG_AUTO, EIG_FULL_JACOBI, EIG_SUBSPACE = 0, 1, 2
+BATCH_OPT_VARIANT, BATCH_OPT_GRAPH, BATCH_OPT_SYNC, BATCH_OPT_JACOBI_MAX_SWEEPS = 1, 2, 3, 4
 PHASES = ("gram", "gram_reduce", "eig", "ttm", "als", "norms", "total", "gram_launches", "launches", "runs")
 _STATUS = {EINVAL: "EINVAL", ERANK: "ERANK", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENOCONV: "ENOCONV",
            ETIMEOUT: "ETIMEOUT", EUNSUPPORTED: "EUNSUPPORTED"}
@@ -58,6 +59,14 @@ _SIGS = {
     "atucker_ttm": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _i32, _vp, _vp]),
     "atucker_eig": (_i32, [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _vp, _vp]),
     "atucker_als_mode": (_i32, [_vp, _i64, _i64, _i64, _i64, _vp, _u64, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "atucker_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp]),
+    "atucker_batch_set_option": (_i32, [_vp, _i32, _i64]),
+    "atucker_batch_run": (_i32, [_vp, _vp, _vp, _vp]),
+    "atucker_batch_sync": (_i32, [_vp]),
+    "atucker_batch_tune": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "atucker_batch_get_variant": (_i32, [_vp, _vp]),
+    "atucker_batch_variants": (_i32, [_vp, _vp, _vp]),
+    "atucker_batch_destroy": (None, [_vp]),
 }
 
 
@@ -275,3 +284,114 @@ def als_mode(y, lo: int, n: int, hi: int, R: int, L0=None, seed: int = 0, mode: 
                                   precision, _dev(U, torch.float32), _dev(core, torch.float32), _stream_ptr()),
            "atucker_als_mode")
     return U.view(R, n).t(), core
+
+
+class Batch:
+    """Many small order-3 tensors decomposed by one persistent launch (atucker_batch_*).
+
+    dims, ranks: sequences of (d1, d2, d3) and (R1, R2, R3), one per tensor.
+    run() takes lists of CUDA float32 tensors (each contiguous, column-major
+    d1 x d2 x d3 data) and returns lists of cores and concatenated factors.
+    """
+
+    def __init__(self, dims, ranks, stream=None, max_sweeps: int | None = None):
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.ranks = [tuple(int(v) for v in r) for r in ranks]
+        if len(self.dims) != len(self.ranks) or not self.dims:
+            raise ValueError("dims and ranks need the same, non-zero length")
+        self.count = len(self.dims)
+        flat_d = [v for d in self.dims for v in d]
+        flat_r = [v for r in self.ranks for v in r]
+        self._h = ctypes.c_void_p(None)
+        self.stream = stream
+        _check(lib().atucker_batch_create(ctypes.byref(self._h), self.count, _i64arr(flat_d), _i64arr(flat_r),
+                                          _stream_ptr(stream)), "atucker_batch_create")
+        if max_sweeps is not None:
+            self.set_option(BATCH_OPT_JACOBI_MAX_SWEEPS, max_sweeps)
+
+    def set_option(self, option: int, value: int):
+        _check(lib().atucker_batch_set_option(self._h, option, int(value)), "atucker_batch_set_option")
+
+    @property
+    def variant(self) -> int:
+        v = ctypes.c_int(0)
+        _check(lib().atucker_batch_get_variant(self._h, ctypes.byref(v)), "atucker_batch_get_variant")
+        return v.value
+
+    @staticmethod
+    def variants():
+        """[(threads per CTA, c values per Gram chunk)] for every launch variant."""
+        n = ctypes.c_int(0)
+        _check(lib().atucker_batch_variants(ctypes.byref(n), None, None), "atucker_batch_variants")
+        th, kc = _i32arr([0] * n.value), _i32arr([0] * n.value)
+        _check(lib().atucker_batch_variants(None, th, kc), "atucker_batch_variants")
+        return list(zip(list(th), list(kc)))
+
+    def outputs(self):
+        """Freshly allocated (cores, factors) lists on the current device."""
+        torch = _torch()
+        cores = [torch.empty(r[0] * r[1] * r[2], device="cuda", dtype=torch.float32) for r in self.ranks]
+        facs = [torch.empty(sum(d * r for d, r in zip(dd, rr)), device="cuda", dtype=torch.float32)
+                for dd, rr in zip(self.dims, self.ranks)]
+        return cores, facs
+
+    def _tables(self, xs, cores, factors):
+        torch = _torch()
+        if not (len(xs) == len(cores) == len(factors) == self.count):
+            raise ValueError("need one input, core and factor buffer per tensor")
+        for t, d in zip(xs, self.dims):
+            _dev(t, torch.float32)
+            if t.numel() != d[0] * d[1] * d[2]:
+                raise ValueError("input size does not match its dims")
+        for c, r in zip(cores, self.ranks):
+            _dev(c, torch.float32)
+            if c.numel() < r[0] * r[1] * r[2]:
+                raise ValueError("core buffer too small")
+        for f, d, r in zip(factors, self.dims, self.ranks):
+            _dev(f, torch.float32)
+            if f.numel() < sum(a * b for a, b in zip(d, r)):
+                raise ValueError("factor buffer too small")
+        mk = lambda ts: (ctypes.c_void_p * self.count)(*[t.data_ptr() for t in ts])  # noqa: E731
+        return mk(xs), mk(cores), mk(factors)
+
+    def run(self, xs, cores=None, factors=None, sync: bool = True):
+        if cores is None or factors is None:
+            cores, factors = self.outputs()
+        px, pc, pf = self._tables(xs, cores, factors)
+        _check(lib().atucker_batch_run(self._h, px, pc, pf), "atucker_batch_run")
+        if sync:
+            self.sync()
+        return cores, factors
+
+    def sync(self):
+        _check(lib().atucker_batch_sync(self._h), "atucker_batch_sync")
+
+    def tune(self, xs, cores=None, factors=None, reps: int = 2):
+        """Time every launch variant on this batch and keep the fastest; returns ms per variant."""
+        if cores is None or factors is None:
+            cores, factors = self.outputs()
+        px, pc, pf = self._tables(xs, cores, factors)
+        nv = len(self.variants())
+        ms = (ctypes.c_float * nv)()
+        _check(lib().atucker_batch_tune(self._h, px, pc, pf, int(reps), ms), "atucker_batch_tune")
+        return list(ms)
+
+    def close(self):
+        if self._h:
+            lib().atucker_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def split_factors(flat, dims, ranks):
+        out, off = [], 0
+        for d, r in zip(dims, ranks):
+            out.append(flat[off:off + d * r].view(r, d).t())
+            off += d * r
+        return out
+

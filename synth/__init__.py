@@ -25,7 +25,8 @@ synthetic stand-ins carry the shapes and structure of its workloads):
   log-uniform on [16, 1024], at most 2 GB of float32, rank ratios on
   [0.02, 0.5]).
 * ``batched_shapes``: 4096 order-3 tensors, dims uniform in [16, 96], ranks
-  uniform in [4, 16].
+  uniform in [4, 16]; ``batched_tensor`` draws member t as a random Tucker
+  tensor (noise 1e-3) from the stream (seed, t).
 """
 from __future__ import annotations
 
@@ -35,11 +36,14 @@ import numpy as np
 
 __all__ = [
     "rng", "random_tucker", "decaying_tucker", "feasible_ranks",
-    "selector_shapes", "batched_shapes", "to_colmajor_f32", "from_colmajor",
+    "selector_shapes", "batched_shapes", "batched_tensor", "to_colmajor_f32", "from_colmajor",
 ]
 
 
-def rng(seed: int) -> np.random.Generator:
+def rng(seed) -> np.random.Generator:
+    """PCG64 stream for an int seed or a tuple of ints (e.g. (batch seed, tensor index))."""
+    if isinstance(seed, (tuple, list)):
+        seed = np.random.SeedSequence([int(v) for v in seed])
     return np.random.Generator(np.random.PCG64(seed))
 
 
@@ -149,3 +153,14 @@ def batched_shapes(count: int = 4096, seed: int = 0, lo: int = 16, hi: int = 96,
         ranks = [int(v) for v in g.integers(rlo, rhi + 1, size=3)]
         out.append((dims, feasible_ranks(dims, ranks)))
     return out
+
+
+def batched_tensor(shapes, t: int, seed: int = 0, noise: float = 1e-3):
+    """Tensor t of a batch: random Tucker of shapes[t] from the stream (seed, t).
+
+    Any subset of a batch regenerates bit-identically, so the oracle can check
+    sampled members of a large batch.
+    """
+    dims, ranks = shapes[t]
+    return random_tucker(dims, ranks, noise=noise, seed=(seed, t))[0]
+

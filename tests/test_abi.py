@@ -49,6 +49,24 @@ def test_argument_validation_runs_on_host():
     assert lib.atucker_gram(None, 1, 1, 1, 0, None, None) == atk.EINVAL
 
 
+def test_batch_validation_runs_on_host():
+    """The batched form rejects shapes outside its limits before touching the device."""
+    lib = atk.lib()
+    h = ctypes.c_void_p()
+    too_big = (ctypes.c_int64 * 6)(16, 16, 16, 97, 20, 20)
+    ranks = (ctypes.c_int64 * 6)(4, 4, 4, 4, 4, 4)
+    assert lib.atucker_batch_create(ctypes.byref(h), 2, too_big, ranks, None) == atk.EUNSUPPORTED
+    dims = (ctypes.c_int64 * 3)(16, 16, 16)
+    infeasible = (ctypes.c_int64 * 3)(9, 2, 4)
+    assert lib.atucker_batch_create(ctypes.byref(h), 1, dims, infeasible, None) == atk.ERANK
+    rank_over_dim = (ctypes.c_int64 * 3)(17, 4, 4)
+    assert lib.atucker_batch_create(ctypes.byref(h), 1, dims, rank_over_dim, None) == atk.ERANK
+    assert lib.atucker_batch_create(ctypes.byref(h), 0, dims, ranks, None) == atk.EINVAL
+    assert lib.atucker_batch_run(None, None, None, None) == atk.EINVAL
+    n = ctypes.c_int(0)
+    assert lib.atucker_batch_variants(ctypes.byref(n), None, None) == atk.OK and n.value >= 2
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(atk, "LIB_PATH", str(tmp_path / "nope.so"))
     monkeypatch.setattr(atk, "_lib", None)
