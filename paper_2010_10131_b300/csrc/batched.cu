@@ -6,14 +6,17 @@
 // small ones).  A tensor never leaves its CTA:
 //   for each mode n:  S = Y_(n) Y_(n)^T over the stride view (a2), staged
 //                     through shared memory, split over c among thread groups;
-//                     cyclic Jacobi on S in shared memory (a3, float32
-//                     rotations, the routine of the single-tensor path);
-//                     U = the R_n leading eigenvectors, sign rule, written out;
+//                     one-sided (Hestenes) Jacobi on S in shared memory
+//                     (a3, float32 rotations): S's columns rotate into
+//                     lambda_i u_i, so no eigenvector matrix is carried;
+//                     U = the R_n leading eigenvectors, one polar step,
+//                     sign rule, written out;
 //                     Y <- Y x_n U^T (a4) into this CTA's workspace (L2), or
 //                     into the core after the last mode.
-// Sizes: every mode <= 96, every rank <= 32.  Shared memory holds the Jacobi
-// matrix A and eigenvector matrix V (96 x 97 floats each); the Gram and TTM
-// staging tiles reuse V's space, the kept factor reuses A's.
+// Sizes: every mode <= 96, every rank <= 32.  Shared memory (54 KB, so up to
+// four tensors per SM) holds the Gram matrix A (96 x 97 floats), a 16 KB
+// staging area for the Gram and TTM tiles, and the eigenvalues; the kept
+// factor reuses A's space.
 //
 // The launch shape (threads per CTA, CTAs per SM, c values per staged chunk)
 // is a template/launch choice picked by an autotuner that times every
@@ -30,9 +33,9 @@ namespace batch {
 
 constexpr int DMAX = 96;
 constexpr int RMAX = 32;
-constexpr int LDA = DMAX + 1;                 // pitch of A and V
-constexpr int MAT = DMAX * LDA;               // floats of A (and of V)
-constexpr int NBLK = (DMAX / 2) * (DMAX / 2 + 1) / 2;
+constexpr int LDA = DMAX + 1;                 // pitch of A
+constexpr int MAT = DMAX * LDA;               // floats of A
+constexpr int STG = 4096;                     // floats of the staging area
 
 struct Desc {
   int d[3], r[3];
@@ -43,8 +46,8 @@ struct Ptrs {
   float* factors;
 };
 
-// Shared-memory layout (floats): A | V | cs | pq (int) | ord (int) | flag (int) | blk (ushort).
-constexpr size_t SMEM_FLOATS = 2 * (size_t)MAT + 3 * DMAX + 4 + (2 * NBLK + 1) / 2;
+// Shared-memory layout (floats): A | stage | lam | ord (int).
+constexpr size_t SMEM_FLOATS = (size_t)MAT + STG + 2 * DMAX;
 constexpr size_t SMEM_BYTES = SMEM_FLOATS * sizeof(float);
 
 // ------------------------------------------------------------------ Gram
@@ -153,7 +156,7 @@ __device__ __host__ inline void gram_shape(int n, int cap, int& tm_out, int& g_o
 template <int NT, int KC>
 __device__ void cta_gram(const float* y, int lo, int n, int64_t J, float* S, int lds, float* stage) {
   int tm, G;
-  gram_shape<NT, KC>(n, MAT, tm, G);
+  gram_shape<NT, KC>(n, STG, tm, G);
   switch (tm) {
     case 8: gram_tm<NT, KC, 8>(y, lo, n, J, S, lds, stage, G); break;
     case 6: gram_tm<NT, KC, 6>(y, lo, n, J, S, lds, stage, G); break;
@@ -171,7 +174,7 @@ __device__ void cta_ttm(const float* y, int lo, int n, int64_t hi, const float* 
                         float* stage) {
   const int64_t J = (int64_t)lo * hi;
   const int lt = n | 1;
-  const int ct = std::min(256, MAT / lt);
+  const int ct = std::min(256, STG / lt);
   const int rg = r4 / 4;
   const int t = threadIdx.x;
   for (int64_t c0 = 0; c0 < J; c0 += ct) {
@@ -231,12 +234,9 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(const Desc* __restric
                                                            int* __restrict__ status) {
   extern __shared__ __align__(16) float smem[];
   float* A = smem;
-  float* V = A + MAT;
-  float* cs = V + MAT;
-  int* pq = reinterpret_cast<int*>(cs + DMAX);
-  int* ord = pq + DMAX;
-  int* flag = ord + DMAX;
-  unsigned short* blk = reinterpret_cast<unsigned short*>(flag + 4);
+  float* stage = A + MAT;
+  float* lam = stage + STG;
+  int* ord = reinterpret_cast<int*>(lam + DMAX);
   __shared__ int cur;
   __shared__ double red[32];
   const int t = threadIdx.x, lane = t % 32, warp = t / 32;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(const Desc* __restric
       const int m = n + (n & 1), ld = m + 1;
       const int r4 = (R + 3) & ~3;
       // 1. Gram into A (pitch ld); padding row/column of an odd n is zero.
-      cta_gram<NT, KC>(src, (int)lo, n, lo * hi, A, ld, V);
+      cta_gram<NT, KC>(src, (int)lo, n, lo * hi, A, ld, stage);
       if (m != n) {
         for (int i = t; i < m; i += NT) {
           A[(m - 1) * ld + i] = 0.f;
@@ -267,12 +267,11 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(const Desc* __restric
         }
         __syncthreads();
       }
-      // 2. Jacobi: V = I, ||A||_F for the absolute threshold.
+      // 2. One-sided Jacobi on S (PSD): its normalised columns become the
+      //    eigenvectors, lam the eigenvalues.  ||S||_F for the absolute floor.
       double fl = 0.0;
       for (int idx = t; idx < m * m; idx += NT) {
-        const int i = idx / m, j = idx % m;
-        V[i * ld + j] = i == j ? 1.f : 0.f;
-        const double a = A[i * ld + j];
+        const double a = A[(idx / m) * ld + idx % m];
         fl += a * a;
       }
       for (int o = 16; o > 0; o >>= 1) fl += __shfl_xor_sync(0xffffffffu, fl, o);
@@ -286,33 +285,33 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(const Desc* __restric
       __syncthreads();
       const float fro = (float)sqrt(red[0]);
       bool conv = true;
-      JWork<float> w{A, V, cs, pq, flag, blk, ld};
-      if (m >= 2) jacobi_smem<float>(w, m, fro, max_sweeps, &conv);
+      if (m >= 2) hestenes_smem<8, DMAX / 8>(A, ld, m, fro, max_sweeps, lam, &conv);
       if (!conv && t == 0) atomicOr(status, DEV_NOCONV);
       // 3. Order by eigenvalue (descending; NaN lowest; ties by index).
       for (int i = t; i < n; i += NT) {
-        const float di = A[i * ld + i];
+        const float di = lam[i];
         const float ki = isnan(di) ? -INFINITY : di;
         int rank = 0;
         for (int j = 0; j < n; ++j) {
-          const float dj = A[j * ld + j];
+          const float dj = lam[j];
           const float kj = isnan(dj) ? -INFINITY : dj;
           rank += (kj > ki) || (kj == ki && j < i);
         }
         ord[rank] = i;
       }
       __syncthreads();
-      // 4. U = the kept columns of V (row-major n x r4 in A's space, zero
-      //    padded), one Newton-Schulz polar step U <- U (3 I - U^T U) / 2 to
-      //    undo the rounding the float32 rotations left in its orthonormality,
-      //    then the sign rule: each column's largest-magnitude entry positive
-      //    (ties: lowest row).
-      float* Ug = A;                       // gathered, n x r4
-      float* M = A + DMAX * RMAX;          // U^T U, r4 x r4
-      float* Us = M + RMAX * RMAX;         // polished factor, n x r4
+      // 4. U = the kept eigenvectors (row-major n x r4, zero padded), one
+      //    Newton-Schulz polar step U <- U (3 I - U^T U) / 2 to undo the
+      //    rounding the float32 rotations left in its orthonormality, then
+      //    the sign rule: each column's largest-magnitude entry positive
+      //    (ties: lowest row).  Gathered copy and U^T U in the staging area,
+      //    the result in A's space.
+      float* Ug = stage;                   // n x r4
+      float* M = stage + DMAX * RMAX;      // U^T U, r4 x r4
+      float* Us = A;                       // polished factor, n x r4
       for (int idx = t; idx < n * r4; idx += NT) {
         const int i = idx / r4, r = idx % r4;
-        Ug[idx] = r < R ? V[i * ld + ord[r]] : 0.f;
+        Ug[idx] = r < R ? A[ord[r] * ld + i] : 0.f;  // column ord[r] of the rotated S
       }
       __syncthreads();
       for (int idx = t; idx < r4 * r4; idx += NT) {
@@ -353,7 +352,7 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(const Desc* __restric
       __syncthreads();
       // 5. TTM into the workspace, or the core after the last mode.
       float* dst = k == 2 ? pt.core : bufs[k & 1];
-      cta_ttm<NT>(src, (int)lo, n, hi, Us, R, r4, dst, V);
+      cta_ttm<NT>(src, (int)lo, n, hi, Us, R, r4, dst, stage);
       src = dst;
       fac += (int64_t)n * R;
       lo *= R;
@@ -383,18 +382,18 @@ Variant make_variant() {
 
 const std::vector<Variant>& variants() {
   static const std::vector<Variant> v = {
-      make_variant<128, 16, 2>(), make_variant<256, 16, 1>(), make_variant<256, 16, 2>(),
+      make_variant<128, 16, 4>(), make_variant<128, 32, 4>(), make_variant<256, 16, 2>(),
       make_variant<256, 32, 2>(), make_variant<512, 16, 1>(), make_variant<512, 32, 1>(),
   };
   return v;
 }
 
-// CTAs per SM a variant reaches (shared memory and registers), at most 2.
+// CTAs per SM a variant reaches (shared memory and registers), at most 4.
 int resident(const Variant& v) {
   cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   int per = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, v.fn, v.nt, SMEM_BYTES);
-  return std::max(1, std::min(per, 2));
+  return std::max(1, std::min(per, 4));
 }
 
 }  // namespace batch

@@ -199,4 +199,103 @@ __device__ int jacobi_smem(JWork<T> w, int m, T fro, int max_sweeps, bool* conve
   return conv ? sweep + 1 : sweep;
 }
 
+// ------------------------------------------------------------ one-sided
+// One-sided (Hestenes) Jacobi on the columns of a symmetric positive
+// semidefinite H held column-major in shared memory (W[j * ldw + i] = h_ij; a
+// symmetric matrix stored row-major is the same array).  The rotation of pair
+// (p, q) makes columns w_p and w_q orthogonal: with alpha = |w_p|^2,
+// beta = |w_q|^2, gamma = w_p . w_q, zeta = (beta - alpha) / (2 gamma),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t:
+// w_p <- c w_p - s w_q, w_q <- s w_p + c w_q.  This is the two-sided Jacobi
+// of H^T H = H^2 carried on H's columns, so at convergence W = H V = U diag(s)
+// with V orthogonal, and for PSD H the normalised columns u_i are
+// eigenvectors of H with eigenvalue s_i = |w_i| (Golub & Van Loan, Matrix
+// Computations, Sec. 8.6.3).  No separate eigenvector matrix is carried.
+//
+// Round-robin ordering as in jacobi_smem; groups of L lanes own one pair at a
+// time (rows gl, gl + L, ... of the two columns in registers, the three dot
+// products reduced with shuffles), one barrier per round.  A pair rotates when
+// |gamma| > tol sqrt(alpha beta) with tol = 5e-7 sqrt(m) (the float32
+// rounding level of an m-term dot product) and |gamma| > 1e-12 ||H||_F^2.
+// m must be even (pad with a zero column) and at most L * MR.
+// On return lam[i] = |w_i| and w_i is normalised (zero columns stay zero).
+__device__ __forceinline__ float hj_rot_t(float x) {
+  if (x > 1.1529215e18f) return __fdividef(0.5f, x);
+  const float w = fmaf(x, x, 1.f);
+  return __fdividef(1.f, fmaf(w, rsqrtf(w), x));
+}
+
+template <int L, int MR>
+__device__ int hestenes_smem(float* W, int ldw, int m, float fro, int max_sweeps, float* lam, bool* converged) {
+  static_assert(L == 8 || L == 16 || L == 32, "group width");
+  const int t = threadIdx.x, gl = t % L, grp = t / L, ngrp = blockDim.x / L;
+  const int lane = t % 32;
+  const unsigned gmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (lane / L * L));
+  const int half = m / 2;
+  const float tol = 5e-7f * sqrtf((float)m);
+  const float tol2 = tol * tol;
+  const float absg = 1e-12f * fro * fro;
+  int sweep = 0;
+  bool conv = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = grp; k < half; k += ngrp) {
+        int p, q;
+        rr_pair(r, k, m, p, q);
+        float a[MR], b[MR];
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int j = 0; j < MR; ++j) {
+          const int i = gl + L * j;
+          a[j] = i < m ? W[p * ldw + i] : 0.f;
+          b[j] = i < m ? W[q * ldw + i] : 0.f;
+          al = fmaf(a[j], a[j], al);
+          be = fmaf(b[j], b[j], be);
+          ga = fmaf(a[j], b[j], ga);
+        }
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(gmask, al, o);
+          be += __shfl_xor_sync(gmask, be, o);
+          ga += __shfl_xor_sync(gmask, ga, o);
+        }
+        if (ga * ga > tol2 * (al * be) && fabsf(ga) > absg) {
+          const float zeta = __fdividef(be - al, 2.f * ga);
+          const float tt = zeta >= 0.f ? hj_rot_t(zeta) : -hj_rot_t(-zeta);
+          const float c = rsqrtf(fmaf(tt, tt, 1.f)), s = c * tt;
+#pragma unroll
+          for (int j = 0; j < MR; ++j) {
+            const int i = gl + L * j;
+            if (i < m) {
+              W[p * ldw + i] = c * a[j] - s * b[j];
+              W[q * ldw + i] = s * a[j] + c * b[j];
+            }
+          }
+          rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) {
+      conv = true;
+      break;
+    }
+  }
+  // Norms and normalisation, one group per column.
+  for (int j = grp; j < m; j += ngrp) {
+    float ss = 0.f;
+    for (int i = gl; i < m; i += L) ss = fmaf(W[j * ldw + i], W[j * ldw + i], ss);
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(gmask, ss, o);
+    const float nrm = sqrtf(ss);
+    const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+    for (int i = gl; i < m; i += L) W[j * ldw + i] *= inv;
+    if (gl == 0) lam[j] = nrm;
+  }
+  __syncthreads();
+  *converged = conv;
+  return conv ? sweep + 1 : sweep;
+}
+
 }  // namespace atk

@@ -40,7 +40,27 @@ def _check_member(x, dims, ranks, core, flat_fac):
     for U, Uo in zip(facs, ref["factors"]):
         assert oracle.projector_distance(U, Uo) <= 1e-4, (dims, ranks)
         assert np.linalg.norm(U.T @ U - np.eye(U.shape[1])) <= 1e-6
+    core = _align_signs(core, facs, ref["factors"], ranks)
     np.testing.assert_allclose(core, ref["core"], atol=1e-3 * np.abs(ref["core"]).max())
+
+
+def _align_signs(core, facs, facs_o, ranks):
+    """The sign rule (largest-magnitude entry positive) is only determined when
+    a column's two largest magnitudes differ by more than the float32
+    eigenvector error.  A column whose sign differs from the oracle's is
+    accepted only at such a near-tie (within 1e-3 relative), and is then
+    flipped, with its core slice, before the cores are compared."""
+    g = core.reshape(ranks, order="F").copy()
+    for n, (U, Uo) in enumerate(zip(facs, facs_o)):
+        for r in range(U.shape[1]):
+            if U[:, r] @ Uo[:, r] < 0:
+                top = np.sort(np.abs(Uo[:, r]))[::-1]
+                assert top[0] - top[1] <= 1e-3 * top[0], ("sign rule violated", n, r)
+                U[:, r] *= -1.0
+                idx = [slice(None)] * len(ranks)
+                idx[n] = r
+                g[tuple(idx)] *= -1.0
+    return g.ravel(order="F")
 
 
 def _run(atk, shapes, xs_np, variant=None, graph=True):
