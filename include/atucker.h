@@ -50,7 +50,26 @@ typedef enum {
 } atucker_status;
 
 /* Per-mode solver, Alg. 2: 0 = EIG (Gram + eigen-decomposition), 1 = ALS (Alg. 3). */
-typedef enum { ATK_EIG = 0, ATK_ALS = 1 } atucker_solver;
+typedef enum { ATK_AUTO = -1, ATK_EIG = 0, ATK_ALS = 1 } atucker_solver;
+
+/* Per-mode configuration classes: the output space of the learned selector
+ * (solver x tile class).  "Tile" is the row tile of the float32 Gram (a2):
+ * AUTO picks 128 / 64 / 32 from I_n; SMALL takes the next smaller one.
+ * The eigensolver methods are those of atucker_eig_method.
+ *   ATK_CLASS_EIG             EIG, eigensolver ATK_EIG_AUTO (or the plan's
+ *                             ATK_OPT_EIG_METHOD), Gram tile AUTO
+ *   ATK_CLASS_EIG_SMALL       EIG, same eigensolver, Gram tile SMALL
+ *   ATK_CLASS_EIG_JACOBI      EIG, full Jacobi eigensolver, Gram tile AUTO
+ *   ATK_CLASS_EIG_JACOBI_SMALL EIG, full Jacobi, Gram tile SMALL
+ *   ATK_CLASS_ALS             ALS (Alg. 3) with the plan's sweep count */
+typedef enum {
+  ATK_CLASS_EIG = 0,
+  ATK_CLASS_EIG_SMALL = 1,
+  ATK_CLASS_EIG_JACOBI = 2,
+  ATK_CLASS_EIG_JACOBI_SMALL = 3,
+  ATK_CLASS_ALS = 4,
+  ATK_NUM_CLASSES = 5
+} atucker_mode_class;
 
 /* Arithmetic for the bulk Gram / TTM / ALS contractions.
  * ATK_FP32 is plain float32 on the CUDA cores, accumulated in float32 and
@@ -102,7 +121,9 @@ typedef struct atucker_plan_s* atucker_plan_t;
  *   mode_order       host permutation of 0..N-1: the order modes are processed
  *                    in (the paper's loop runs n = 1..N); NULL = 0,1,..,N-1
  *   solver_per_mode  host array of N atucker_solver values indexed by mode;
- *                    NULL = EIG for every mode
+ *                    NULL = EIG for every mode.  ATK_AUTO lets the learned
+ *                    selector (atucker_selector_set) pick the mode's class;
+ *                    with no selector loaded AUTO means ATK_CLASS_EIG.
  *   precision        atucker_precision
  *   als_sweeps       ALS iterations (num_iters of Eq. 5; the paper's default is
  *                    5); <= 0 selects 5
@@ -246,6 +267,81 @@ int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, int eig_me
 int atucker_als_mode(const float* y, int64_t lo, int64_t n, int64_t hi, int64_t R, const double* L0,
                      uint64_t seed, int mode, int sweeps, int precision, float* U_out, float* core_out,
                      void* stream);
+
+/* As atucker_plan_create, with one atucker_mode_class per mode (host array of
+ * N values indexed by mode) instead of solver_per_mode. */
+int atucker_plan_create_classes(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
+                                const int* mode_order, const int* class_per_mode, int precision, int als_sweeps,
+                                uint64_t seed, void* stream);
+
+/* The class each mode of the plan runs with (host array of N, by mode). */
+int atucker_plan_classes(atucker_plan_t plan, int* class_out);
+
+/* Per-mode device time (ms, CUDA events on the plan's stream, ATK_OPT_TIMING
+ * = 1) summed over the runs since the last call; ms_out has N entries indexed
+ * by mode.  Synchronises the plan's stream. */
+int atucker_plan_mode_timings(atucker_plan_t plan, double* ms_out, int count);
+
+/* ---------------------------------------------------------------------------
+ * Learned per-mode selector (the paper's adaptive solver selection, Sec. IV-C,
+ * with an MLP in place of the decision tree).
+ *
+ * Features of mode n when it is processed (Table I's ten, plus two):
+ *   0 I_n  1 R_n  2 J_n  3 I_n^2  4 R_n^2  5 I_n R_n  6 R_n^2/I_n
+ *   7 R_n^2/J_n  8 I_n/J_n  9 R_n/J_n  10 position  11 remaining size
+ * J_n is the product of the other modes' current sizes (modes processed
+ * earlier are already truncated to R), position = step / (N - 1) (0 for
+ * N = 1) and remaining size = I_n J_n.  Every feature except the position
+ * enters as log2.  The network is 12 -> 64 -> 64 -> ATK_NUM_CLASSES with
+ * ReLU hidden layers; its outputs predict, for each class, log2 of the mode's
+ * time relative to the fastest class, and the selector takes the smallest.
+ * ------------------------------------------------------------------------ */
+#define ATK_SELECTOR_FEATURES 12
+#define ATK_SELECTOR_HIDDEN 64
+
+/* Model inputs (log2 applied, not standardised) of every mode: out holds
+ * order x 12 values, row n for mode n. */
+int atucker_mode_features(int order, const int64_t* dims, const int64_t* ranks, const int* mode_order,
+                          double* out);
+
+/* Number of network parameters for (in, hidden, out): hidden*in + hidden +
+ * hidden*hidden + hidden + out*hidden + out.  Layout, all row-major float32:
+ * W1 [hidden x in], b1, W2 [hidden x hidden], b2, W3 [out x hidden], b3. */
+int64_t atucker_mlp_param_count(int in, int hidden, int out);
+
+/* Load the selector used by ATK_AUTO: 12 feature means, 12 feature scales
+ * (standardised x = (f - mean) / scale), then the network parameters for
+ * (12, 64, ATK_NUM_CLASSES).  count must be 24 + that parameter count.
+ * Process-wide; the values are copied. */
+int atucker_selector_set(const float* params, int64_t count);
+void atucker_selector_clear(void);
+
+/* Host inference of the loaded selector on `rows` raw feature rows (rows x 12,
+ * as from atucker_mode_features): class_out[rows] the chosen class,
+ * scores_out (nullable) rows x ATK_NUM_CLASSES network outputs. */
+int atucker_selector_predict(const double* features, int rows, int* class_out, float* scores_out);
+
+/* GPU training of the network (the project's own CUDA kernels).  All pointers
+ * are device float32:
+ *   X       B x in standardised inputs (row-major)
+ *   Y       B x out targets, M the B x out mask (1 = target present)
+ *   params  parameter vector (layout above), updated in place
+ *   grad    gradient of the loss, same layout
+ * Loss = sum over masked entries of (output - Y)^2 / (number of masked entries).
+ * atucker_mlp_forward: out (B x out) = network(X).
+ * atucker_mlp_loss_grad: loss (1 value, device) and grad at params.
+ * atucker_mlp_train: `steps` full-batch Adam steps (beta1 0.9, beta2 0.999,
+ *   eps 1e-8, step size lr, bias-corrected; `state` holds 2 x param count
+ *   floats of moments, zero at the first call, and step_base the number of
+ *   steps already taken); loss_out (device, nullable) receives the loss of
+ *   every step. */
+int atucker_mlp_forward(const float* X, int B, int in, int hidden, int out, const float* params, float* Y_out,
+                        void* stream);
+int atucker_mlp_loss_grad(const float* X, const float* Y, const float* M, int B, int in, int hidden, int out,
+                          const float* params, float* loss, float* grad, void* stream);
+int atucker_mlp_train(const float* X, const float* Y, const float* M, int B, int in, int hidden, int out,
+                      float* params, float* state, int steps, int step_base, float lr, float* loss_out,
+                      void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched form: many small order-3 tensors in one persistent launch.

@@ -30,6 +30,10 @@ EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
 OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD = 1, 2, 3, 4, 5
 EIG_AUTO, EIG_FULL_JACOBI, EIG_SUBSPACE = 0, 1, 2
 BATCH_OPT_VARIANT, BATCH_OPT_GRAPH, BATCH_OPT_SYNC, BATCH_OPT_JACOBI_MAX_SWEEPS = 1, 2, 3, 4
+AUTO = -1
+CLASS_EIG, CLASS_EIG_SMALL, CLASS_EIG_JACOBI, CLASS_EIG_JACOBI_SMALL, CLASS_ALS, NUM_CLASSES = 0, 1, 2, 3, 4, 5
+CLASS_NAMES = ("EIG", "EIG-small-tile", "EIG-Jacobi", "EIG-Jacobi-small-tile", "ALS")
+SELECTOR_FEATURES, SELECTOR_HIDDEN = 12, 64
 PHASES = ("gram", "gram_reduce", "eig", "ttm", "als", "norms", "total", "gram_launches", "launches", "runs")
 _STATUS = {EINVAL: "EINVAL", ERANK: "ERANK", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENOCONV: "ENOCONV",
            ETIMEOUT: "ETIMEOUT", EUNSUPPORTED: "EUNSUPPORTED"}
@@ -67,6 +71,18 @@ _SIGS = {
     "atucker_batch_get_variant": (_i32, [_vp, _vp]),
     "atucker_batch_variants": (_i32, [_vp, _vp, _vp]),
     "atucker_batch_destroy": (None, [_vp]),
+    "atucker_plan_create_classes": (_i32, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _i32, _i32, _u64, _vp]),
+    "atucker_plan_classes": (_i32, [_vp, _vp]),
+    "atucker_plan_mode_timings": (_i32, [_vp, _vp, _i32]),
+    "atucker_mode_features": (_i32, [_i32, _vp, _vp, _vp, _vp]),
+    "atucker_mlp_param_count": (_i64, [_i32, _i32, _i32]),
+    "atucker_selector_set": (_i32, [_vp, _i64]),
+    "atucker_selector_clear": (None, []),
+    "atucker_selector_predict": (_i32, [_vp, _i32, _vp, _vp]),
+    "atucker_mlp_forward": (_i32, [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "atucker_mlp_loss_grad": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "atucker_mlp_train": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _i32, ctypes.c_float, _vp,
+                                 _vp]),
 }
 
 
@@ -140,17 +156,25 @@ class Plan:
 
     def __init__(self, dims, ranks, mode_order=None, solver=None, precision: int = FP32, als_sweeps: int = 5,
                  seed: int = 0, stream=None, eig_arith: int | None = None, sync: bool = False,
-                 eig_method: int | None = None):
+                 eig_method: int | None = None, classes=None):
+        """solver: per-mode EIG / ALS / AUTO (learned selector); classes: per-mode
+        atucker_mode_class values instead (atucker_plan_create_classes)."""
         self.dims = [int(d) for d in dims]
         self.ranks = [int(r) for r in ranks]
         self.order = len(self.dims)
         self._h = ctypes.c_void_p(None)
         self.stream = stream
         mo = _i32arr(mode_order) if mode_order is not None else None
-        sv = _i32arr(solver) if solver is not None else None
-        _check(lib().atucker_plan_create(ctypes.byref(self._h), self.order, _i64arr(self.dims), _i64arr(self.ranks),
-                                         mo, sv, int(precision), int(als_sweeps), int(seed) & (2**64 - 1),
-                                         _stream_ptr(stream)), "atucker_plan_create")
+        if classes is not None:
+            _check(lib().atucker_plan_create_classes(ctypes.byref(self._h), self.order, _i64arr(self.dims),
+                                                     _i64arr(self.ranks), mo, _i32arr(classes), int(precision),
+                                                     int(als_sweeps), int(seed) & (2**64 - 1), _stream_ptr(stream)),
+                   "atucker_plan_create_classes")
+        else:
+            sv = _i32arr(solver) if solver is not None else None
+            _check(lib().atucker_plan_create(ctypes.byref(self._h), self.order, _i64arr(self.dims),
+                                             _i64arr(self.ranks), mo, sv, int(precision), int(als_sweeps),
+                                             int(seed) & (2**64 - 1), _stream_ptr(stream)), "atucker_plan_create")
         if eig_arith is not None:
             _check(lib().atucker_plan_set_option(self._h, OPT_EIG_ARITH, int(eig_arith)), "set_option")
         if sync:
@@ -198,6 +222,18 @@ class Plan:
         buf = (ctypes.c_double * 10)()
         _check(lib().atucker_plan_timings(self._h, buf, 10), "atucker_plan_timings")
         return dict(zip(PHASES, list(buf)))
+
+    def mode_timings(self):
+        """Per-mode device ms (by mode index) since the last read (atucker_plan_mode_timings)."""
+        buf = (ctypes.c_double * self.order)()
+        _check(lib().atucker_plan_mode_timings(self._h, buf, self.order), "atucker_plan_mode_timings")
+        return list(buf)
+
+    @property
+    def classes(self):
+        buf = _i32arr([0] * self.order)
+        _check(lib().atucker_plan_classes(self._h, buf), "atucker_plan_classes")
+        return list(buf)
 
     def sync(self):
         _check(lib().atucker_plan_sync(self._h), "atucker_plan_sync")

@@ -133,10 +133,15 @@ struct Arena {
 
 // ------------------------------------------------------------ kernel entry points
 // FP32 CUDA-core contractions (fp32_ops.cu).
-size_t gram_scratch_bytes(const View& v);
+// Gram row tile the float32 engine picks for a mode of size n (128, 64 or 32).
+int gram_tile(int64_t n);
+// True once atucker_selector_set has loaded a selector (selector.cu).
+bool selector_loaded();
+// `bm` forces the Gram row tile (32, 64 or 128); 0 picks it from n.
+size_t gram_scratch_bytes(const View& v, int bm = 0);
 // `mid` (nullable) is recorded between the partial-tile kernel and the reduction.
 int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st,
-             cudaEvent_t mid = nullptr);
+             cudaEvent_t mid = nullptr, int bm = 0);
 // As gram_f32, with the number of split-K partials capped to fit scratch_bytes.
 int gram_f32_fixed_scratch(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes,
                            cudaStream_t st);

@@ -420,6 +420,8 @@ ttm_co_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, co
 }
 
 // ------------------------------------------------------------ host side
+int gram_tile(int64_t n) { return n > 64 ? 128 : (n > 32 ? 64 : 32); }
+
 namespace {
 struct SplitPlan {
   int nsplit;
@@ -438,7 +440,7 @@ SplitPlan choose_split(int64_t J, int ntiles) {
   nsplit = ceil_div(J, kc);
   return {(int)std::max<int64_t>(1, nsplit), kc};
 }
-int gram_bm(int64_t n) { return n > 64 ? 128 : (n > 32 ? 64 : 32); }
+int gram_bm(int64_t n) { return gram_tile(n); }
 int cross_bn(int64_t R) { return R > 64 ? 128 : (R > 32 ? 64 : (R > 16 ? 32 : 16)); }
 }  // namespace
 
@@ -447,9 +449,9 @@ struct GramPlan {
   int bm, T, nt;
   SplitPlan d, o;
 };
-static GramPlan gram_plan(const View& v) {
+static GramPlan gram_plan(const View& v, int bm_force = 0) {
   GramPlan g;
-  g.bm = gram_bm(v.n);
+  g.bm = (bm_force == 32 || bm_force == 64 || bm_force == 128) ? bm_force : gram_bm(v.n);
   g.T = (int)ceil_div(v.n, g.bm);
   g.nt = g.T * (g.T + 1) / 2;
   g.d = choose_split(v.J(), g.T);
@@ -457,20 +459,20 @@ static GramPlan gram_plan(const View& v) {
   return g;
 }
 
-size_t gram_scratch_bytes(const View& v) {
-  GramPlan g = gram_plan(v);
+size_t gram_scratch_bytes(const View& v, int bm) {
+  GramPlan g = gram_plan(v, bm);
   return (size_t)std::max(g.d.nsplit, g.o.nsplit) * g.nt * g.bm * g.bm * sizeof(float);
 }
 
 int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st,
-             cudaEvent_t mid) {
+             cudaEvent_t mid, int bm) {
   if (v.n <= 0) return ATK_OK;
   if (v.J() == 0) {
     ATK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * v.n * v.n, st));
     return ATK_OK;
   }
-  GramPlan g = gram_plan(v);
-  if (gram_scratch_bytes(v) > scratch_bytes) {
+  GramPlan g = gram_plan(v, bm);
+  if (gram_scratch_bytes(v, bm) > scratch_bytes) {
     set_error("gram_f32: scratch too small");
     return ATK_EINVAL;
   }

@@ -115,6 +115,7 @@ struct atucker_plan_s {
   int order = 0;
   int64_t dims[8], ranks[8], foff[8];
   int mode_order[8], solver[8];
+  int cls[8], eigm[8], gbm[8];  // per-mode class, eigensolver method (-1 = plan's), Gram row tile (0 = auto)
   int precision = ATK_FP32, als_sweeps = 5;
   uint64_t seed = 0;
   cudaStream_t st = nullptr;
@@ -136,6 +137,7 @@ struct atucker_plan_s {
   size_t evnext = 0;
   struct Rec { int phase; cudaEvent_t a, b; };
   std::vector<Rec> recs;
+  std::vector<Rec> mrecs;  // per-mode records: phase = mode index
   long long gram_launches = 0, runs = 0, launches_mark = 0;
   cudaEvent_t ev() {
     if (evnext == evpool.size()) {
@@ -177,7 +179,10 @@ static int validate(int order, const int64_t* dims, const int64_t* ranks, const 
   }
   for (int k = 0; k < order; ++k) {
     int s = solver ? solver[k] : ATK_EIG;
-    if (s != ATK_EIG && s != ATK_ALS) { set_error("solver_per_mode entries must be 0 (EIG) or 1 (ALS)"); return ATK_EINVAL; }
+    if (s != ATK_EIG && s != ATK_ALS && s != ATK_AUTO) {
+      set_error("solver_per_mode entries must be 0 (EIG), 1 (ALS) or -1 (AUTO)");
+      return ATK_EINVAL;
+    }
     if (s == ATK_EIG && dims[k] > 1024) { set_error("EIG modes need I_n <= 1024"); return ATK_EUNSUPPORTED; }
   }
   return ATK_OK;
@@ -200,7 +205,7 @@ static int plan_alloc(atucker_plan_s* p) {
     maxr = std::max(maxr, R);
     if (p->solver[n] == ATK_EIG) {
       s_elems = std::max(s_elems, (size_t)(v.n * v.n));
-      scratch = std::max(scratch, gram_scratch_bytes(v));
+      scratch = std::max(scratch, gram_scratch_bytes(v, p->gbm[n]));
       if (p->precision != ATK_FP32) scratch = std::max(scratch, tc_gram_scratch_bytes(v, p->precision));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP64));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP32));
@@ -273,6 +278,39 @@ int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, co
   if (!plan) { set_error("plan is null"); return ATK_EINVAL; }
   *plan = nullptr;
   ATK_TRY(validate(order, dims, ranks, mode_order, solver_per_mode));
+  int cls[8];
+  bool any_auto = false;
+  for (int k = 0; k < order; ++k) {
+    const int s = solver_per_mode ? solver_per_mode[k] : ATK_EIG;
+    cls[k] = s == ATK_ALS ? ATK_CLASS_ALS : ATK_CLASS_EIG;
+    any_auto = any_auto || s == ATK_AUTO;
+  }
+  if (any_auto) {
+    double feat[8 * ATK_SELECTOR_FEATURES];
+    int pick[8];
+    ATK_TRY(atucker_mode_features(order, dims, ranks, mode_order, feat));
+    if (selector_loaded() && atucker_selector_predict(feat, order, pick, nullptr) == ATK_OK) {
+      for (int k = 0; k < order; ++k)
+        if (solver_per_mode[k] == ATK_AUTO) cls[k] = pick[k];
+    }
+  }
+  return atucker_plan_create_classes(plan, order, dims, ranks, mode_order, cls, precision, als_sweeps, seed,
+                                     stream);
+}
+
+int atucker_plan_create_classes(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
+                                const int* mode_order, const int* class_per_mode, int precision, int als_sweeps,
+                                uint64_t seed, void* stream) {
+  if (!plan) { set_error("plan is null"); return ATK_EINVAL; }
+  *plan = nullptr;
+  if (!class_per_mode) { set_error("class_per_mode is null"); return ATK_EINVAL; }
+  int solver[8];
+  if (order < 1 || order > 8) { set_error("order must be in [1, 8]; dims/ranks non-null"); return ATK_EINVAL; }
+  for (int k = 0; k < order; ++k) {
+    if (class_per_mode[k] < 0 || class_per_mode[k] >= ATK_NUM_CLASSES) { set_error("unknown mode class"); return ATK_EINVAL; }
+    solver[k] = class_per_mode[k] == ATK_CLASS_ALS ? ATK_ALS : ATK_EIG;
+  }
+  ATK_TRY(validate(order, dims, ranks, mode_order, solver));
   if (precision < ATK_FP32 || precision > ATK_FP8E4M3) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
   atucker_plan_s* p = new atucker_plan_s();
   p->order = order;
@@ -281,9 +319,20 @@ int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, co
     p->dims[k] = dims[k];
     p->ranks[k] = ranks[k];
     p->mode_order[k] = mode_order ? mode_order[k] : k;
-    p->solver[k] = solver_per_mode ? solver_per_mode[k] : ATK_EIG;
+    p->solver[k] = solver[k];
+    p->cls[k] = class_per_mode[k];
     p->foff[k] = off;
     off += dims[k] * ranks[k];
+  }
+  // Per-mode eigensolver method and Gram row tile.  The tile depends on the
+  // mode's size, which is fixed by the shape whatever the mode order.
+  for (int k = 0; k < order; ++k) {
+    const int c = p->cls[k];
+    const bool jac = c == ATK_CLASS_EIG_JACOBI || c == ATK_CLASS_EIG_JACOBI_SMALL;
+    const bool small = c == ATK_CLASS_EIG_SMALL || c == ATK_CLASS_EIG_JACOBI_SMALL;
+    p->eigm[k] = jac ? ATK_EIG_FULL_JACOBI : -1;
+    const int t = gram_tile(dims[k]);
+    p->gbm[k] = small ? std::max(32, t / 2) : 0;
   }
   p->fac_total = off;
   p->total = 1;
@@ -296,6 +345,26 @@ int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, co
   int s = plan_alloc(p);
   if (s != ATK_OK) { atucker_plan_destroy(p); return s; }
   *plan = p;
+  return ATK_OK;
+}
+
+int atucker_plan_classes(atucker_plan_t p, int* class_out) {
+  if (!p || !class_out) { set_error("plan_classes: null argument"); return ATK_EINVAL; }
+  for (int k = 0; k < p->order; ++k) class_out[k] = p->cls[k];
+  return ATK_OK;
+}
+
+int atucker_plan_mode_timings(atucker_plan_t p, double* out, int count) {
+  if (!p || !out || count < p->order) { set_error("mode_timings: need a plan and one slot per mode"); return ATK_EINVAL; }
+  ATK_CUDA(cudaStreamSynchronize(p->st));
+  for (int i = 0; i < count; ++i) out[i] = 0.0;
+  for (const auto& r : p->mrecs) {
+    float ms = 0.f;
+    ATK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    out[r.phase] += ms;
+  }
+  p->mrecs.clear();
+  if (p->recs.empty()) p->evnext = 0;
   return ATK_OK;
 }
 
@@ -369,6 +438,7 @@ int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* fa
   for (int step = 0; step < p->order; ++step) {
     const int n = p->mode_order[step];
     const View v = make_view(p->order, cur, n);
+    cudaEvent_t e_mode = e_prev;
     const int64_t R = p->ranks[n];
     float* out = (step == p->order - 1) ? core_out : p->buf[step & 1];
     float* U32 = factors_out + p->foff[n];
@@ -377,7 +447,7 @@ int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* fa
       // S = Y_(n) Y_(n)^T; U = leading eigenvectors; Y' = Y x_n U^T.
       cudaEvent_t mid = tm ? p->ev() : nullptr;
       if (p->precision == ATK_FP32) {
-        ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid));
+        ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid, p->gbm[n]));
       } else {
         ATK_TRY(tc_gram(Y, v, p->precision, p->S, (float*)p->scratch, p->scratch_bytes, p->dev_status, st));
         if (mid) ATK_CUDA(cudaEventRecord(mid, st));
@@ -388,7 +458,8 @@ int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* fa
         p->gram_launches++;
       }
       ATK_TRY(mark(PH_GRAM_REDUCE));
-      ATK_TRY(eig_top(p->S, v.n, R, p->eig_arith, p->eig_method, p->max_sweeps, U32, p->U64, nullptr, disc,
+      const int em = p->eigm[n] >= 0 ? p->eigm[n] : p->eig_method;
+      ATK_TRY(eig_top(p->S, v.n, R, p->eig_arith, em, p->max_sweeps, U32, p->U64, nullptr, disc,
                       p->dev_status, p->scratch, p->scratch_bytes, st));
       ATK_TRY(mark(PH_EIG));
       ATK_TRY(ttm_f32(Y, v, U32, R, out, st));
@@ -404,6 +475,7 @@ int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* fa
         ATK_TRY(mark(PH_OTHER));
       }
     }
+    if (tm) p->mrecs.push_back({n, e_mode, e_prev});
     cur[n] = R;
     Y = out;
   }
@@ -450,6 +522,7 @@ int atucker_plan_timings(atucker_plan_t p, double* out, int count) {
   out[PH_TOTAL + 2] = (double)(now - p->launches_mark);
   out[PH_TOTAL + 3] = (double)p->runs;
   p->recs.clear();
+  p->mrecs.clear();  // per-mode records are read first (atucker_plan_mode_timings) or dropped here
   p->evnext = 0;
   p->gram_launches = p->runs = 0;
   p->launches_mark = now;

@@ -1,0 +1,327 @@
+"""Learned per-mode solver-and-tile selector (Sec. IV-C, with an MLP in place of
+the paper's decision tree).
+
+Every step here is a call into the CUDA library: features come from
+``atucker_mode_features``, the network is trained on the GPU by
+``atucker_mlp_train`` (the project's own forward/backward/Adam kernels), and
+plans created with solver ``AUTO`` run the library's host-side inference
+(``atucker_selector_predict``).  This module only marshals data.
+
+Labels are measured by this build: for each shape, every mode is timed under
+every class (CUDA events around each mode inside the plan), and the network
+learns, per class, y = log2(t_class / t_fastest) (capped at 4, i.e. 16x).  The
+selector takes the class with the smallest prediction.
+
+``python -m paper_2010_10131_b300.selector collect`` measures the timing set on
+the current GPU; ``... train`` fits the network and writes the weights that
+``install()`` loads.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import (AUTO, NUM_CLASSES, CLASS_NAMES, SELECTOR_FEATURES, SELECTOR_HIDDEN, Plan, _check, _i32arr, _i64arr,
+               lib)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS = os.path.join(HERE, "selector_weights.json")
+TIMINGS = os.path.join(HERE, "selector_timings.json")
+TARGET_CAP = 4.0  # log2 of the largest slowdown the network is asked to resolve
+
+
+# ---------------------------------------------------------------- features
+def mode_features(dims, ranks, mode_order=None) -> np.ndarray:
+    """Model inputs (log2, not standardised) of every mode: (N, 12), row n = mode n."""
+    n = len(dims)
+    out = np.zeros(n * SELECTOR_FEATURES)
+    mo = _i32arr(mode_order) if mode_order is not None else None
+    _check(lib().atucker_mode_features(n, _i64arr(dims), _i64arr(ranks), mo,
+                                       out.ctypes.data_as(ctypes.c_void_p)), "atucker_mode_features")
+    return out.reshape(n, SELECTOR_FEATURES)
+
+
+def targets(times: np.ndarray):
+    """Per-row log2 slowdown vs the fastest measured class, and its mask."""
+    t = np.asarray(times, dtype=np.float64)
+    mask = np.isfinite(t) & (t > 0)
+    best = np.where(mask, t, np.inf).min(axis=1, keepdims=True)
+    y = np.where(mask, np.log2(np.where(mask, t, 1.0) / best), 0.0)
+    return np.minimum(y, TARGET_CAP), mask.astype(np.float64)
+
+
+# ------------------------------------------------------------------ network
+def param_count(n_in=SELECTOR_FEATURES, hidden=SELECTOR_HIDDEN, n_out=NUM_CLASSES) -> int:
+    return int(lib().atucker_mlp_param_count(n_in, hidden, n_out))
+
+
+def init_params(seed: int = 0, n_in=SELECTOR_FEATURES, hidden=SELECTOR_HIDDEN, n_out=NUM_CLASSES) -> np.ndarray:
+    """He-normal weights, zero biases (float32, the layout of atucker_mlp_param_count)."""
+    g = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((n_in, hidden), (hidden, hidden), (hidden, n_out)):
+        parts.append(g.standard_normal(fan_out * fan_in) * math.sqrt(2.0 / fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+class GpuMLP:
+    """Device-resident network trained by the library's kernels."""
+
+    def __init__(self, params: np.ndarray, n_in=SELECTOR_FEATURES, hidden=SELECTOR_HIDDEN, n_out=NUM_CLASSES):
+        import torch
+        self.torch = torch
+        self.shape = (n_in, hidden, n_out)
+        self.params = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+        self.state = torch.zeros(2 * self.params.numel(), device="cuda")
+        self.steps = 0
+
+    def _stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def _dev(self, a):
+        t = self.torch
+        return a if isinstance(a, t.Tensor) else t.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+    def forward(self, X) -> np.ndarray:
+        X = self._dev(X)
+        B = X.shape[0]
+        out = self.torch.empty(B, self.shape[2], device="cuda")
+        _check(lib().atucker_mlp_forward(ctypes.c_void_p(X.data_ptr()), B, *self.shape,
+                                         ctypes.c_void_p(self.params.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         self._stream()), "atucker_mlp_forward")
+        return out.cpu().numpy()
+
+    def loss_grad(self, X, Y, M):
+        X, Y, M = self._dev(X), self._dev(Y), self._dev(M)
+        loss = self.torch.empty(1, device="cuda")
+        grad = self.torch.empty_like(self.params)
+        _check(lib().atucker_mlp_loss_grad(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                           ctypes.c_void_p(M.data_ptr()), X.shape[0], *self.shape,
+                                           ctypes.c_void_p(self.params.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                           ctypes.c_void_p(grad.data_ptr()), self._stream()), "atucker_mlp_loss_grad")
+        return float(loss.item()), grad.cpu().numpy()
+
+    def train(self, X, Y, M, steps: int, lr: float) -> np.ndarray:
+        X, Y, M = self._dev(X), self._dev(Y), self._dev(M)
+        losses = self.torch.empty(max(steps, 1), device="cuda")
+        _check(lib().atucker_mlp_train(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                       ctypes.c_void_p(M.data_ptr()), X.shape[0], *self.shape,
+                                       ctypes.c_void_p(self.params.data_ptr()), ctypes.c_void_p(self.state.data_ptr()),
+                                       int(steps), int(self.steps), ctypes.c_float(lr),
+                                       ctypes.c_void_p(losses.data_ptr()), self._stream()), "atucker_mlp_train")
+        self.steps += steps
+        return losses[:steps].cpu().numpy()
+
+    def host_params(self) -> np.ndarray:
+        return self.params.cpu().numpy()
+
+
+# ---------------------------------------------------------- selector state
+def pack(fmean, fscale, params) -> np.ndarray:
+    return np.concatenate([np.asarray(fmean, np.float32), np.asarray(fscale, np.float32),
+                           np.asarray(params, np.float32)])
+
+
+def install(packed=None, path: str = WEIGHTS) -> bool:
+    """Load a selector into the library (atucker_selector_set); from `path` when
+    no packed vector is given.  Returns False when there is nothing to load."""
+    if packed is None:
+        if not os.path.exists(path):
+            return False
+        with open(path) as f:
+            packed = np.asarray(json.load(f)["packed"], dtype=np.float32)
+    packed = np.ascontiguousarray(packed, dtype=np.float32)
+    _check(lib().atucker_selector_set(packed.ctypes.data_as(ctypes.c_void_p), packed.size), "atucker_selector_set")
+    return True
+
+
+def predict(features: np.ndarray):
+    """(classes, scores) from the loaded selector (host inference in the library)."""
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    rows = f.shape[0]
+    cls = (ctypes.c_int * rows)()
+    scores = np.zeros(rows * NUM_CLASSES, dtype=np.float32)
+    _check(lib().atucker_selector_predict(f.ctypes.data_as(ctypes.c_void_p), rows, cls,
+                                          scores.ctypes.data_as(ctypes.c_void_p)), "atucker_selector_predict")
+    return np.array(list(cls)), scores.reshape(rows, NUM_CLASSES)
+
+
+# ------------------------------------------------------------ timing labels
+def random_tucker_gpu(dims, ranks, seed: int, noise: float = 1e-3):
+    """Random Tucker tensor + noise built on the GPU with torch (timing inputs
+    only; the content sets the spectra the solvers see).  Column-major flat."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(int(seed))
+    x = torch.randn(*[int(r) for r in reversed(ranks)], device="cuda", generator=g)  # C order = reversed dims
+    for n in range(len(dims)):
+        u, _ = torch.linalg.qr(torch.randn(int(dims[n]), int(ranks[n]), device="cuda", generator=g))
+        ax = len(dims) - 1 - n
+        x = torch.movedim(torch.tensordot(u, x, dims=([1], [ax])), 0, ax)
+    x = x + noise * torch.randn(x.shape, device="cuda", generator=g)
+    return x.contiguous().view(-1)
+
+
+def time_shape(dims, ranks, x, reps: int = 2, slow_ms: float = 1500.0):
+    """Per-mode ms of every class: array (N, NUM_CLASSES), NaN where a class
+    failed.  One warm-up run per shape, then the median of `reps` timed runs
+    per class (one, when a mode already took over `slow_ms`)."""
+    import torch
+    N = len(dims)
+    out = np.full((N, NUM_CLASSES), np.nan)
+    for c in range(NUM_CLASSES):
+        try:
+            p = Plan(dims, ranks, classes=[c] * N)
+        except Exception:
+            continue
+        try:
+            core = torch.empty(p.core_numel, device="cuda")
+            fac = torch.empty(p.factors_numel, device="cuda")
+            if c == 0:  # one warm-up per shape
+                p.run(x, core, fac)
+                p.sync()
+            p.set_timing(True)
+            runs = []
+            for _ in range(max(reps, 1)):
+                p.run(x, core, fac)
+                p.sync()
+                runs.append(p.mode_timings())
+                p.timings()  # drop the phase records
+                if max(runs[-1]) > slow_ms:
+                    break
+            out[:, c] = np.median(np.array(runs), axis=0)
+        except Exception:
+            pass
+        finally:
+            p.close()
+    return out
+
+
+def collect(shapes, seed: int = 0, reps: int = 2, log=None):
+    """Timing set for `shapes` [(dims, ranks)]: list of per-shape (N, K) arrays."""
+    import torch
+    res = []
+    for i, (dims, ranks) in enumerate(shapes):
+        t0 = time.time()
+        x = random_tucker_gpu(dims, ranks, seed * 100003 + i)
+        res.append(time_shape(dims, ranks, x, reps=reps))
+        del x
+        torch.cuda.empty_cache()
+        if log:
+            log(f"{i + 1}/{len(shapes)} {dims} {ranks} {time.time() - t0:.1f}s")
+    return res
+
+
+# ------------------------------------------------------------- train / eval
+def dataset(shapes, times):
+    """Stack (features, times) of every (shape, mode)."""
+    F = np.concatenate([mode_features(d, r) for d, r in shapes])
+    T = np.concatenate([np.asarray(t, dtype=np.float64) for t in times])
+    return F, T
+
+
+def fit(F, T, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
+    """Standardise the features, train on the GPU; returns (packed vector, losses)."""
+    fmean = F.mean(axis=0)
+    fscale = F.std(axis=0)
+    fscale[fscale < 1e-6] = 1.0
+    X = ((F - fmean) / fscale).astype(np.float32)
+    Y, M = targets(T)
+    net = GpuMLP(init_params(seed))
+    losses = net.train(X, Y.astype(np.float32), M.astype(np.float32), steps, lr)
+    return pack(fmean, fscale, net.host_params()), losses
+
+
+def regret(T, chosen):
+    """Sum of chosen times / sum of best times - 1, over rows with a measured choice."""
+    T = np.asarray(T, dtype=np.float64)
+    rows = np.arange(len(T))
+    tc = T[rows, chosen]
+    best = np.nanmin(T, axis=1)
+    ok = np.isfinite(tc) & np.isfinite(best)
+    return float(tc[ok].sum() / best[ok].sum() - 1.0), ok
+
+
+def evaluate(F, T, shapes_rows=None):
+    """Regret of the loaded selector on (F, T), and its gain over fixed classes."""
+    cls, _ = predict(F)
+    r, ok = regret(T, cls)
+    best = np.nanmin(T, axis=1)
+    out = {"rows": int(ok.sum()), "regret": r,
+           "chosen_ms": float(T[np.arange(len(T)), cls][ok].sum()), "best_ms": float(best[ok].sum()),
+           "class_counts": {CLASS_NAMES[k]: int((cls == k).sum()) for k in range(NUM_CLASSES)}}
+    for k, name in enumerate(CLASS_NAMES):
+        tk = T[:, k]
+        m = ok & np.isfinite(tk)
+        out[f"fixed_{name}_ms"] = float(tk[m].sum())
+        out[f"gain_vs_fixed_{name}"] = float(tk[m].sum() / T[np.arange(len(T)), cls][m].sum())
+    if shapes_rows is not None:
+        per_shape = []
+        for a, b in shapes_rows:
+            rr, _ = regret(T[a:b], cls[a:b])
+            per_shape.append(rr)
+        out["max_shape_regret"] = float(np.max(per_shape))
+    return out
+
+
+def shape_rows(shapes):
+    rows, o = [], 0
+    for d, _ in shapes:
+        rows.append((o, o + len(d)))
+        o += len(d)
+    return rows
+
+
+RMAX = 128  # the library's rank limit (atucker_plan_create)
+
+
+def selector_shapes(count: int = 256, seed: int = 0):
+    """The selector workload: synth.selector_shapes with every rank clamped to
+    the library's limit of 128 (then made Tucker-feasible again)."""
+    import synth
+    return [(list(d), synth.feasible_ranks(d, [min(r, RMAX) for r in rr]))
+            for d, rr in synth.selector_shapes(count=count, seed=seed)]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_2010_10131_b300.selector")
+    ap.add_argument("cmd", choices=["collect", "train"])
+    ap.add_argument("--count", type=int, default=256)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--train", type=int, default=192)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--seed", type=int, default=0, help="shape-set seed (collect)")
+    ap.add_argument("--timings", default=TIMINGS, help="timing set (written by collect, read by train)")
+    ap.add_argument("--weights", default=WEIGHTS, help="weights written by train")
+    args = ap.parse_args(argv)
+    shapes = selector_shapes(args.count, seed=args.seed)
+    if args.cmd == "collect":
+        times = collect(shapes, seed=args.seed, reps=args.reps, log=lambda s: print(s, flush=True))
+        with open(args.timings, "w") as f:
+            json.dump({"shapes": shapes, "classes": list(CLASS_NAMES),
+                       "times_ms": [np.where(np.isfinite(t), t, -1.0).tolist() for t in times]}, f)
+        return 0
+    with open(args.timings) as f:
+        data = json.load(f)
+    shapes = [(list(d), list(r)) for d, r in data["shapes"]]
+    times = [np.where(np.asarray(t) < 0, np.nan, np.asarray(t)) for t in data["times_ms"]]
+    n_tr = args.train
+    F, T = dataset(shapes[:n_tr], times[:n_tr])
+    packed, losses = fit(F, T, steps=args.steps)
+    with open(args.weights, "w") as f:
+        json.dump({"packed": packed.tolist(), "train_shapes": n_tr, "steps": args.steps,
+                   "final_loss": float(losses[-1])}, f)
+    install(packed)
+    Ft, Tt = dataset(shapes[n_tr:], times[n_tr:])
+    print(json.dumps(evaluate(Ft, Tt, shape_rows(shapes[n_tr:]))))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -290,3 +290,62 @@ def test_feasible_ranks():
     for n in range(3):
         others = int(np.prod([r[k] for k in range(3) if k != n]))
         assert 1 <= r[n] <= min((30, 40, 50)[n], others)
+
+
+# ----------------------------------------------------------------- selector MLP
+from oracle import mlp as omlp  # noqa: E402
+
+_IN, _H, _K = 12, 64, 5
+
+
+def _mlp_case(seed, B=40):
+    g = np.random.default_rng(seed)
+    p = g.standard_normal(omlp.param_count(_IN, _H, _K)) * 0.3
+    X = g.standard_normal((B, _IN))
+    Y = g.standard_normal((B, _K))
+    M = (g.random((B, _K)) > 0.2).astype(np.float64)
+    return p, X, Y, M
+
+
+def test_mlp_gradient_central_differences():
+    """The backpropagated gradient against central differences of the loss on
+    20 randomly chosen parameters (the loss is piecewise smooth: ReLU kinks
+    are avoided by the small step)."""
+    p, X, Y, M = _mlp_case(91)
+    L, g = omlp.grad(p, X, Y, M, _IN, _H, _K)
+    assert abs(L - omlp.loss(p, X, Y, M, _IN, _H, _K)) <= 1e-12 * max(1.0, L)
+    idx = np.random.default_rng(92).choice(p.size, 20, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (omlp.loss(p + e, X, Y, M, _IN, _H, _K) - omlp.loss(p - e, X, Y, M, _IN, _H, _K)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_mlp_dead_hidden_layer_closed_form():
+    """With b2 very negative every a2 is zero: the output is b3 for every row,
+    so dL/db3 = 2 sum_b M (b3 - Y) / sum M and every other gradient is zero."""
+    p, X, Y, M = _mlp_case(93)
+    W1, b1, W2, b2, W3, b3 = omlp.unpack(p, _IN, _H, _K)
+    q = p.copy()
+    off_b2 = _H * _IN + _H + _H * _H
+    q[off_b2:off_b2 + _H] = -1e6
+    out, _ = omlp.forward(q, X, _IN, _H, _K)
+    np.testing.assert_allclose(out, np.broadcast_to(b3, out.shape), rtol=0, atol=0)
+    L, g = omlp.grad(q, X, Y, M, _IN, _H, _K)
+    expect_b3 = 2 * (M * (b3[None, :] - Y)).sum(axis=0) / M.sum()
+    np.testing.assert_allclose(g[-_K:], expect_b3, rtol=1e-12)
+    assert np.all(g[:-_K] == 0.0)
+
+
+def test_mlp_adam_first_step_is_sign_step():
+    """Adam's first bias-corrected step is lr * g / (|g| + eps): every parameter
+    with a non-zero gradient moves by lr (to 1e-6) against its sign."""
+    p, X, Y, M = _mlp_case(94)
+    _, g = omlp.grad(p, X, Y, M, _IN, _H, _K)
+    q, m, v = omlp.adam_step(p, g, np.zeros_like(p), np.zeros_like(p), 1, 1e-2)
+    nz = np.abs(g) > 1e-4
+    np.testing.assert_allclose((p - q)[nz], 1e-2 * np.sign(g[nz]), rtol=1e-3)
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
