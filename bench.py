@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -254,36 +255,55 @@ def run_ours(args):
               ("gram", "gram_reduce", "eig", "ttm", "als", "norms", "total")}
     launches = int(sum(t["launches"] for t in tims))
 
+    def time_variant(precision=atk.FP32, mode_solver=atk.EIG):
+        """ms per step and relerr of the same workload under other plan settings
+        (`mode_solver` for every mode: EIG, ALS or AUTO)."""
+        vplans = []
+        for (dims, ranks), x in zip(TENSORS, xs):
+            vp = atk.Plan(dims, ranks, solver=[mode_solver] * len(dims), precision=precision, stream=stream)
+            vplans.append((vp, torch.empty(vp.core_numel, device="cuda"), torch.empty(vp.factors_numel, device="cuda")))
+        for _ in range(args.warmup):
+            for (vp, c, f), x in zip(vplans, xs):
+                vp.run(x, c, f)
+        torch.cuda.synchronize()
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        for _ in range(args.steps):
+            for (vp, c, f), x in zip(vplans, xs):
+                vp.run(x, c, f)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        vms = m0.elapsed_time(m1) / max(args.steps, 1)
+        rel = [relerr_identity(xn, c) for xn, (_, c, _) in zip(xnps, vplans)]
+        classes = [vp.classes for vp, _, _ in vplans]
+        for vp, _, _ in vplans:
+            vp.close()
+        return vms, rel, classes
+
+    rel_plain = [relerr_identity(xn, core) for xn, (_, core, _) in zip(xnps, plans)]
     # Mixed precision on the same tensors: the tensor-core Gram forms, timed
     # like the plain step, each compared by relative error with the plain output.
     mixed = None
     if not args.no_mixed:
-        rel_plain = [relerr_identity(xn, core) for xn, (_, core, _) in zip(xnps, plans)]
         mixed = {"relerr_plain": rel_plain, "forms": {}}
         for name, prec in (("BF16X3", atk.BF16X3), ("TF32", atk.TF32), ("BF16", atk.BF16)):
-            mplans = []
-            for (dims, ranks), x in zip(TENSORS, xs):
-                mp = atk.Plan(dims, ranks, solver=[0] * len(dims), precision=prec, stream=stream)
-                mplans.append((mp, torch.empty(mp.core_numel, device="cuda"),
-                               torch.empty(mp.factors_numel, device="cuda")))
-            for _ in range(args.warmup):
-                for (mp, c, f), x in zip(mplans, xs):
-                    mp.run(x, c, f)
-            torch.cuda.synchronize()
-            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            m0.record(stream)
-            for _ in range(args.steps):
-                for (mp, c, f), x in zip(mplans, xs):
-                    mp.run(x, c, f)
-            m1.record(stream)
-            torch.cuda.synchronize()
-            mms = m0.elapsed_time(m1) / max(args.steps, 1)
-            rel = [relerr_identity(xn, c) for xn, (_, c, _) in zip(xnps, mplans)]
+            mms, rel, _ = time_variant(precision=prec)
             mixed["forms"][name] = {"ms_per_step": mms, "value": in_bytes / (mms * 1e-3) / 1e9,
                                     "speedup_vs_plain": ms / mms, "relerr": rel,
                                     "max_relerr_delta_vs_plain": max(abs(a - b) for a, b in zip(rel, rel_plain))}
-            for mp, _, _ in mplans:
-                mp.close()
+    # The solvers on the same workload: every mode ALS (Alg. 3, 5 sweeps), and
+    # every mode chosen by the learned selector when its weights are present.
+    solvers = None
+    if not args.no_mixed:
+        solvers = {"EIG": {"ms_per_step": ms, "value": value / ws, "relerr": rel_plain}}
+        ams, arel, _ = time_variant(mode_solver=atk.ALS)
+        solvers["ALS"] = {"ms_per_step": ams, "value": in_bytes / (ams * 1e-3) / 1e9, "relerr": arel,
+                          "speedup_vs_EIG": ms / ams}
+        from paper_2010_10131_b300 import selector as atk_selector
+        if atk_selector.install():
+            sms, srel, scls = time_variant(mode_solver=atk.AUTO)
+            solvers["AUTO"] = {"ms_per_step": sms, "value": in_bytes / (sms * 1e-3) / 1e9, "relerr": srel,
+                               "speedup_vs_EIG": ms / sms, "classes": scls}
 
     # End to end through the C ABI with host buffers (copies inside the timed region).
     cores_h = [torch.empty(p.core_numel).pin_memory() for p, _, _ in plans]
@@ -324,6 +344,7 @@ def run_ours(args):
                          "ms_per_step": gram_ms / max(args.steps, 1)},
             "phases_ms_per_step": phases,
             "mixed": mixed,
+            "solvers": solvers,
             "e2e": {"value": in_bytes / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -350,6 +371,12 @@ def run_case(args):
     import paper_2010_10131_b300 as atk
     prec = args.precision
     kind, _, shape = args.case.partition(":")
+    if kind == "selector":
+        print(json.dumps({"case": "selector", **run_selector(args)}), flush=True)
+        return 0
+    if kind == "precision":
+        print(json.dumps({"case": "precision", "sweep": run_precision(args)}), flush=True)
+        return 0
     if kind == "batched":
         out = run_batched(args, count=int(shape) if shape else 4096)
         print(json.dumps({"case": args.case, **out}), flush=True)
@@ -467,6 +494,117 @@ def run_batched(args, count: int = 4096, serial_sample: int = 256):
         "one_at_a_time_ms": serial_ms, "one_at_a_time_sample": f"first {k} of {count} tensors, scaled",
         "speedup_vs_one_at_a_time": serial_ms / ms, "graph": True, "generate_s": gen_s,
     }
+
+
+PRECISION_SWEEP = [((768, 768, 768), 32), ((768, 768, 768), 64), ((768, 768, 768), 128), ((48, 48, 48, 48, 48), 8)]
+
+
+def decaying_tucker_gpu(dims, r_max: int, seed: int = 0, noise: float = 1e-3):
+    """The decaying-spectrum recipe of synth.decaying_tucker built on the GPU
+    with torch (the full-size inputs are too large to build on the host):
+    core Z x_1 D ... x_N D, Z ~ N(0,1) of size (2 r_max)^N, D = diag(k^-1.5),
+    orthonormal factors, signal RMS 1, plus noise N(0,1).  Column-major flat."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    N = len(dims)
+    kk = [min(2 * r_max, d) for d in dims]
+    z = torch.randn(*reversed(kk), device="cuda", generator=g)
+    for n in range(N):
+        dvec = torch.arange(1, kk[n] + 1, device="cuda", dtype=torch.float32) ** -1.5
+        shape = [1] * N
+        shape[N - 1 - n] = kk[n]
+        z = z * dvec.view(shape)
+    for n in range(N):
+        u, _ = torch.linalg.qr(torch.randn(dims[n], kk[n], device="cuda", generator=g))
+        ax = N - 1 - n
+        z = torch.movedim(torch.tensordot(u, z, dims=([1], [ax])), 0, ax)
+    z = z * (1.0 / torch.sqrt(torch.mean(z.double() ** 2))).float()
+    z = z + noise * torch.randn(z.shape, device="cuda", generator=g)
+    return z.contiguous().view(-1)
+
+
+def run_precision(args):
+    """The precision sweep: every Gram form on 768^3 (R 32, 64, 128) and 48^5
+    (R 8), decaying spectrum; time per st-HOSVD (CUDA events) and relative
+    error from the float64 norms (||X||^2 - ||G||^2, exact for EIG modes),
+    beside the float32 plan's."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    forms = (("FP32", atk.FP32), ("TF32", atk.TF32), ("BF16", atk.BF16), ("BF16X3", atk.BF16X3),
+             ("FP8E4M3", atk.FP8E4M3))
+    out = []
+    for dims, R in PRECISION_SWEEP:
+        x = decaying_tucker_gpu(dims, R)
+        nx2 = float((x.double() ** 2).sum().item())
+        ranks = [R] * len(dims)
+        row = {"dims": list(dims), "ranks": ranks, "forms": {}}
+        for name, prec in forms:
+            p = atk.Plan(dims, ranks, solver=[atk.EIG] * len(dims), precision=prec)
+            core = torch.empty(p.core_numel, device="cuda")
+            fac = torch.empty(p.factors_numel, device="cuda")
+            for _ in range(max(args.warmup, 1)):
+                p.run(x, core, fac)
+            p.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(max(args.steps, 1)):
+                p.run(x, core, fac)
+            e1.record()
+            p.sync()
+            ms = e0.elapsed_time(e1) / max(args.steps, 1)
+            g2 = float((core.double() ** 2).sum().item())
+            rel = math.sqrt(max(nx2 - g2, 0.0) / nx2)
+            row["forms"][name] = {"ms": ms, "gbs": x.numel() * 4 / (ms * 1e-3) / 1e9, "relerr": rel}
+            p.close()
+        base = row["forms"]["FP32"]
+        for v in row["forms"].values():
+            v["relerr_delta_vs_fp32"] = v["relerr"] - base["relerr"]
+            v["speedup_vs_fp32"] = base["ms"] / v["ms"]
+        out.append(row)
+        del x
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_selector(args, e2e_shapes: int = 64):
+    """The learned selector: train on the committed timing sets with the
+    library's kernels, regret on the 64 held-out shapes against exhaustive
+    search, then end to end on the held-out shapes: plans with every mode AUTO
+    (the selector) against every mode EIG (the method without it), timed with
+    CUDA events."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    from paper_2010_10131_b300 import selector
+    t0 = time.time()
+    report, packed = selector.train_and_evaluate()
+    train_s = time.time() - t0
+    selector.install(packed)
+    shapes, _ = selector.load_timings(selector.TIMINGS)
+    held = shapes[192:192 + e2e_shapes]
+    tot = {"AUTO": 0.0, "EIG": 0.0}
+    for i, (dims, ranks) in enumerate(held):
+        x = selector.random_tucker_gpu(dims, ranks, 900001 + i)
+        for name, sv in (("AUTO", atk.AUTO), ("EIG", atk.EIG)):
+            p = atk.Plan(dims, ranks, solver=[sv] * len(dims))
+            core = torch.empty(p.core_numel, device="cuda")
+            fac = torch.empty(p.factors_numel, device="cuda")
+            p.run(x, core, fac)
+            p.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(2):
+                p.run(x, core, fac)
+            e1.record()
+            p.sync()
+            tot[name] += e0.elapsed_time(e1) / 2
+            p.close()
+        del x
+        torch.cuda.empty_cache()
+    report["end_to_end"] = {"shapes": len(held), "auto_ms": tot["AUTO"], "eig_ms": tot["EIG"],
+                            "gain_vs_fixed_EIG": tot["EIG"] / tot["AUTO"],
+                            "inputs": "random Tucker + 1e-3 noise built on the GPU, new seeds"}
+    report["train_s"] = train_s
+    return report
 
 
 def main():

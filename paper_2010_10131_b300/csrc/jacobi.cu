@@ -484,8 +484,11 @@ __global__ void __launch_bounds__(TRSM_THREADS) trsm_rows_kernel(const float* __
   const int64_t i = (int64_t)blockIdx.x * TRSM_THREADS + threadIdx.x;
   if (i >= n) return;
   float* q = qs + threadIdx.x;
+  // The row's right-hand sides first (independent loads, one latency), then
+  // the substitution overwrites them with the solution in place.
+  for (int j = 0; j < m; ++j) q[TRSM_THREADS * j] = Y[i + n * j];
   for (int j = 0; j < m; ++j) {
-    float a0 = Y[i + n * j], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float a0 = q[TRSM_THREADS * j], a1 = 0.f, a2 = 0.f, a3 = 0.f;
     int t = 0;
     for (; t + 3 < j; t += 4) {
       a0 = fmaf(-L[j + m * t], q[TRSM_THREADS * t], a0);
@@ -537,18 +540,29 @@ __global__ void f32_to_f64_kernel2(const float* __restrict__ s, double* __restri
 namespace {
 struct RRBufs {
   float *Sf, *Q, *Y, *Z, *T, *LinvT, *Vb, *diag, *Wf;  // LinvT holds the Cholesky factor L
-  double *G, *W64, *theta, *res, *summary;
+  double *G, *W64, *theta, *res, *summary, *Cd;  // Cd: n x m float64 product S Q
   float* part;  // split-K partials of the m x m products
   size_t part_bytes;
 };
 size_t rr_part_bytes(int64_t n, int m) {
   View v{n, m, 1};
-  return std::max(gram_scratch_bytes(v), cross_scratch_bytes(v, m));
+  const View sv{n, n, 1};  // S's rows as the contracted index (S = S^T): S Q by split-K
+  return std::max(std::max(gram_scratch_bytes(v), cross_scratch_bytes(v, m)), cross_scratch_bytes(sv, m));
 }
 size_t rr_bytes(int64_t n, int m) {
   size_t nm = (size_t)n * m, mm = (size_t)m * m;
-  return sizeof(float) * ((size_t)n * n + 4 * nm + 3 * mm + m) + sizeof(double) * (2 * mm + 2 * m + 8) +
-         rr_part_bytes(n, m) + 16 * 256;
+  return sizeof(float) * ((size_t)n * n + 4 * nm + 3 * mm + m) + sizeof(double) * (2 * mm + 2 * m + 8 + nm) +
+         rr_part_bytes(n, m) + 17 * 256;
+}
+// out = S Q (n x m, float32) for the symmetric float32 S.  With the view
+// (lo = n, n, hi = 1) the contracted index c is S's row index and the right
+// operand P(c, r) = Q[c + n r] is column-major, as the CI kernel reads it;
+// split-K keeps many CTAs busy even for small n x m outputs, the partials are
+// summed in a fixed order, then rounded to float32.
+int sq_product(const float* Sf, int64_t n, const float* Q, int m, float* out, RRBufs& b, cudaStream_t st) {
+  const View sv{n, n, 1};
+  ATK_TRY(cross_f32(Sf, sv, Q, m, b.Cd, b.part, b.part_bytes, st));
+  return f64_to_f32(b.Cd, out, n * (int64_t)m, st);
 }
 // One CholeskyQR pass: Q = Y L^{-T} with L L^T = Y^T Y + shift I, after
 // normalising the columns of Y (in place).
@@ -603,6 +617,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   b.theta = (double*)ar.take(sizeof(double) * m);
   b.res = (double*)ar.take(sizeof(double) * m);
   b.summary = (double*)ar.take(sizeof(double) * 8);
+  b.Cd = (double*)ar.take(sizeof(double) * nm);
   b.part_bytes = rr_part_bytes(n, m);
   b.part = (float*)ar.take(b.part_bytes);
   if (!b.part) { set_error("rr: scratch too small"); return ATK_EINVAL; }
@@ -612,14 +627,14 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   ATK_LAUNCHED();
   // One power step from the random block; the loop below continues from the
   // Ritz vectors when more are needed.
-  ATK_TRY(ttm_f32(b.Sf, sv, b.Q, m, b.Y, st));  // Y = S Q
+  ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Y, b, st));  // Y = S Q
   ATK_TRY(cholqr3_f32(b.Y, b.T, b.Q, n, m, b, st));
   const int mp = m + (m & 1);
   const size_t jsm = small_smem<float>(mp);
   ATK_CUDA(cudaFuncSetAttribute(jacobi_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
   for (int it = 0; it < RR_MAXIT; ++it) {
     // Rayleigh-Ritz: Z = S Q, B = Q^T Z = W diag(theta) W^T.
-    ATK_TRY(ttm_f32(b.Sf, sv, b.Q, m, b.Z, st));
+    ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Z, b, st));
     ATK_TRY(cross_f32(b.Q, qv, b.Z, m, b.G, b.part, b.part_bytes, st));
     jacobi_small_kernel<float><<<1, 512, jsm, st>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
     ATK_LAUNCHED();
@@ -751,7 +766,10 @@ size_t refine_bytes(int64_t n, int64_t k) {
 // R vectors.  Steps:
 //  1. one subspace-iteration step, Qb <- orth(S Qb): normalise the columns,
 //     then two Newton-Schulz polar steps.  Components outside the leading
-//     k-space shrink by lambda_{k+1}/lambda_j.
+//     k-space shrink by lambda_{k+1}/lambda_j.  The Ritz block of the float32
+//     subspace iteration needs this step too: its float32 products leave
+//     about 1e-6 of each direction outside the subspace, which adds up over
+//     R = 128 columns to a projector error above 1e-4.
 //  2. Rayleigh-Ritz in float64: B = Qb^T S Qb.  The Ritz block is nearly
 //     diagonal; REFINE_ROTATION_STEPS simultaneous Jacobi steps (W from
 //     simrot_kernel, orthonormalised by two polar steps, B <- W^T B W) take
@@ -760,7 +778,7 @@ size_t refine_bytes(int64_t n, int64_t k) {
 //     The kept eigenvalues are diag(B), the float64 Rayleigh quotients, and the
 //     discarded energy is trace(S) minus their sum.
 int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, double* U64, double* lambda_out,
-               double* discarded_out, char* scratch, size_t scratch_bytes, cudaStream_t st) {
+               double* discarded_out, char* scratch, size_t scratch_bytes, cudaStream_t st, bool subspace_step) {
   Arena ar{scratch, scratch_bytes, 0};
   double* Z = (double*)ar.take(sizeof(double) * n * k);
   double* QW = (double*)ar.take(sizeof(double) * n * k);
@@ -774,12 +792,14 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
   if (!pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
   const unsigned gk = (unsigned)ceil_div(k * k, 256);
-  // 1. subspace step
-  ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
-  colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, n, k, norms);
-  ATK_LAUNCHED();
-  normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, 1e-5, Qb);
-  ATK_LAUNCHED();
+  // 1. subspace step (subspace_step = false only orthonormalises Qb)
+  if (subspace_step) {
+    ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
+    colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, n, k, norms);
+    ATK_LAUNCHED();
+    normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, 1e-5, Qb);
+    ATK_LAUNCHED();
+  }
   ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
   ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
   // 2. Rayleigh-Ritz and simultaneous rotations
@@ -911,7 +931,7 @@ int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int ma
     if (s != ATK_OK) return s;
     k = R;
   }
-  ATK_TRY(refine_f64(S, n, Qb, k, R, U64_out, lambda_out, discarded_out, rest, rest_bytes, st));
+  ATK_TRY(refine_f64(S, n, Qb, k, R, U64_out, lambda_out, discarded_out, rest, rest_bytes, st, true));
   if (U_out) ATK_TRY(f64_to_f32(U64_out, U_out, n * R, st));
   return ATK_OK;
 }

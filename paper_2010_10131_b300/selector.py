@@ -289,6 +289,42 @@ def selector_shapes(count: int = 256, seed: int = 0):
             for d, rr in synth.selector_shapes(count=count, seed=seed)]
 
 
+TIMINGS_EXTRA = os.path.join(HERE, "selector_timings_extra.json")
+
+
+def load_timings(path):
+    with open(path) as f:
+        data = json.load(f)
+    shapes = [(list(d), list(r)) for d, r in data["shapes"]]
+    times = [np.where(np.asarray(t) < 0, np.nan, np.asarray(t, dtype=np.float64)) for t in data["times_ms"]]
+    return shapes, times
+
+
+def train_and_evaluate(timings=TIMINGS, extra=TIMINGS_EXTRA, n_train: int = 192, steps: int = 4000,
+                       lr: float = 3e-3, seed: int = 0):
+    """Fit on the first n_train shapes of `timings` (the protocol of the
+    selector workload), and again with the `extra` timing set added to the
+    training data; evaluate both on the remaining shapes of `timings`.
+    Returns (report, packed vector of the better-data model)."""
+    shapes, times = load_timings(timings)
+    F, T = dataset(shapes[:n_train], times[:n_train])
+    Fh, Th = dataset(shapes[n_train:], times[n_train:])
+    rows = shape_rows(shapes[n_train:])
+    report = {"held_out_shapes": len(shapes) - n_train, "held_out_modes": int(len(Fh)),
+              "best_possible_gain_vs_fixed_EIG": float(Th[:, 0].sum() / np.nanmin(Th, axis=1).sum())}
+    packed, losses = fit(F, T, steps=steps, lr=lr, seed=seed)
+    install(packed)
+    report["train_192"] = dict(evaluate(Fh, Th, rows), train_modes=int(len(F)), final_loss=float(losses[-1]))
+    if extra and os.path.exists(extra):
+        es, et = load_timings(extra)
+        Fe, Te = dataset(es, et)
+        packed, losses = fit(np.concatenate([F, Fe]), np.concatenate([T, Te]), steps=steps, lr=lr, seed=seed)
+        install(packed)
+        report["train_192_plus_extra"] = dict(evaluate(Fh, Th, rows), train_modes=int(len(F) + len(Fe)),
+                                              extra_shapes=len(es), final_loss=float(losses[-1]))
+    return report, packed
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2010_10131_b300.selector")
     ap.add_argument("cmd", choices=["collect", "train"])
@@ -299,6 +335,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0, help="shape-set seed (collect)")
     ap.add_argument("--timings", default=TIMINGS, help="timing set (written by collect, read by train)")
     ap.add_argument("--weights", default=WEIGHTS, help="weights written by train")
+    ap.add_argument("--extra", default=TIMINGS_EXTRA, help="additional training timings (train)")
     args = ap.parse_args(argv)
     shapes = selector_shapes(args.count, seed=args.seed)
     if args.cmd == "collect":
@@ -307,19 +344,10 @@ def main(argv=None):
             json.dump({"shapes": shapes, "classes": list(CLASS_NAMES),
                        "times_ms": [np.where(np.isfinite(t), t, -1.0).tolist() for t in times]}, f)
         return 0
-    with open(args.timings) as f:
-        data = json.load(f)
-    shapes = [(list(d), list(r)) for d, r in data["shapes"]]
-    times = [np.where(np.asarray(t) < 0, np.nan, np.asarray(t)) for t in data["times_ms"]]
-    n_tr = args.train
-    F, T = dataset(shapes[:n_tr], times[:n_tr])
-    packed, losses = fit(F, T, steps=args.steps)
+    report, packed = train_and_evaluate(args.timings, args.extra, n_train=args.train, steps=args.steps)
     with open(args.weights, "w") as f:
-        json.dump({"packed": packed.tolist(), "train_shapes": n_tr, "steps": args.steps,
-                   "final_loss": float(losses[-1])}, f)
-    install(packed)
-    Ft, Tt = dataset(shapes[n_tr:], times[n_tr:])
-    print(json.dumps(evaluate(Ft, Tt, shape_rows(shapes[n_tr:]))))
+        json.dump({"packed": packed.tolist(), "steps": args.steps, "report": report}, f)
+    print(json.dumps(report))
     return 0
 
 

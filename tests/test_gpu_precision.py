@@ -75,3 +75,27 @@ def test_mixed_precision_sthosvd_relerr(atk, prec, dims, ranks):
     rel_o = oracle.relerr(x64, ref["core"], ranks, ref["factors"], dims)
     bound = 3e-3 if prec == FP8 else 1e-4
     assert abs(rel_g - rel_o) <= bound, (rel_g, rel_o)
+
+
+@pytest.mark.parametrize("prec", [TF32, BF16, BF16X3])
+@pytest.mark.parametrize("dims,rmax", [([96, 96, 96], 16), ([16, 16, 16, 16, 16], 4)])
+def test_mixed_precision_decaying_spectrum(atk, prec, dims, rmax):
+    """The precision sweep's spectrum (core singular values decaying like k^-1.5)
+    at sizes the oracle finishes in seconds: each form's relative error stays
+    within the form's bound of the float64 oracle's.  Without a gap at the cut
+    the Gram's rounding moves the captured energy at first order, and the
+    change in relerr is that energy change divided by 2 relerr (here relerr
+    is about 0.011).  TF32 and 3xBF16 stay within 1e-4; BF16 (unit roundoff
+    2^-9) measured 1.1e-4 on 96^3 R 16 and is held to 3e-4.  FP8-e4m3 resolves
+    eigenvalues only down to about 1e-3 lambda_1, above this cut (2.4e-4
+    lambda_1 at R = 16): it is not a usable form on such spectra (measured
+    relerr 0.026 against 0.011) and is not held to a bound here."""
+    x, _, _ = synth.decaying_tucker(dims, rmax, noise=1e-3, seed=4)
+    ranks = [rmax] * len(dims)
+    core, facs, _ = atk.sthosvd(torch.from_numpy(x).cuda(), dims, ranks, solver=[0] * len(dims), precision=prec)
+    x64 = x.astype(np.float64)
+    ref = oracle.sthosvd(x64, dims, ranks, solver=[0] * len(dims))
+    rel_g = oracle.relerr(x64, core.cpu().double().numpy(), ranks, [f.cpu().double().numpy() for f in facs], dims)
+    rel_o = oracle.relerr(x64, ref["core"], ranks, ref["factors"], dims)
+    bound = 3e-4 if prec == BF16 else 1e-4
+    assert abs(rel_g - rel_o) <= bound, (rel_g, rel_o)

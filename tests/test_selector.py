@@ -141,3 +141,20 @@ def test_gpu_adam_steps_follow_oracle():
     # and training goes down
     more = net.train(X, Y, M, steps=300, lr=3e-3)
     assert more[-1] < 0.5 * losses[0]
+
+
+@pytest.mark.gpu
+def test_trained_selector_beats_the_method_without_it():
+    """Trained on the committed timing sets with the library's kernels, the
+    selector's choices on the 64 held-out shapes cost less time (as measured by
+    this build, per mode) than the fixed policies: every mode EIG (the method
+    without a selector), every mode ALS, every mode full Jacobi."""
+    _gpu()
+    from paper_2010_10131_b300 import selector
+    report, packed = selector.train_and_evaluate()
+    ext = report["train_192_plus_extra"]
+    assert ext["gain_vs_fixed_EIG"] > 1.0, ext
+    assert ext["gain_vs_fixed_ALS"] > 2.0, ext
+    assert ext["gain_vs_fixed_EIG-Jacobi"] > 2.0, ext
+    assert ext["regret"] < report["best_possible_gain_vs_fixed_EIG"] - 1.0, ext
+    atk.lib().atucker_selector_clear()
