@@ -428,9 +428,10 @@ __global__ void colnorm_f32_kernel(float* __restrict__ Y, int64_t n, int64_t m) 
 // One CTA: Cholesky L L^T = G + shift * max(diag G) * I (G m x m SPD, float64
 // in, float32 work in shared memory), L written column-major (lower).  A pivot
 // at or below a tiny floor (rank-deficient block) is raised to the floor, so
-// the factor stays finite.  Two barriers per column.
+// the factor stays finite, and *breakdown (nullable) is set.  Two barriers
+// per column.
 __global__ void __launch_bounds__(512) chol_f32_kernel(const double* __restrict__ G, int m, float shift,
-                                                       float* __restrict__ Lout) {
+                                                       float* __restrict__ Lout, int* __restrict__ breakdown) {
   extern __shared__ float L[];  // m x m, column-major; lower triangle used
   __shared__ float dmax, dinv;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) L[idx] = (float)G[idx];
@@ -447,6 +448,10 @@ __global__ void __launch_bounds__(512) chol_f32_kernel(const double* __restrict_
     // pivot j is final here; publish l_jj and its inverse
     if (threadIdx.x == 0) {
       float d = L[j + m * j];
+      // A pivot at the floor (or not finite) means the block is numerically
+      // rank deficient in float32: the factor is kept finite, and the caller
+      // is told so it can take the full solver instead.
+      if (!(d > floor_v) && breakdown) atomicOr(breakdown, 1);
       float ljj = sqrtf(d > floor_v ? d : floor_v);
       L[j + m * j] = ljj;
       dinv = 1.f / ljj;
@@ -520,16 +525,20 @@ __global__ void ritz_residual_kernel(const float* __restrict__ Z, const float* _
   if (lane == 0) res[j] = sqrt(s);
 }
 
-// out[0] = max_j res[j], out[1] = theta[0], out[2] = theta[R-1], out[3] = theta[m-1].
+// out[0] = max_j res[j] (NaN if any residual is NaN), out[1] = theta[0],
+// out[2] = theta[R-1], out[3] = theta[m-1], out[4] = 1 if a CholeskyQR pass
+// broke down since the last summary (the flag is cleared).
 __global__ void ritz_summary_kernel(const double* __restrict__ res, const double* __restrict__ theta, int R, int m,
-                                    double* __restrict__ out) {
+                                    int* __restrict__ breakdown, double* __restrict__ out) {
   if (threadIdx.x != 0) return;
   double w = 0.0;
-  for (int j = 0; j < R; ++j) w = fmax(w, res[j]);
+  for (int j = 0; j < R; ++j) w = (res[j] > w || res[j] != res[j]) ? res[j] : w;
   out[0] = w;
   out[1] = theta[0];
   out[2] = theta[R - 1];
   out[3] = theta[m - 1];
+  out[4] = *breakdown ? 1.0 : 0.0;
+  *breakdown = 0;
 }
 
 __global__ void f32_to_f64_kernel2(const float* __restrict__ s, double* __restrict__ d, int64_t count) {
@@ -541,6 +550,7 @@ namespace {
 struct RRBufs {
   float *Sf, *Q, *Y, *Z, *T, *LinvT, *Vb, *diag, *Wf;  // LinvT holds the Cholesky factor L
   double *G, *W64, *theta, *res, *summary, *Cd;  // Cd: n x m float64 product S Q
+  int* breakdown;  // set by chol_f32_kernel when a pivot hits its floor
   float* part;  // split-K partials of the m x m products
   size_t part_bytes;
 };
@@ -552,7 +562,7 @@ size_t rr_part_bytes(int64_t n, int m) {
 size_t rr_bytes(int64_t n, int m) {
   size_t nm = (size_t)n * m, mm = (size_t)m * m;
   return sizeof(float) * ((size_t)n * n + 4 * nm + 3 * mm + m) + sizeof(double) * (2 * mm + 2 * m + 8 + nm) +
-         rr_part_bytes(n, m) + 17 * 256;
+         rr_part_bytes(n, m) + 18 * 256 + 16;
 }
 // out = S Q (n x m, float32) for the symmetric float32 S.  With the view
 // (lo = n, n, hi = 1) the contracted index c is S's row index and the right
@@ -573,7 +583,7 @@ int cholqr_pass_f32(float* Y, float* Q, int64_t n, int m, float shift, RRBufs& b
   ATK_TRY(gram_f32(Y, v, b.G, b.part, b.part_bytes, st));
   const size_t sm = (size_t)m * m * sizeof(float);
   ATK_CUDA(cudaFuncSetAttribute(chol_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  chol_f32_kernel<<<1, 512, sm, st>>>(b.G, m, shift, b.LinvT);
+  chol_f32_kernel<<<1, 512, sm, st>>>(b.G, m, shift, b.LinvT, b.breakdown);
   ATK_LAUNCHED();
   const size_t sm2 = sm + (size_t)TRSM_THREADS * m * sizeof(float);
   ATK_CUDA(cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
@@ -618,10 +628,12 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   b.res = (double*)ar.take(sizeof(double) * m);
   b.summary = (double*)ar.take(sizeof(double) * 8);
   b.Cd = (double*)ar.take(sizeof(double) * nm);
+  b.breakdown = (int*)ar.take(sizeof(int) * 4);
   b.part_bytes = rr_part_bytes(n, m);
   b.part = (float*)ar.take(b.part_bytes);
   if (!b.part) { set_error("rr: scratch too small"); return ATK_EINVAL; }
-  const View sv{n, n, 1}, qv{n, m, 1};
+  const View qv{n, m, 1};
+  ATK_CUDA(cudaMemsetAsync(b.breakdown, 0, sizeof(int), st));
   ATK_TRY(f64_to_f32(S, b.Sf, n * n, st));
   rand_fill_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, st>>>(b.Q, (int64_t)nm, 0x5EEDULL + (uint64_t)n);
   ATK_LAUNCHED();
@@ -646,13 +658,14 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
     ATK_TRY(ttm_f32(b.Z, qv, b.Wf, m, b.T, st));
     ritz_residual_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(b.T, b.Y, b.theta, n, R, b.res);
     ATK_LAUNCHED();
-    ritz_summary_kernel<<<1, 32, 0, st>>>(b.res, b.theta, (int)R, m, b.summary);
+    ritz_summary_kernel<<<1, 32, 0, st>>>(b.res, b.theta, (int)R, m, b.breakdown, b.summary);
     ATK_LAUNCHED();
-    double h[4] = {0.0, 0.0, 0.0, 0.0};
+    double h[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     ATK_CUDA(cudaMemcpyAsync(h, b.summary, sizeof(h), cudaMemcpyDeviceToHost, st));
     ATK_CUDA(cudaStreamSynchronize(st));
     const double res = h[0], thR = h[2], thm = fmax(h[3], 0.0);
-    if (!(res == res) || !(thR == thR) || res > 1e300) return ATK_ENOCONV;  // non-finite: full Jacobi
+    if (h[4] != 0.0) return ATK_ENOCONV;  // rank-deficient basis in float32: full Jacobi
+    if (!(res == res) || !(thR == thR) || !(h[1] == h[1]) || res > 1e300) return ATK_ENOCONV;  // non-finite
     if (!(thR > 0.0) || thm > RR_SLOW_RATIO * thR) return ATK_ENOCONV;     // clustered: full Jacobi
     const double predicted = (thm / thR) * res / (thR - thm);
     if (predicted <= RR_TARGET) {
