@@ -767,7 +767,7 @@ __global__ void identity_kernel(double* __restrict__ W, int64_t k) {
   if (o < k * k) W[o] = (o % k == o / k) ? 1.0 : 0.0;
 }
 
-constexpr int REFINE_ROTATION_STEPS = 3;
+constexpr int REFINE_ROTATION_STEPS = 2;
 
 size_t refine_bytes(int64_t n, int64_t k) {
   return sizeof(double) * (size_t)(2 * n * k + 5 * k * k + k + 8) + sizeof(int) * (size_t)k +
@@ -784,7 +784,7 @@ size_t refine_bytes(int64_t n, int64_t k) {
 //     about 1e-6 of each direction outside the subspace, which adds up over
 //     R = 128 columns to a projector error above 1e-4.
 //  2. Rayleigh-Ritz in float64: B = Qb^T S Qb.  The Ritz block is nearly
-//     diagonal; REFINE_ROTATION_STEPS simultaneous Jacobi steps (W from
+//     diagonal; REFINE_ROTATION_STEPS (2) simultaneous Jacobi steps (W from
 //     simrot_kernel, orthonormalised by two polar steps, B <- W^T B W) take
 //     the off-diagonal entries to float64 level.
 //  3. U = (Qb W)[:, top R of diag(B)], one more polar step and the sign rule.
