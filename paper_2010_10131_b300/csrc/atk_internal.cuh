@@ -47,6 +47,7 @@ int cuda_status(cudaError_t e, const char* what);
 // counts it (the count is reported by atucker_plan_timings).
 void count_launch();
 long long launch_count();
+void count_launches(long long k);
 #define ATK_LAUNCHED()                                                   \
   do {                                                                   \
     cudaError_t _e = cudaGetLastError();                                 \

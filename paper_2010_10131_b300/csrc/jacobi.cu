@@ -14,6 +14,8 @@
 //    is a persistent cooperative kernel with a bounded grid barrier between
 //    phases.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "jacobi_dev.cuh"
 
@@ -908,6 +910,74 @@ __global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R) {
     for (int64_t i = lane; i < n; i += 32) u[i] = -u[i];
 }
 
+// ------------------------------------------------------------ graph cache
+// A launch sequence with no host synchronisation inside (the refinement tail
+// of the eigensolver: about 60 small kernels) is captured once into a CUDA
+// graph per key (every pointer and size it uses) and replayed afterwards, so
+// the host enqueues one graph instead of every kernel.  A key fixes every
+// kernel argument, so a replay does exactly what the direct launches would.
+namespace {
+struct GraphKey {
+  const void* p[8];
+  int64_t v[4];
+  bool operator==(const GraphKey& o) const {
+    for (int i = 0; i < 8; ++i)
+      if (p[i] != o.p[i]) return false;
+    for (int i = 0; i < 4; ++i)
+      if (v[i] != o.v[i]) return false;
+    return true;
+  }
+};
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  long long kernels;  // launches recorded at capture, counted again per replay
+};
+constexpr size_t GRAPH_CACHE_MAX = 64;
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+
+template <class F>
+int run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
+  {
+    std::lock_guard<std::mutex> g(g_graph_mu);
+    for (const GraphEntry& e : g_graphs)
+      if (e.key == key) {
+        ATK_CUDA(cudaGraphLaunch(e.exec, st));
+        count_launches(e.kernels);
+        return ATK_OK;
+      }
+  }
+  thread_local cudaStream_t cap = nullptr;
+  if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cap = nullptr;
+    return body(st);
+  }
+  const long long before = launch_count();
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return body(st);
+  const int s = body(cap);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (s != ATK_OK || e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (s != ATK_OK) return s;
+    return body(st);  // capture refused: run the launches directly
+  }
+  cudaGraphDestroy(graph);
+  const long long kernels = launch_count() - before;
+  ATK_CUDA(cudaGraphLaunch(exec, st));
+  std::lock_guard<std::mutex> g(g_graph_mu);
+  if (g_graphs.size() >= GRAPH_CACHE_MAX) {
+    cudaGraphExecDestroy(g_graphs.front().exec);
+    g_graphs.erase(g_graphs.begin());
+  }
+  g_graphs.push_back({key, exec, kernels});
+  return ATK_OK;
+}
+}  // namespace
+
 // Eigen-decomposition + selection + float64 polar orthonormalisation.
 // U64_out (n x R float64) is the orthonormalised basis; U_out its float32 copy.
 int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, float* U_out,
@@ -944,9 +1014,15 @@ int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int ma
     if (s != ATK_OK) return s;
     k = R;
   }
-  ATK_TRY(refine_f64(S, n, Qb, k, R, U64_out, lambda_out, discarded_out, rest, rest_bytes, st, true));
-  if (U_out) ATK_TRY(f64_to_f32(U64_out, U_out, n * R, st));
-  return ATK_OK;
+  // The refinement and the float32 copy of U: no host synchronisation inside,
+  // so one cached graph per (buffers, sizes).
+  const GraphKey key{{S, Qb, U64_out, lambda_out, discarded_out, U_out, rest, nullptr},
+                     {n, k, R, (int64_t)rest_bytes}};
+  return run_graph(key, st, [&](cudaStream_t s2) -> int {
+    ATK_TRY(refine_f64(S, n, Qb, k, R, U64_out, lambda_out, discarded_out, rest, rest_bytes, s2, true));
+    if (U_out) ATK_TRY(f64_to_f32(U64_out, U_out, n * R, s2));
+    return ATK_OK;
+  });
 }
 
 }  // namespace atk

@@ -22,6 +22,7 @@ int cuda_status(cudaError_t e, const char* what) {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 int num_sms() {
   static int sms = 0;
