@@ -21,6 +21,25 @@
 
 namespace atk {
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never
+// lower it: launches captured in cached graphs keep their sizes, so a later
+// call with a smaller block must not shrink the limit under them.
+static int raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, size_t>> seen;
+  std::lock_guard<std::mutex> g(mu);
+  for (auto& e : seen)
+    if (e.first == fn) {
+      if (e.second >= bytes) return ATK_OK;
+      ATK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      e.second = bytes;
+      return ATK_OK;
+    }
+  ATK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  seen.push_back({fn, bytes});
+  return ATK_OK;
+}
+
 // ---------------------------------------------------------- one-CTA driver
 // One matrix per CTA (blockIdx.x), padded to m = n rounded up to even.
 // Writes diag (n) and V (n x n, row-major, column j = eigenvector j) to global.
@@ -323,7 +342,7 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
     T* V = (T*)ar.take(sizeof(T) * n * n);
     if (!diag || !V) { set_error("eig: scratch too small"); return ATK_EINVAL; }
     size_t sm = small_smem<T>(m);
-    ATK_CUDA(cudaFuncSetAttribute(jacobi_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ATK_TRY(raise_smem_limit((const void*)jacobi_small_kernel<T>, sm));
     jacobi_small_kernel<T><<<1, 256, sm, st>>>(S, (int)n, m, max_sweeps, diag, V, dev_status);
     ATK_LAUNCHED();
     select_kernel<T><<<1, 1024, 0, st>>>(diag, 1, V, (int)n, (int)n, (int)R, U64, lam_out, nullptr);
@@ -359,7 +378,7 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
   args.sweep_flags = words + 2;
   args.status = dev_status;
   size_t sm = block_smem<T>();
-  ATK_CUDA(cudaFuncSetAttribute(jacobi_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  ATK_TRY(raise_smem_limit((const void*)jacobi_block_kernel<T>, sm));
   int per_sm = 0;
   ATK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel<T>, 256, sm));
   if (per_sm < 1) { set_error("eig: block Jacobi kernel does not fit on an SM"); return ATK_EUNSUPPORTED; }
@@ -371,6 +390,74 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
   count_launch();
   select_kernel<T><<<1, 1024, 0, st>>>(A, (int64_t)m + 1, V, m, (int)n, (int)R, U64, lam_out, nullptr);
   ATK_LAUNCHED();
+  return ATK_OK;
+}
+}  // namespace
+
+// ------------------------------------------------------------ graph cache
+// A launch sequence with no host synchronisation inside (the refinement tail
+// of the eigensolver: about 60 small kernels) is captured once into a CUDA
+// graph per key (every pointer and size it uses) and replayed afterwards, so
+// the host enqueues one graph instead of every kernel.  A key fixes every
+// kernel argument, so a replay does exactly what the direct launches would.
+namespace {
+struct GraphKey {
+  const void* p[8];
+  int64_t v[4];
+  bool operator==(const GraphKey& o) const {
+    for (int i = 0; i < 8; ++i)
+      if (p[i] != o.p[i]) return false;
+    for (int i = 0; i < 4; ++i)
+      if (v[i] != o.v[i]) return false;
+    return true;
+  }
+};
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  long long kernels;  // launches recorded at capture, counted again per replay
+};
+constexpr size_t GRAPH_CACHE_MAX = 64;
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+
+template <class F>
+int run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
+  {
+    std::lock_guard<std::mutex> g(g_graph_mu);
+    for (const GraphEntry& e : g_graphs)
+      if (e.key == key) {
+        ATK_CUDA(cudaGraphLaunch(e.exec, st));
+        count_launches(e.kernels);
+        return ATK_OK;
+      }
+  }
+  thread_local cudaStream_t cap = nullptr;
+  if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cap = nullptr;
+    return body(st);
+  }
+  const long long before = launch_count();
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return body(st);
+  const int s = body(cap);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (s != ATK_OK || e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (s != ATK_OK) return s;
+    return body(st);  // capture refused: run the launches directly
+  }
+  cudaGraphDestroy(graph);
+  const long long kernels = launch_count() - before;
+  ATK_CUDA(cudaGraphLaunch(exec, st));
+  std::lock_guard<std::mutex> g(g_graph_mu);
+  if (g_graphs.size() >= GRAPH_CACHE_MAX) {
+    cudaGraphExecDestroy(g_graphs.front().exec);
+    g_graphs.erase(g_graphs.begin());
+  }
+  g_graphs.push_back({key, exec, kernels});
   return ATK_OK;
 }
 }  // namespace
@@ -584,11 +671,9 @@ int cholqr_pass_f32(float* Y, float* Q, int64_t n, int m, float shift, RRBufs& b
   ATK_LAUNCHED();
   ATK_TRY(gram_f32(Y, v, b.G, b.part, b.part_bytes, st));
   const size_t sm = (size_t)m * m * sizeof(float);
-  ATK_CUDA(cudaFuncSetAttribute(chol_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   chol_f32_kernel<<<1, 512, sm, st>>>(b.G, m, shift, b.LinvT, b.breakdown);
   ATK_LAUNCHED();
   const size_t sm2 = sm + (size_t)TRSM_THREADS * m * sizeof(float);
-  ATK_CUDA(cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
   trsm_rows_kernel<<<(unsigned)ceil_div(n, TRSM_THREADS), TRSM_THREADS, sm2, st>>>(Y, b.LinvT, n, m, Q);
   ATK_LAUNCHED();
   return ATK_OK;
@@ -635,33 +720,54 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   b.part = (float*)ar.take(b.part_bytes);
   if (!b.part) { set_error("rr: scratch too small"); return ATK_EINVAL; }
   const View qv{n, m, 1};
-  ATK_CUDA(cudaMemsetAsync(b.breakdown, 0, sizeof(int), st));
-  ATK_TRY(f64_to_f32(S, b.Sf, n * n, st));
-  rand_fill_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, st>>>(b.Q, (int64_t)nm, 0x5EEDULL + (uint64_t)n);
-  ATK_LAUNCHED();
-  // One power step from the random block; the loop below continues from the
-  // Ritz vectors when more are needed.
-  ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Y, b, st));  // Y = S Q
-  ATK_TRY(cholqr3_f32(b.Y, b.T, b.Q, n, m, b, st));
   const int mp = m + (m & 1);
   const size_t jsm = small_smem<float>(mp);
-  ATK_CUDA(cudaFuncSetAttribute(jacobi_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
+  // Shared-memory limits of the one-CTA kernels, set outside the captured
+  // launch sequences (for the widest block, once).
+  {
+    const size_t mmax = 156;
+    ATK_TRY(raise_smem_limit((const void*)chol_f32_kernel, mmax * mmax * 4));
+    ATK_TRY(raise_smem_limit((const void*)trsm_rows_kernel, (mmax * mmax + TRSM_THREADS * mmax) * 4));
+    ATK_TRY(raise_smem_limit((const void*)jacobi_small_kernel<float>, small_smem<float>((int)mmax)));
+  }
+  // The three launch sequences between host reads, each a cached graph:
+  // setup (the float32 copy of S, a random block, one power step, shifted
+  // CholeskyQR3), one Rayleigh-Ritz step up to its summary, and the two
+  // CholeskyQR passes that start the next step.
+  const GraphKey kpre{{S, scratch, nullptr, nullptr, nullptr, nullptr, nullptr, (const void*)1},
+                      {n, R, m, (int64_t)scratch_bytes}};
+  ATK_TRY(run_graph(kpre, st, [&](cudaStream_t s2) -> int {
+    ATK_CUDA(cudaMemsetAsync(b.breakdown, 0, sizeof(int), s2));
+    ATK_TRY(f64_to_f32(S, b.Sf, n * n, s2));
+    rand_fill_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, s2>>>(b.Q, (int64_t)nm,
+                                                                          0x5EEDULL + (uint64_t)n);
+    ATK_LAUNCHED();
+    ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Y, b, s2));  // Y = S Q
+    return cholqr3_f32(b.Y, b.T, b.Q, n, m, b, s2);
+  }));
+  const GraphKey kit{{scratch, dev_status, nullptr, nullptr, nullptr, nullptr, nullptr, (const void*)2},
+                     {n, R, m, (int64_t)max_sweeps}};
+  const GraphKey knext{{scratch, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (const void*)3},
+                       {n, R, m, (int64_t)scratch_bytes}};
   for (int it = 0; it < RR_MAXIT; ++it) {
-    // Rayleigh-Ritz: Z = S Q, B = Q^T Z = W diag(theta) W^T.
-    ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Z, b, st));
-    ATK_TRY(cross_f32(b.Q, qv, b.Z, m, b.G, b.part, b.part_bytes, st));
-    jacobi_small_kernel<float><<<1, 512, jsm, st>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
-    ATK_LAUNCHED();
-    select_kernel<float><<<1, 1024, 0, st>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
-    ATK_LAUNCHED();
-    ATK_TRY(f64_to_f32(b.W64, b.Wf, (int64_t)mm, st));
-    // Ritz vectors Y = Q W (descending theta) and S Q W = Z W.
-    ATK_TRY(ttm_f32(b.Q, qv, b.Wf, m, b.Y, st));
-    ATK_TRY(ttm_f32(b.Z, qv, b.Wf, m, b.T, st));
-    ritz_residual_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(b.T, b.Y, b.theta, n, R, b.res);
-    ATK_LAUNCHED();
-    ritz_summary_kernel<<<1, 32, 0, st>>>(b.res, b.theta, (int)R, m, b.breakdown, b.summary);
-    ATK_LAUNCHED();
+    // Rayleigh-Ritz: Z = S Q, B = Q^T Z = W diag(theta) W^T; Ritz vectors
+    // Y = Q W (descending theta) and S Q W = Z W; residuals and summary.
+    ATK_TRY(run_graph(kit, st, [&](cudaStream_t s2) -> int {
+      ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Z, b, s2));
+      ATK_TRY(cross_f32(b.Q, qv, b.Z, m, b.G, b.part, b.part_bytes, s2));
+      jacobi_small_kernel<float><<<1, 512, jsm, s2>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
+      ATK_LAUNCHED();
+      select_kernel<float><<<1, 1024, 0, s2>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
+      ATK_LAUNCHED();
+      ATK_TRY(f64_to_f32(b.W64, b.Wf, (int64_t)mm, s2));
+      ATK_TRY(ttm_f32(b.Q, qv, b.Wf, m, b.Y, s2));
+      ATK_TRY(ttm_f32(b.Z, qv, b.Wf, m, b.T, s2));
+      ritz_residual_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, s2>>>(b.T, b.Y, b.theta, n, R, b.res);
+      ATK_LAUNCHED();
+      ritz_summary_kernel<<<1, 32, 0, s2>>>(b.res, b.theta, (int)R, m, b.breakdown, b.summary);
+      ATK_LAUNCHED();
+      return ATK_OK;
+    }));
     double h[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     ATK_CUDA(cudaMemcpyAsync(h, b.summary, sizeof(h), cudaMemcpyDeviceToHost, st));
     ATK_CUDA(cudaStreamSynchronize(st));
@@ -677,8 +783,10 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
     }
     // Next step from the Ritz vectors: S (Q W) = Z W is in T; its columns are
     // nearly orthogonal, so two plain CholeskyQR passes orthonormalise it.
-    ATK_TRY(cholqr_pass_f32(b.T, b.Y, n, m, 0.f, b, st));
-    ATK_TRY(cholqr_pass_f32(b.Y, b.Q, n, m, 0.f, b, st));
+    ATK_TRY(run_graph(knext, st, [&](cudaStream_t s2) -> int {
+      ATK_TRY(cholqr_pass_f32(b.T, b.Y, n, m, 0.f, b, s2));
+      return cholqr_pass_f32(b.Y, b.Q, n, m, 0.f, b, s2);
+    }));
   }
   return ATK_ENOCONV;
 }
@@ -909,74 +1017,6 @@ __global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R) {
   if (u[arg] < 0.0)
     for (int64_t i = lane; i < n; i += 32) u[i] = -u[i];
 }
-
-// ------------------------------------------------------------ graph cache
-// A launch sequence with no host synchronisation inside (the refinement tail
-// of the eigensolver: about 60 small kernels) is captured once into a CUDA
-// graph per key (every pointer and size it uses) and replayed afterwards, so
-// the host enqueues one graph instead of every kernel.  A key fixes every
-// kernel argument, so a replay does exactly what the direct launches would.
-namespace {
-struct GraphKey {
-  const void* p[8];
-  int64_t v[4];
-  bool operator==(const GraphKey& o) const {
-    for (int i = 0; i < 8; ++i)
-      if (p[i] != o.p[i]) return false;
-    for (int i = 0; i < 4; ++i)
-      if (v[i] != o.v[i]) return false;
-    return true;
-  }
-};
-struct GraphEntry {
-  GraphKey key;
-  cudaGraphExec_t exec;
-  long long kernels;  // launches recorded at capture, counted again per replay
-};
-constexpr size_t GRAPH_CACHE_MAX = 64;
-std::mutex g_graph_mu;
-std::vector<GraphEntry> g_graphs;
-
-template <class F>
-int run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
-  {
-    std::lock_guard<std::mutex> g(g_graph_mu);
-    for (const GraphEntry& e : g_graphs)
-      if (e.key == key) {
-        ATK_CUDA(cudaGraphLaunch(e.exec, st));
-        count_launches(e.kernels);
-        return ATK_OK;
-      }
-  }
-  thread_local cudaStream_t cap = nullptr;
-  if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
-    cap = nullptr;
-    return body(st);
-  }
-  const long long before = launch_count();
-  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return body(st);
-  const int s = body(cap);
-  cudaGraph_t graph = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(cap, &graph);
-  cudaGraphExec_t exec = nullptr;
-  if (s != ATK_OK || e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    cudaGetLastError();
-    if (s != ATK_OK) return s;
-    return body(st);  // capture refused: run the launches directly
-  }
-  cudaGraphDestroy(graph);
-  const long long kernels = launch_count() - before;
-  ATK_CUDA(cudaGraphLaunch(exec, st));
-  std::lock_guard<std::mutex> g(g_graph_mu);
-  if (g_graphs.size() >= GRAPH_CACHE_MAX) {
-    cudaGraphExecDestroy(g_graphs.front().exec);
-    g_graphs.erase(g_graphs.begin());
-  }
-  g_graphs.push_back({key, exec, kernels});
-  return ATK_OK;
-}
-}  // namespace
 
 // Eigen-decomposition + selection + float64 polar orthonormalisation.
 // U64_out (n x R float64) is the orthonormalised basis; U_out its float32 copy.
