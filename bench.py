@@ -377,6 +377,21 @@ def run_case(args):
     if kind == "precision":
         print(json.dumps({"case": "precision", "sweep": run_precision(args)}), flush=True)
         return 0
+    if kind == "batchrun":
+        # The batched kernel alone (fixed launch variant, no tuning and no
+        # one-at-a-time leg): the command profiles of the kernel use.
+        import paper_2010_10131_b300 as atk
+        vals = [int(v) for v in shape.split(",")] if shape else [512]
+        shapes, xs_np = batched_inputs(vals[0])
+        xs = [torch.from_numpy(x).cuda() for x in xs_np]
+        b = atk.Batch([d for d, _ in shapes], [r for _, r in shapes])
+        b.set_option(atk.BATCH_OPT_VARIANT, vals[1] if len(vals) > 1 else 0)
+        cores, facs = b.outputs()
+        for _ in range(max(args.warmup, 0) + max(args.steps, 1)):
+            b.run(xs, cores, facs)
+        b.close()
+        print(json.dumps({"case": args.case, "tensors": vals[0]}), flush=True)
+        return 0
     if kind == "batched":
         out = run_batched(args, count=int(shape) if shape else 4096)
         print(json.dumps({"case": args.case, **out}), flush=True)

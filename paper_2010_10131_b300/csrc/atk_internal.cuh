@@ -179,12 +179,11 @@ int polar_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_
 // CholeskyQR2 in float64: L (n x R) = Q R^, Q overwrites L, R^ (R x R) upper, diag > 0.
 int cholqr2_f64(double* L, int64_t n, int64_t R, double* Rhat, double* scratch, int* dev_status,
                 cudaStream_t st);
-// C (m x p) = A (m x k) B (k x p), column-major float64.
-int gemm_f64(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, cudaStream_t st);
-// Rayleigh quotients lam[r] = u_r^T S u_r of orthonormal U (n x R) and
-// disc = trace(S) - sum_r lam[r]; Z is n x R scratch.  Outputs nullable.
-int rayleigh_f64(const double* S, const double* U, int64_t n, int64_t R, double* Z, double* lam_out,
-                 double* disc_out, cudaStream_t st);
+// C (m x p) = A (m x k) B (k x p), column-major float64, split over k into
+// at most part_cap / (m p) partial products (part: float64 scratch that
+// overlaps none of A, B, C) so that small outputs still cover the chip.
+int gemm_f64_split(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, double* part,
+                   int64_t part_cap, cudaStream_t st);
 int f64_to_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 int f32_to_f64(const float* src, double* dst, int64_t count, cudaStream_t st);
 // Square of the Frobenius norm of a float32 tensor, accumulated in float64.

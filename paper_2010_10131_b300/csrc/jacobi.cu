@@ -515,87 +515,103 @@ __global__ void colnorm_f32_kernel(float* __restrict__ Y, int64_t n, int64_t m) 
 }
 
 // One CTA: Cholesky L L^T = G + shift * max(diag G) * I (G m x m SPD, float64
-// in, float32 work in shared memory), L written column-major (lower).  A pivot
-// at or below a tiny floor (rank-deficient block) is raised to the floor, so
-// the factor stays finite, and *breakdown (nullable) is set.  Two barriers
-// per column.
-__global__ void __launch_bounds__(512) chol_f32_kernel(const double* __restrict__ G, int m, float shift,
-                                                       float* __restrict__ Lout, int* __restrict__ breakdown) {
-  extern __shared__ float L[];  // m x m, column-major; lower triangle used
-  __shared__ float dmax, dinv;
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) L[idx] = (float)G[idx];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float d = 0.f;
-    for (int j = 0; j < m; ++j) d = fmaxf(d, L[j + m * j]);
-    for (int j = 0; j < m; ++j) L[j + m * j] += shift * d;
-    dmax = d;
+// in, float32 work in shared memory) and the triangular inverse X = L^{-1},
+// written as Mout = X^T (m x m column-major, upper triangular) so that the
+// CholeskyQR update Y L^{-T} is the plain product Y Mout.  A pivot at or below
+// a tiny floor (rank-deficient block) is raised to the floor, so the factor
+// stays finite, and *breakdown (nullable) is set.
+// Both run right-looking in the same m steps, one barrier each.  Step j
+// reads the unscaled column j of L (final after step j-1) and row j of the
+// forward-substitution workspace W (W = I at the start, X[j, :] = W[j, :] /
+// l_jj), and every row i > j is updated by its four owner threads:
+// L[i, k] -= l_ij l_kj for j < k <= i and W[i, c] -= l_ij X[j, c] for c <= j.
+// L itself is never scaled (only its unscaled columns are read, times
+// 1/l_jj); row j of W becomes X[j, :] in step j+1, when nothing reads it any
+// more.  Each thread loads a batch of its operands before it stores any
+// result, so the shared-memory loads overlap instead of waiting on the
+// previous store.
+constexpr int CHOL_THREADS = 512;
+__global__ void __launch_bounds__(CHOL_THREADS) cholinv_f32_kernel(const double* __restrict__ G, int m, float shift,
+                                                                    float* __restrict__ Mout,
+                                                                    int* __restrict__ breakdown) {
+  extern __shared__ float sm[];
+  const int ld = m + 1;
+  float* L = sm;           // column-major, L[i + ld k]
+  float* W = sm + m * ld;  // row-major, W[t * ld + c]
+  __shared__ float dmax_s;
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  for (int idx = tid; idx < m * m; idx += CHOL_THREADS) {
+    const int r = idx % m, c = idx / m;
+    L[r + ld * c] = (float)G[idx];
+    W[c * ld + r] = (r == c) ? 1.f : 0.f;
   }
+  __syncthreads();
+  if (warp == 0) {
+    float d = 0.f;
+    for (int j = lane; j < m; j += 32) d = fmaxf(d, L[j + ld * j]);
+    for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if (lane == 0) dmax_s = d;
+  }
+  __syncthreads();
+  const float dmax = dmax_s;
+  for (int j = tid; j < m; j += CHOL_THREADS) L[j + ld * j] += shift * dmax;
   __syncthreads();
   const float floor_v = 1e-12f * dmax + 1e-30f;
+  float inv_prev = 0.f;
+  const int sub = tid % 4;
+  constexpr int CB = 8;  // operands loaded per batch
   for (int j = 0; j < m; ++j) {
-    // pivot j is final here; publish l_jj and its inverse
-    if (threadIdx.x == 0) {
-      float d = L[j + m * j];
-      // A pivot at the floor (or not finite) means the block is numerically
-      // rank deficient in float32: the factor is kept finite, and the caller
-      // is told so it can take the full solver instead.
-      if (!(d > floor_v) && breakdown) atomicOr(breakdown, 1);
-      float ljj = sqrtf(d > floor_v ? d : floor_v);
-      L[j + m * j] = ljj;
-      dinv = 1.f / ljj;
+    const float d = L[j + ld * j];
+    if (tid == 0 && !(d > floor_v) && breakdown) atomicOr(breakdown, 1);
+    const float inv = 1.f / sqrtf(d > floor_v ? d : floor_v);
+    if (j > 0)
+      for (int c = tid; c < j; c += CHOL_THREADS) W[(j - 1) * ld + c] *= inv_prev;
+    for (int i = j + 1 + tid / 4; i < m; i += CHOL_THREADS / 4) {
+      const float lij = L[i + ld * j] * inv;
+      for (int k0 = j + 1 + sub; k0 <= i; k0 += 4 * CB) {
+        float a[CB], b[CB];
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+          const int k = k0 + 4 * u;
+          if (k <= i) {
+            a[u] = L[k + ld * j];
+            b[u] = L[i + ld * k];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+          const int k = k0 + 4 * u;
+          if (k <= i) L[i + ld * k] = fmaf(-lij, a[u] * inv, b[u]);
+        }
+      }
+      for (int c0 = sub; c0 <= j; c0 += 4 * CB) {
+        float a[CB], b[CB];
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+          const int c = c0 + 4 * u;
+          if (c <= j) {
+            a[u] = W[j * ld + c];
+            b[u] = W[i * ld + c];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+          const int c = c0 + 4 * u;
+          if (c <= j) W[i * ld + c] = fmaf(-lij, a[u] * inv, b[u]);
+        }
+      }
     }
+    inv_prev = inv;
     __syncthreads();
-    const float inv = dinv;
-    const int rem = m - j - 1;
-    // trailing update with the unscaled column, then scale column j
-    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-      int i = j + 1 + idx % rem, k = j + 1 + idx / rem;
-      if (i >= k) L[i + m * k] = fmaf(-(L[i + m * j] * inv), L[k + m * j] * inv, L[i + m * k]);
-    }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i + m * j] *= inv;
   }
+  for (int c = tid; c < m; c += CHOL_THREADS) W[(m - 1) * ld + c] *= inv_prev;
   __syncthreads();
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    int r = idx % m, c = idx / m;
-    Lout[idx] = (r >= c) ? L[idx] : 0.f;
+  for (int idx = tid; idx < m * m; idx += CHOL_THREADS) {
+    const int i = idx % m, r = idx / m;
+    Mout[idx] = r >= i ? W[r * ld + i] : 0.f;
   }
 }
-
-// Q = Y L^{-T}: row i of Q solves L q = y_i (forward substitution).  One
-// thread per row of Y (n x m column-major); L (m x m, lower) and the thread's
-// partial solution live in shared memory.
-constexpr int TRSM_THREADS = 64;
-__global__ void __launch_bounds__(TRSM_THREADS) trsm_rows_kernel(const float* __restrict__ Y,
-                                                                 const float* __restrict__ Lg, int64_t n, int m,
-                                                                 float* __restrict__ Q) {
-  extern __shared__ float sm[];
-  float* L = sm;                   // m x m
-  float* qs = sm + (size_t)m * m;  // TRSM_THREADS x m, element (t, j) at t + TRSM_THREADS * j
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) L[idx] = Lg[idx];
-  __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * TRSM_THREADS + threadIdx.x;
-  if (i >= n) return;
-  float* q = qs + threadIdx.x;
-  // The row's right-hand sides first (independent loads, one latency), then
-  // the substitution overwrites them with the solution in place.
-  for (int j = 0; j < m; ++j) q[TRSM_THREADS * j] = Y[i + n * j];
-  for (int j = 0; j < m; ++j) {
-    float a0 = q[TRSM_THREADS * j], a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    int t = 0;
-    for (; t + 3 < j; t += 4) {
-      a0 = fmaf(-L[j + m * t], q[TRSM_THREADS * t], a0);
-      a1 = fmaf(-L[j + m * (t + 1)], q[TRSM_THREADS * (t + 1)], a1);
-      a2 = fmaf(-L[j + m * (t + 2)], q[TRSM_THREADS * (t + 2)], a2);
-      a3 = fmaf(-L[j + m * (t + 3)], q[TRSM_THREADS * (t + 3)], a3);
-    }
-    for (; t < j; ++t) a0 = fmaf(-L[j + m * t], q[TRSM_THREADS * t], a0);
-    float qj = ((a0 + a1) + (a2 + a3)) / L[j + m * j];
-    q[TRSM_THREADS * j] = qj;
-    Q[i + n * j] = qj;
-  }
-}
+inline size_t cholinv_smem(int m) { return (size_t)2 * m * (m + 1) * sizeof(float); }
 
 // res[j] = ||Z[:, j] - theta_j Q[:, j]|| for j < R; one warp per column.
 __global__ void ritz_residual_kernel(const float* __restrict__ Z, const float* __restrict__ Q,
@@ -637,9 +653,9 @@ __global__ void f32_to_f64_kernel2(const float* __restrict__ s, double* __restri
 
 namespace {
 struct RRBufs {
-  float *Sf, *Q, *Y, *Z, *T, *LinvT, *Vb, *diag, *Wf;  // LinvT holds the Cholesky factor L
+  float *Sf, *Q, *Y, *Z, *T, *LinvT, *Vb, *diag, *Wf;  // LinvT = L^{-T} of the last CholeskyQR pass
   double *G, *W64, *theta, *res, *summary, *Cd;  // Cd: n x m float64 product S Q
-  int* breakdown;  // set by chol_f32_kernel when a pivot hits its floor
+  int* breakdown;  // set by cholinv_f32_kernel when a pivot hits its floor
   float* part;  // split-K partials of the m x m products
   size_t part_bytes;
 };
@@ -670,13 +686,9 @@ int cholqr_pass_f32(float* Y, float* Q, int64_t n, int m, float shift, RRBufs& b
   colnorm_f32_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Y, n, m);
   ATK_LAUNCHED();
   ATK_TRY(gram_f32(Y, v, b.G, b.part, b.part_bytes, st));
-  const size_t sm = (size_t)m * m * sizeof(float);
-  chol_f32_kernel<<<1, 512, sm, st>>>(b.G, m, shift, b.LinvT, b.breakdown);
+  cholinv_f32_kernel<<<1, CHOL_THREADS, cholinv_smem(m), st>>>(b.G, m, shift, b.LinvT, b.breakdown);
   ATK_LAUNCHED();
-  const size_t sm2 = sm + (size_t)TRSM_THREADS * m * sizeof(float);
-  trsm_rows_kernel<<<(unsigned)ceil_div(n, TRSM_THREADS), TRSM_THREADS, sm2, st>>>(Y, b.LinvT, n, m, Q);
-  ATK_LAUNCHED();
-  return ATK_OK;
+  return ttm_f32(Y, v, b.LinvT, m, Q, st);  // Q = Y L^{-T}
 }
 // Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Zhang, Yamamoto, SISC 2020):
 // the shifted first pass cannot break down, and it leaves a basis with modest
@@ -726,8 +738,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   // launch sequences (for the widest block, once).
   {
     const size_t mmax = 156;
-    ATK_TRY(raise_smem_limit((const void*)chol_f32_kernel, mmax * mmax * 4));
-    ATK_TRY(raise_smem_limit((const void*)trsm_rows_kernel, (mmax * mmax + TRSM_THREADS * mmax) * 4));
+    ATK_TRY(raise_smem_limit((const void*)cholinv_f32_kernel, cholinv_smem((int)mmax)));
     ATK_TRY(raise_smem_limit((const void*)jacobi_small_kernel<float>, small_smem<float>((int)mmax)));
   }
   // The three launch sequences between host reads, each a cached graph:
@@ -878,9 +889,12 @@ __global__ void identity_kernel(double* __restrict__ W, int64_t k) {
 }
 
 constexpr int REFINE_ROTATION_STEPS = 2;
+// Split-K partials of the float64 products: one n x k output plus enough for
+// about two 32 x 32 tiles per SM of any smaller output.
+constexpr int64_t REFINE_PART_EXTRA = 512 * 1024;
 
 size_t refine_bytes(int64_t n, int64_t k) {
-  return sizeof(double) * (size_t)(2 * n * k + 5 * k * k + k + 8) + sizeof(int) * (size_t)k +
+  return sizeof(double) * (size_t)(2 * n * k + 5 * k * k + k + 8 + n * k + REFINE_PART_EXTRA) + sizeof(int) * (size_t)k +
          smallla_scratch_bytes(std::max(n, k), k) + 4096;
 }
 
@@ -913,11 +927,13 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   double* norms = (double*)ar.take(sizeof(double) * (k + 8));
   int* order = (int*)ar.take(sizeof(int) * k);
   double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
-  if (!pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
+  const int64_t gcap = n * k + REFINE_PART_EXTRA;
+  double* gpart = (double*)ar.take(sizeof(double) * gcap);
+  if (!pol || !gpart) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
   const unsigned gk = (unsigned)ceil_div(k * k, 256);
   // 1. subspace step (subspace_step = false only orthonormalises Qb)
   if (subspace_step) {
-    ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
+    ATK_TRY(gemm_f64_split(S, Qb, n, n, k, Z, gpart, gcap, st));
     colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, n, k, norms);
     ATK_LAUNCHED();
     normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, 1e-5, Qb);
@@ -926,7 +942,7 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
   ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
   // 2. Rayleigh-Ritz and simultaneous rotations
-  ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
+  ATK_TRY(gemm_f64_split(S, Qb, n, n, k, Z, gpart, gcap, st));
   ATK_TRY(gemm_tn_f64(Qb, Z, n, k, B, pol, st));
   identity_kernel<<<gk, 256, 0, st>>>(Wt, k);
   ATK_LAUNCHED();
@@ -935,15 +951,15 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
     ATK_LAUNCHED();
     ATK_TRY(polar_step_f64(W, k, k, pol, st));
     ATK_TRY(polar_step_f64(W, k, k, pol, st));
-    ATK_TRY(gemm_f64(B, W, k, k, k, T, st));
+    ATK_TRY(gemm_f64_split(B, W, k, k, k, T, gpart, gcap, st));
     ATK_TRY(gemm_tn_f64(W, T, k, k, B, pol, st));
-    ATK_TRY(gemm_f64(Wt, W, k, k, k, T2, st));
+    ATK_TRY(gemm_f64_split(Wt, W, k, k, k, T2, gpart, gcap, st));
     std::swap(Wt, T2);
   }
   // 3. kept vectors
   order_diag_kernel<<<1, 256, 0, st>>>(B, (int)k, (int)R, S, n, order, lambda_out, discarded_out);
   ATK_LAUNCHED();
-  ATK_TRY(gemm_f64(Qb, Wt, n, k, k, QW, st));
+  ATK_TRY(gemm_f64_split(Qb, Wt, n, k, k, QW, gpart, gcap, st));
   gather_cols_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(QW, order, n, R, U64);
   ATK_LAUNCHED();
   ATK_TRY(polar_step_f64(U64, n, R, pol, st));

@@ -4,35 +4,174 @@
 // CholeskyQR2.
 //
 // On B300, float64 runs at about 1/60 of the float32 rate, and one SM manages
-// only about 8 GFLOP/s.  So every O(n R^2) product here is spread over many
-// CTAs.  Only the O(R^3) factorisations run on a single CTA.
+// only about 8 GFLOP/s.  So the products take float64 operands and results
+// but compute in float-float on the float32 pipe, spread over many CTAs;
+// only the O(R^3) factorisations run in float64 on a single CTA.
 #include <algorithm>
 
 #include "atk_internal.cuh"
 
 namespace atk {
 
+// ------------------------------------------------------------ tiled DGEMM
+// C (m x p) = op(A) (m x k) op(B) (k x p), column-major float64 in and out;
+// op(A) = A (lda >= m) or A^T (A stored k x m, lda >= k), likewise op(B).
+//
+// B300 issues about two float64 FMAs per clock per SM against 128 float32
+// lanes, so the products run in float-float arithmetic on the float32 pipe:
+// each operand is split into hi = fl32(x) and lo = fl32(x - hi) as it is
+// staged (48 significant bits), each term a*b is formed as the float32 product
+// of the high parts plus its exact rounding error (an FMA) and the two cross
+// terms, and the running sum is a (hi, lo) pair updated by TwoSum (Knuth,
+// TAOCP vol. 2, 4.2.2).  The omitted lo*lo term and the float32 rounding of
+// the low-order sum leave a relative error near k * 2^-48 of the largest
+// partial sum.  The intrinsics keep the compiler from contracting the
+// TwoSum steps into FMAs, which would break them.
+//
+// A CTA of 256 threads computes a 32 x 32 tile, 2 x 2 values per thread,
+// through 16-deep k tiles staged in shared memory (double-buffered).  With
+// splits > 1 each split of k writes a float64 partial tile (part[s] is
+// m x p) and dgemm_reduce_kernel sums the splits in order.
+constexpr int DG_T = 32, DG_K = 16, DG_THREADS = 256;
+
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_split(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+// (sh, sl) += a * b for float-float a, b.
+__device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(DG_THREADS) dgemm_kernel(const double* __restrict__ A, int64_t lda,
+                                                          const double* __restrict__ B, int64_t ldb, int64_t m,
+                                                          int64_t k, int64_t p, int64_t kc, double* __restrict__ C,
+                                                          int64_t ldc, double* __restrict__ part) {
+  __shared__ float Ah[2][DG_K][DG_T + 1], Al[2][DG_K][DG_T + 1];
+  __shared__ float Bh[2][DG_K][DG_T + 1], Bl[2][DG_K][DG_T + 1];
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const int64_t i0 = (int64_t)blockIdx.x * DG_T, c0 = (int64_t)blockIdx.y * DG_T;
+  const int64_t kb = (int64_t)blockIdx.z * kc, ke = min(k, kb + kc);
+  float sh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, sl[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  double ra[2], rb[2];
+  // Element e of this thread's share of a staged tile: (row ii, depth kk) of
+  // op(A) and (depth kb2, column cc) of op(B); the fastest index follows the
+  // operand's contiguous dimension so the global loads coalesce.
+  auto a_at = [&](int e, int& ii, int& kk) {
+    if (!TA) { ii = t % 32; kk = t / 32 + 8 * e; } else { kk = t % 16; ii = t / 16 + 16 * e; }
+  };
+  auto b_at = [&](int e, int& kb2, int& cc) {
+    if (!TB) { kb2 = t % 16; cc = t / 16 + 16 * e; } else { cc = t % 32; kb2 = t / 32 + 8 * e; }
+  };
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      int ii, kk, kb2, cc;
+      a_at(e, ii, kk);
+      b_at(e, kb2, cc);
+      const int64_t gi = i0 + ii, gk = k0 + kk, gc = c0 + cc, gk2 = k0 + kb2;
+      ra[e] = (gi < m && gk < ke) ? (TA ? A[gk + lda * gi] : A[gi + lda * gk]) : 0.0;
+      rb[e] = (gc < p && gk2 < ke) ? (TB ? B[gc + ldb * gk2] : B[gk2 + ldb * gc]) : 0.0;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      int ii, kk, kb2, cc;
+      a_at(e, ii, kk);
+      b_at(e, kb2, cc);
+      const FF a = ff_split(ra[e]), b = ff_split(rb[e]);
+      Ah[buf][kk][ii] = a.hi;
+      Al[buf][kk][ii] = a.lo;
+      Bh[buf][kb2][cc] = b.hi;
+      Bl[buf][kb2][cc] = b.lo;
+    }
+  };
+  const int64_t ntile = kb < ke ? (ke - kb + DG_K - 1) / DG_K : 0;
+  if (ntile > 0) {
+    fetch(kb);
+    store(0);
+    __syncthreads();
+    for (int64_t tt = 0; tt < ntile; ++tt) {
+      const int buf = tt & 1;
+      if (tt + 1 < ntile) fetch(kb + (tt + 1) * DG_K);
+#pragma unroll 4
+      for (int kk = 0; kk < DG_K; ++kk) {
+        const float ah0 = Ah[buf][kk][ty], ah1 = Ah[buf][kk][ty + 16];
+        const float al0 = Al[buf][kk][ty], al1 = Al[buf][kk][ty + 16];
+        const float bh0 = Bh[buf][kk][tx], bh1 = Bh[buf][kk][tx + 16];
+        const float bl0 = Bl[buf][kk][tx], bl1 = Bl[buf][kk][tx + 16];
+        ff_fma(ah0, al0, bh0, bl0, sh[0][0], sl[0][0]);
+        ff_fma(ah0, al0, bh1, bl1, sh[0][1], sl[0][1]);
+        ff_fma(ah1, al1, bh0, bl0, sh[1][0], sl[1][0]);
+        ff_fma(ah1, al1, bh1, bl1, sh[1][1], sl[1][1]);
+      }
+      if (tt + 1 < ntile) store(buf ^ 1);
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int64_t gi = i0 + ty + 16 * u, gc = c0 + tx + 16 * v;
+      if (gi < m && gc < p) {
+        const double r = (double)sh[u][v] + (double)sl[u][v];
+        if (part) part[((int64_t)blockIdx.z * p + gc) * m + gi] = r;
+        else C[gi + ldc * gc] = r;
+      }
+    }
+}
+
+__global__ void dgemm_reduce_kernel(const double* __restrict__ part, int splits, int64_t m, int64_t p,
+                                    double* __restrict__ C, int64_t ldc) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= m * p) return;
+  const int64_t i = o % m, c = o / m;
+  double s = 0.0;
+  for (int sp = 0; sp < splits; ++sp) s += part[(int64_t)sp * m * p + o];
+  C[i + ldc * c] = s;
+}
+
+// op(A) op(B) with a split count for about two CTAs per SM (the grid has to
+// cover the chip: the tiles are small), limited by the k tiles and by the
+// partial buffer (part_cap doubles; nullptr = no split).
+// part must not overlap A, B or C.
+template <bool TA, bool TB>
+static int dgemm(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int64_t k, int64_t p,
+                 double* C, int64_t ldc, double* part, int64_t part_cap, cudaStream_t st) {
+  if (m <= 0 || p <= 0) return ATK_OK;
+  const int64_t tiles = ceil_div(m, DG_T) * ceil_div(p, DG_T);
+  int64_t splits = std::max<int64_t>(1, ceil_div(2 * (int64_t)num_sms(), tiles));
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, ceil_div(k, DG_K)));
+  if (!part) splits = 1;
+  else splits = std::min<int64_t>(splits, std::max<int64_t>(1, part_cap / (m * p)));
+  const int64_t kc = ceil_div(ceil_div(std::max<int64_t>(k, 1), splits), DG_K) * DG_K;
+  splits = std::max<int64_t>(1, ceil_div(std::max<int64_t>(k, 1), kc));
+  dim3 grid((unsigned)ceil_div(m, DG_T), (unsigned)ceil_div(p, DG_T), (unsigned)splits);
+  dgemm_kernel<TA, TB><<<grid, DG_THREADS, 0, st>>>(A, lda, B, ldb, m, k, p, kc, C, ldc,
+                                                   splits > 1 ? part : nullptr);
+  ATK_LAUNCHED();
+  if (splits > 1) {
+    dgemm_reduce_kernel<<<(unsigned)ceil_div(m * p, 256), 256, 0, st>>>(part, (int)splits, m, p, C, ldc);
+    ATK_LAUNCHED();
+  }
+  return ATK_OK;
+}
+
 constexpr int GT_CHUNK = 16;  // rows of A per CTA in A^T B
-
-// part[chunk][R x R] = A[chunk rows]^T B[chunk rows]
-__global__ void gemm_tn_part_kernel(const double* __restrict__ A, const double* __restrict__ B, int64_t n, int64_t R,
-                                    double* __restrict__ part) {
-  int64_t o = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
-  if (o >= R * R) return;
-  int64_t r1 = o % R, r2 = o / R;
-  int64_t i0 = (int64_t)blockIdx.x * GT_CHUNK, i1 = min(n, i0 + GT_CHUNK);
-  double s = 0.0;
-  for (int64_t i = i0; i < i1; ++i) s = fma(A[i + n * r1], B[i + n * r2], s);
-  part[(int64_t)blockIdx.x * R * R + o] = s;
-}
-
-__global__ void sum_parts_kernel(const double* __restrict__ part, int nparts, int64_t len, double* __restrict__ out) {
-  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= len) return;
-  double s = 0.0;
-  for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * len + o];
-  out[o] = s;
-}
 
 size_t smallla_scratch_bytes(int64_t n, int64_t R) {
   int64_t chunks = ceil_div(std::max<int64_t>(n, 1), GT_CHUNK);
@@ -40,18 +179,16 @@ size_t smallla_scratch_bytes(int64_t n, int64_t R) {
   return sizeof(double) * (size_t)(chunks * R * R + 4 * R * R + 2 * n * R) + 4096;
 }
 
+// Doubles available for split partials at the head of the scratch.
+static int64_t part_cap(int64_t n, int64_t R) { return ceil_div(std::max<int64_t>(n, 1), GT_CHUNK) * R * R; }
+
 int gemm_tn_f64(const double* A, const double* B, int64_t n, int64_t R, double* G, double* scratch, cudaStream_t st) {
-  int64_t chunks = ceil_div(std::max<int64_t>(n, 1), GT_CHUNK);
   if (n == 0) {
     ATK_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * R * R, st));
     return ATK_OK;
   }
-  dim3 grid((unsigned)chunks, (unsigned)ceil_div(R * R, 256));
-  gemm_tn_part_kernel<<<grid, 256, 0, st>>>(A, B, n, R, scratch);
-  ATK_LAUNCHED();
-  sum_parts_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(scratch, (int)chunks, R * R, G);
-  ATK_LAUNCHED();
-  return ATK_OK;
+  // G = A^T B, split over the n rows into partials at the head of the scratch.
+  return dgemm<true, false>(A, n, B, n, R, n, R, G, R, scratch, part_cap(n, R), st);
 }
 
 // One CTA: Cholesky G = C C^T (C lower), Cinv = C^{-1} (lower) and, if
@@ -118,76 +255,9 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict_
   }
 }
 
-// out (m x R) = X (m x R) * M (R x R), or X * M^T when transM.
-__global__ void gemm_nn_kernel(const double* __restrict__ X, const double* __restrict__ M, int64_t m, int64_t R,
-                               int transM, double* __restrict__ out) {
-  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= m * R) return;
-  int64_t i = o % m, c = o / m;
-  double s = 0.0;
-  for (int64_t t = 0; t < R; ++t) s = fma(X[i + m * t], transM ? M[c + R * t] : M[t + R * c], s);
-  out[o] = s;
-}
-
-// C (m x p) = A (m x k) B (k x p), all column-major float64; one thread per output.
-__global__ void gemm_f64_kernel(const double* __restrict__ A, const double* __restrict__ B, int64_t m, int64_t k,
-                                int64_t p, double* __restrict__ C) {
-  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= m * p) return;
-  int64_t i = o % m, c = o / m;
-  double s = 0.0;
-  for (int64_t t = 0; t < k; ++t) s = fma(A[i + m * t], B[t + k * c], s);
-  C[o] = s;
-}
-
-// lam[r] = u_r^T z_r (Rayleigh quotients, z = S u), disc = trace(S) - sum_r lam[r].
-// One CTA; fixed-order reductions.
-__global__ void __launch_bounds__(256) rayleigh_kernel(const double* __restrict__ S, const double* __restrict__ U,
-                                                       const double* __restrict__ Z, int64_t n, int64_t R,
-                                                       double* __restrict__ lam_out, double* __restrict__ disc_out) {
-  __shared__ double red[256];
-  __shared__ double lam_sum;
-  if (threadIdx.x == 0) lam_sum = 0.0;
-  __syncthreads();
-  for (int64_t r = 0; r < R; ++r) {
-    double part = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) part += U[i + n * r] * Z[i + n * r];
-    red[threadIdx.x] = part;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      if (lam_out) lam_out[r] = red[0];
-      lam_sum += red[0];
-    }
-    __syncthreads();
-  }
-  double tr = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) tr += S[i + n * i];
-  red[threadIdx.x] = tr;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && disc_out) *disc_out = red[0] - lam_sum;
-}
-
-int gemm_f64(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, cudaStream_t st) {
-  gemm_f64_kernel<<<(unsigned)ceil_div(m * p, 256), 256, 0, st>>>(A, B, m, k, p, C);
-  ATK_LAUNCHED();
-  return ATK_OK;
-}
-
-int rayleigh_f64(const double* S, const double* U, int64_t n, int64_t R, double* Z, double* lam_out,
-                 double* disc_out, cudaStream_t st) {
-  gemm_f64_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(S, U, n, n, R, Z);
-  ATK_LAUNCHED();
-  rayleigh_kernel<<<1, 256, 0, st>>>(S, U, Z, n, R, lam_out, disc_out);
-  ATK_LAUNCHED();
-  return ATK_OK;
+int gemm_f64_split(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, double* part,
+                   int64_t part_cap, cudaStream_t st) {
+  return dgemm<false, false>(A, m, B, k, m, k, p, C, m, part, part_cap, st);
 }
 
 __global__ void polar_coef_kernel(const double* __restrict__ G, int64_t R, double* __restrict__ M) {
@@ -231,8 +301,7 @@ int solve_spd_right_f64(double* X, int64_t m, int64_t R, const double* G, double
   if (!b.panel) { set_error("solve_spd: scratch too small"); return ATK_EINVAL; }
   chol_inv_kernel<<<1, 256, 0, st>>>(G, (int)R, b.M1, b.M2, b.M3, dev_status);
   ATK_LAUNCHED();
-  gemm_nn_kernel<<<(unsigned)ceil_div(m * R, 256), 256, 0, st>>>(X, b.M3, m, R, 0, b.panel);
-  ATK_LAUNCHED();
+  ATK_TRY((dgemm<false, false>(X, m, b.M3, R, m, R, R, b.panel, m, b.part, part_cap(m, R), st)));
   ATK_CUDA(cudaMemcpyAsync(X, b.panel, sizeof(double) * m * R, cudaMemcpyDeviceToDevice, st));
   return ATK_OK;
 }
@@ -243,8 +312,7 @@ int polar_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_
   ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, b.part, st));
   polar_coef_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M1, R, b.M2);
   ATK_LAUNCHED();
-  gemm_nn_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(U, b.M2, n, R, 0, b.panel);
-  ATK_LAUNCHED();
+  ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, b.part, part_cap(n, R), st)));
   ATK_CUDA(cudaMemcpyAsync(U, b.panel, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
   return ATK_OK;
 }
@@ -256,14 +324,12 @@ int cholqr2_f64(double* L, int64_t n, int64_t R, double* Rhat, double* scratch, 
   ATK_TRY(gemm_tn_f64(L, L, n, R, b.M1, b.part, st));
   chol_inv_kernel<<<1, 256, 0, st>>>(b.M1, (int)R, b.M2, b.M3, nullptr, dev_status);
   ATK_LAUNCHED();
-  gemm_nn_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(L, b.M3, n, R, 1, b.panel);
-  ATK_LAUNCHED();
+  ATK_TRY((dgemm<false, true>(L, n, b.M3, R, n, R, R, b.panel, n, b.part, part_cap(n, R), st)));
   // Pass 2 on Q1: Q1^T Q1 = C2 C2^T, Q = Q1 C2^{-T}.
   ATK_TRY(gemm_tn_f64(b.panel, b.panel, n, R, b.M1, b.part, st));
   chol_inv_kernel<<<1, 256, 0, st>>>(b.M1, (int)R, b.M4, b.M3, nullptr, dev_status);
   ATK_LAUNCHED();
-  gemm_nn_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(b.panel, b.M3, n, R, 1, L);
-  ATK_LAUNCHED();
+  ATK_TRY((dgemm<false, true>(b.panel, n, b.M3, R, n, R, R, L, n, b.part, part_cap(n, R), st)));
   rhat_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M2, b.M4, R, Rhat);
   ATK_LAUNCHED();
   return ATK_OK;
