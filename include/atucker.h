@@ -179,12 +179,40 @@ int atucker_plan_sync(atucker_plan_t plan);
  *   [0] Gram partial-tile kernel ms   [1] Gram split-K reduction ms
  *   [2] eigensolver ms (Jacobi, selection, float64 polish)
  *   [3] TTM ms   [4] ALS mode ms   [5] norms ms   [6] total ms
- *   [7] Gram kernel launches   [8] kernel launches of this library   [9] runs
+ *   [7] Gram kernel launches   [8] kernel launches made by this plan's runs   [9] runs
  * Resets the accumulators. */
 int atucker_plan_timings(atucker_plan_t plan, double* out, int count);
 
 /* Free the plan and its workspace.  Safe on NULL. */
 void atucker_plan_destroy(atucker_plan_t plan);
+
+/* Several independent tensors at once (Alg. 2 per tensor).  Plan i runs
+ * atucker_sthosvd(plans[i], xs[i], cores[i], factors[i], discarded[i]) on a
+ * host thread of its own (a persistent pool), so one tensor's eigensolver,
+ * which occupies a few CTAs, overlaps another tensor's Gram and TTM.  Give the
+ * plans distinct streams for that overlap; on one shared stream the runs
+ * serialise.  Stream priorities (cudaStreamCreateWithPriority) decide which
+ * plan's kernels the GPU dispatches first when both have work; the plan on the
+ * longest chain benefits from the highest priority.
+ *   count            number of plans, >= 1
+ *   plans            host array of count distinct plans
+ *   xs, cores,       host arrays of count device pointers, as in
+ *   factors          atucker_sthosvd
+ *   discarded        host array of count device pointers (entries nullable),
+ *                    or NULL for none
+ * Returns when every run is enqueued (or finished, for plans with
+ * ATK_OPT_SYNC).  On failure returns the first failing plan's status in plan
+ * order; atucker_last_error() names the plan.  Per-plan timings and launch
+ * counts (atucker_plan_timings) stay per plan. */
+int atucker_sthosvd_many(int count, const atucker_plan_t* plans, const float* const* xs, float* const* cores,
+                         float* const* factors, double* const* discarded);
+
+/* As atucker_sthosvd_many with HOST buffers: plan i runs
+ * atucker_sthosvd_host, so one plan's copies overlap another's kernels.
+ * Synchronous: returns when every result is in host memory. */
+int atucker_sthosvd_host_many(int count, const atucker_plan_t* plans, const float* const* xs_host,
+                              float* const* cores_host, float* const* factors_host,
+                              double* const* discarded_host);
 
 /* One-shot form of the problem statement (Alg. 2): plan, run synchronously on
  * the default stream in FP32, free.  Device pointers as in atucker_sthosvd. */

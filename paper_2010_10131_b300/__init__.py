@@ -52,6 +52,8 @@ _SIGS = {
     "atucker_plan_set_option": (_i32, [_vp, _i32, _i64]),
     "atucker_sthosvd": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "atucker_sthosvd_host": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "atucker_sthosvd_many": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp]),
+    "atucker_sthosvd_host_many": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp]),
     "atucker_plan_sync": (_i32, [_vp]),
     "atucker_plan_timings": (_i32, [_vp, _vp, _i32]),
     "atucker_plan_destroy": (None, [_vp]),
@@ -256,6 +258,44 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _ptrs(vals):
+    return (_vp * len(vals))(*vals)
+
+
+def run_many(plans, xs, cores, factors, discarded=None):
+    """Independent tensors at once (atucker_sthosvd_many): plan i on its own host
+    thread and stream.  Every argument is a list with one entry per plan."""
+    torch = _torch()
+    k = len(plans)
+    if not (len(xs) == len(cores) == len(factors) == k) or (discarded is not None and len(discarded) != k):
+        raise ValueError("run_many: one x, core and factor buffer per plan")
+    d = None
+    if discarded is not None:
+        d = _ptrs([_dev(t, torch.float64).value if t is not None else None for t in discarded])
+    _check(lib().atucker_sthosvd_many(k, _ptrs([p._h.value for p in plans]),
+                                      _ptrs([_dev(x, torch.float32).value for x in xs]),
+                                      _ptrs([_dev(c, torch.float32).value for c in cores]),
+                                      _ptrs([_dev(f, torch.float32).value for f in factors]), d),
+           "atucker_sthosvd_many")
+
+
+def run_many_host(plans, xs_host, cores_host, factors_host, discarded_host=None):
+    """Host-buffer form of run_many (atucker_sthosvd_host_many); synchronous."""
+    torch = _torch()
+    k = len(plans)
+    if not (len(xs_host) == len(cores_host) == len(factors_host) == k):
+        raise ValueError("run_many_host: one x, core and factor buffer per plan")
+    for group in (xs_host, cores_host, factors_host):
+        for t in group:
+            assert t.device.type == "cpu" and t.is_contiguous() and t.dtype == torch.float32
+    d = _ptrs([t.data_ptr() for t in discarded_host]) if discarded_host is not None else None
+    _check(lib().atucker_sthosvd_host_many(k, _ptrs([p._h.value for p in plans]),
+                                           _ptrs([t.data_ptr() for t in xs_host]),
+                                           _ptrs([t.data_ptr() for t in cores_host]),
+                                           _ptrs([t.data_ptr() for t in factors_host]), d),
+           "atucker_sthosvd_host_many")
 
 
 def sthosvd(x, dims, ranks, mode_order=None, solver=None, als_sweeps: int = 5, seed: int = 0,

@@ -19,19 +19,21 @@ int cuda_status(cudaError_t e, const char* what) {
   if (e == cudaErrorMemoryAllocation) return ATK_ENOMEM;
   return ATK_ECUDA;
 }
-static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
-void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// Kernel launches are counted per host thread: a plan's run happens on one
+// thread, so its launches are the thread's count before and after, even when
+// other plans run on other threads (atucker_sthosvd_many).
+static thread_local long long t_launches = 0;
+void count_launch() { ++t_launches; }
+long long launch_count() { return t_launches; }
+void count_launches(long long k) { t_launches += k; }
 
 int num_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {  // thread-safe one-time initialisation
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return sms;
 }
 
@@ -139,7 +141,7 @@ struct atucker_plan_s {
   struct Rec { int phase; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<Rec> mrecs;  // per-mode records: phase = mode index
-  long long gram_launches = 0, runs = 0, launches_mark = 0;
+  long long gram_launches = 0, runs = 0, launches = 0;
   cudaEvent_t ev() {
     if (evnext == evpool.size()) {
       cudaEvent_t e = nullptr;
@@ -387,8 +389,7 @@ int atucker_plan_set_option(atucker_plan_t p, int key, int64_t value) {
       p->timing = value ? 1 : 0;
       p->recs.clear();
       p->evnext = 0;
-      p->gram_launches = p->runs = 0;
-      p->launches_mark = launch_count();
+      p->gram_launches = p->runs = p->launches = 0;
       return ATK_OK;
     case ATK_OPT_JACOBI_MAX_SWEEPS:
       if (value < 1 || value > 200) break;
@@ -413,8 +414,7 @@ int atucker_plan_sync(atucker_plan_t p) {
   return ATK_OK;
 }
 
-int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* factors_out, double* discarded_out) {
-  if (!p || !x || !core_out || !factors_out) { set_error("null argument"); return ATK_EINVAL; }
+static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float* factors_out, double* discarded_out) {
   cudaStream_t st = p->st;
   int64_t cur[8];
   for (int k = 0; k < p->order; ++k) cur[k] = p->dims[k];
@@ -486,6 +486,14 @@ int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* fa
   return ATK_OK;
 }
 
+int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* factors_out, double* discarded_out) {
+  if (!p || !x || !core_out || !factors_out) { set_error("null argument"); return ATK_EINVAL; }
+  const long long l0 = launch_count();
+  const int s = sthosvd_run(p, x, core_out, factors_out, discarded_out);
+  p->launches += launch_count() - l0;
+  return s;
+}
+
 int atucker_sthosvd_host(atucker_plan_t p, const float* x_host, float* core_host, float* factors_host,
                          double* discarded_host) {
   if (!p || !x_host || !core_host || !factors_host) { set_error("null argument"); return ATK_EINVAL; }
@@ -518,15 +526,13 @@ int atucker_plan_timings(atucker_plan_t p, double* out, int count) {
     ATK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
     out[r.phase] += ms;
   }
-  long long now = launch_count();
   out[PH_TOTAL + 1] = (double)p->gram_launches;
-  out[PH_TOTAL + 2] = (double)(now - p->launches_mark);
+  out[PH_TOTAL + 2] = (double)p->launches;
   out[PH_TOTAL + 3] = (double)p->runs;
   p->recs.clear();
   p->mrecs.clear();  // per-mode records are read first (atucker_plan_mode_timings) or dropped here
   p->evnext = 0;
-  p->gram_launches = p->runs = 0;
-  p->launches_mark = now;
+  p->gram_launches = p->runs = p->launches = 0;
   return ATK_OK;
 }
 

@@ -457,15 +457,15 @@ __global__ void __launch_bounds__(RED_THREADS) tc_reduce_sym_kernel(const float*
 
 template <int P>
 int gram_ctas_per_sm() {
-  static int per = -1;  // depends only on the kernel and the device
-  if (per < 0) {
+  // Depends only on the kernel and the device; thread-safe one-time initialisation.
+  static const int per = [] {
     cudaFuncSetAttribute(tc_gram_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Ring<P>::BYTES);
     cudaFuncSetAttribute(tc_pack_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(KP * PACK_LD * sizeof(float)));
     int v = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, tc_gram_kernel<P>, GRAM_THREADS, Ring<P>::BYTES);
-    per = std::max(1, std::min(v, 4));  // TMEM: 4 x 128 columns
-  }
+    return std::max(1, std::min(v, 4));  // TMEM: 4 x 128 columns
+  }();
   return per;
 }
 

@@ -49,6 +49,20 @@ def test_argument_validation_runs_on_host():
     assert lib.atucker_gram(None, 1, 1, 1, 0, None, None) == atk.EINVAL
 
 
+def test_run_many_validation_runs_on_host():
+    """The concurrent entry points check their plan list before any device call."""
+    lib = atk.lib()
+    fake = ctypes.c_void_p(0x1000)
+    plans = (ctypes.c_void_p * 2)(fake, fake)
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert lib.atucker_sthosvd_many(2, plans, arr, arr, arr, None) == atk.EINVAL
+    assert b"twice" in lib.atucker_last_error()
+    none = (ctypes.c_void_p * 2)(fake, None)
+    assert lib.atucker_sthosvd_many(2, none, arr, arr, arr, None) == atk.EINVAL
+    assert lib.atucker_sthosvd_many(0, plans, arr, arr, arr, None) == atk.EINVAL
+    assert lib.atucker_sthosvd_host_many(2, plans, None, arr, arr, None) == atk.EINVAL
+
+
 def test_batch_validation_runs_on_host():
     """The batched form rejects shapes outside its limits before touching the device."""
     lib = atk.lib()
