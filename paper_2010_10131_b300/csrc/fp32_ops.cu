@@ -34,25 +34,44 @@ constexpr int SPLIT_MAX_K = 8192;
 
 // A view operand with k = c (the other index) and m = i (mode index): CI role.
 // Index state is 32-bit: every tensor the library accepts has fewer than 2^31
-// elements, so every offset below fits.
-template <int W>
+// elements, so every offset below fits.  When lo == 1, n % 4 == 0 and the
+// tensor is 16-byte aligned (the first mode of any tensor with I_1 % 4 == 0),
+// the VEC instantiation moves four consecutive i per thread per load and per
+// store (128-bit accesses): a quarter of the load and store instructions,
+// which compete with the FMAs for issue slots.  The caller checks those
+// conditions (kc_vec_ok) before it picks VEC.
+template <int W, bool VEC = false>
 struct ViewLoaderKC {
   static constexpr int PER = TK * W / NT;
+  static constexpr int PER4 = (TK * (W / 4) + NT - 1) / NT;  // float4 per thread (vector path)
   const float* y;
   int lo, n, c_end, i0;
   bool lanes_on_m;  // lo == 1: m (= i) is contiguous
+  bool vec;
   int km, mm, step;
-  float r[PER];
+  float r[VEC ? 4 * PER4 : PER];
   __device__ void init(const float* y_, int64_t lo_, int64_t n_, int64_t c_end_, int64_t i0_) {
     y = y_; lo = (int)lo_; n = (int)n_; c_end = (int)c_end_; i0 = (int)i0_;
     lanes_on_m = (lo == 1);
+    vec = VEC;
     int t = threadIdx.x;
-    if (lanes_on_m) { mm = t % W; km = t / W; step = NT / W; }
+    if (VEC) { mm = 4 * (t % (W / 4)); km = t / (W / 4); step = NT / (W / 4); }
+    else if (lanes_on_m) { mm = t % W; km = t / W; step = NT / W; }
     else { km = t % TK; mm = t / TK; step = NT / TK; }
   }
   __device__ void fetch(int64_t c0_) {
     const int c0 = (int)c0_;
-    if (lanes_on_m) {
+    if (VEC) {
+      const int i = i0 + mm;
+#pragma unroll
+      for (int e = 0; e < PER4; ++e) {
+        const int k = km + e * step;
+        const int c = c0 + k;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < TK && c < c_end && i < n) v = __ldg(reinterpret_cast<const float4*>(y + (i + n * c)));
+        r[4 * e] = v.x; r[4 * e + 1] = v.y; r[4 * e + 2] = v.z; r[4 * e + 3] = v.w;
+      }
+    } else if (lanes_on_m) {
       const int i = i0 + mm;
 #pragma unroll
       for (int e = 0; e < PER; ++e) {
@@ -72,7 +91,15 @@ struct ViewLoaderKC {
     }
   }
   __device__ void store(float* s) const {
-    if (lanes_on_m) {
+    if (VEC) {
+#pragma unroll
+      for (int e = 0; e < PER4; ++e) {
+        const int k = km + e * step;
+        if (k < TK)
+          *reinterpret_cast<float4*>(s + k * (W + PAD) + mm) =
+              make_float4(r[4 * e], r[4 * e + 1], r[4 * e + 2], r[4 * e + 3]);
+      }
+    } else if (lanes_on_m) {
 #pragma unroll
       for (int e = 0; e < PER; ++e) s[(km + e * step) * (W + PAD) + mm] = r[e];
     } else {
@@ -196,6 +223,10 @@ struct Block {
       for (int h = 0; h < H; ++h) dst[h] = src[h];
     }
   }
+  // SKIP_LOWER (diagonal Gram tiles, BM == BN): leave out the accumulators of
+  // the lower-left quadrant (rows >= BM/2, columns < BN/2), which lie wholly
+  // below the diagonal and are never read; a quarter of the tile's FMAs.
+  template <bool SKIP_LOWER = false>
   __device__ void mma(const float* sa, const float* sb) {
 #pragma unroll
     for (int k = 0; k < TK; ++k) {
@@ -211,7 +242,8 @@ struct Block {
 #pragma unroll
       for (int u = 0; u < TM; ++u)
 #pragma unroll
-        for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < TN; ++v)
+          if (!(SKIP_LOWER && TN > 1 && u >= TM / 2 && v < TN / 2)) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
     }
   }
 };
@@ -222,7 +254,7 @@ struct Block {
 // row-major position in the upper triangle.  Diagonal and off-diagonal tiles
 // are separate launches (DIAG): a diagonal tile loads one operand and uses it
 // twice, and neither instantiation carries the other's registers.
-template <int BM, int TM, bool DIAG>
+template <int BM, int TM, bool DIAG, bool VEC>
 __global__ void __launch_bounds__(NT, 2)
 gram_ci_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, int T, int64_t kc,
                float* __restrict__ part) {
@@ -243,7 +275,7 @@ gram_ci_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, i
   const int tile = ti * T - ti * (ti - 1) / 2 + (tj - ti);
   const int64_t J = lo * hi;
   const int64_t cb = (int64_t)split * kc, ce = min(J, cb + kc);
-  ViewLoaderKC<BM> la, lb;
+  ViewLoaderKC<BM, VEC> la, lb;
   la.init(y, lo, n, ce, (int64_t)ti * BM);
   if (!DIAG) lb.init(y, lo, n, ce, (int64_t)tj * BM);
   Block<BM, BM, TM, TM> blk;
@@ -263,7 +295,7 @@ gram_ci_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, i
         la.fetch(cb + (t + 1) * TK);
         if (!DIAG) lb.fetch(cb + (t + 1) * TK);
       }
-      if (DIAG) blk.mma(sA + buf * SA, sA + buf * SA);
+      if (DIAG) blk.template mma<true>(sA + buf * SA, sA + buf * SA);
       else blk.mma(sA + buf * SA, sB + buf * SA);
       if (t + 1 < ntile) {
         la.store(sA + (buf ^ 1) * SA);
@@ -281,12 +313,26 @@ gram_ci_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, i
       out[Block<BM, BM, TM, TM>::row_of(blk.ty, u) * BM + Block<BM, BM, TM, TM>::col_of(blk.tx, v)] = blk.acc[u][v];
 }
 
+// The vector loader's conditions: the mode-n index is contiguous (lo == 1),
+// rows of four floats stay inside one column (n % 4 == 0), and the base is
+// 16-byte aligned.
+static bool kc_vec_ok(const float* y, const View& v) {
+  return v.lo == 1 && v.n % 4 == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0;
+}
+
+template <int BM, int TM, bool VEC>
+static void launch_gram_tiles_v(const float* y, const View& v, int T, int ns_d, int64_t kc_d, int ns_o,
+                                int64_t kc_o, float* part, cudaStream_t st) {
+  gram_ci_kernel<BM, TM, true, VEC><<<dim3(T, ns_d), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_d, part);
+  if (T > 1)
+    gram_ci_kernel<BM, TM, false, VEC><<<dim3(T * (T - 1) / 2, ns_o), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_o,
+                                                                                    part);
+}
 template <int BM, int TM>
 static void launch_gram_tiles(const float* y, const View& v, int T, int ns_d, int64_t kc_d, int ns_o, int64_t kc_o,
                               float* part, cudaStream_t st) {
-  gram_ci_kernel<BM, TM, true><<<dim3(T, ns_d), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_d, part);
-  if (T > 1)
-    gram_ci_kernel<BM, TM, false><<<dim3(T * (T - 1) / 2, ns_o), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_o, part);
+  if (kc_vec_ok(y, v)) launch_gram_tiles_v<BM, TM, true>(y, v, T, ns_d, kc_d, ns_o, kc_o, part, st);
+  else launch_gram_tiles_v<BM, TM, false>(y, v, T, ns_d, kc_d, ns_o, kc_o, part, st);
 }
 
 // Cross product C (n x R) = sum_c Y(c, i) P(c, r), P a (lo, R, hi) tensor.
