@@ -448,7 +448,7 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
       // S = Y_(n) Y_(n)^T; U = leading eigenvectors; Y' = Y x_n U^T.
       cudaEvent_t mid = tm ? p->ev() : nullptr;
       if (p->precision == ATK_FP32) {
-        ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid, p->gbm[n]));
+        ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid, p->gbm[n], p->dev_status));
       } else {
         ATK_TRY(tc_gram(Y, v, p->precision, p->S, (float*)p->scratch, p->scratch_bytes, p->dev_status, st));
         if (mid) ATK_CUDA(cudaEventRecord(mid, st));
@@ -599,9 +599,12 @@ int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precisio
   View v{lo, n, hi};
   StreamScratch sc(st);
   if (precision == ATK_FP32) {
-    size_t bytes = gram_scratch_bytes(v);
+    size_t bytes = gram_scratch_bytes(v) + 256;
     ATK_TRY(sc.alloc(bytes));
-    return gram_f32(y, v, S_out, (float*)sc.ptr, bytes, st);
+    int* status = (int*)((char*)sc.ptr + bytes - 256);
+    ATK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    ATK_TRY(gram_f32(y, v, S_out, (float*)sc.ptr, bytes - 256, st, nullptr, 0, status));
+    return read_status(status, st);
   }
   size_t bytes = tc_gram_scratch_bytes(v, precision) + 256;
   ATK_TRY(sc.alloc(bytes));

@@ -40,6 +40,7 @@
 
 #include <algorithm>
 
+#include "async_copy.cuh"
 #include "atk_internal.cuh"
 
 namespace atk {
@@ -55,9 +56,14 @@ constexpr int GRAM_THREADS = 128;    // warp 0: producer + epilogue, warp 1: MMA
 constexpr int PACK_THREADS = 256;
 constexpr int PACK_LD = BM + 1;      // shared-memory pitch (floats) between the tile's c values
 constexpr int SPLIT_MAX_TERMS = 8192;  // c values per float32 partial sum
-constexpr unsigned long long WAIT_NS = 2000000000ULL;  // 2 s per wait
+using ac::WAIT_NS;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using ac::smem_u32;
+using ac::gtime;
+using ac::mbar_try;
+using ac::mbar_wait;
+using ac::bulk_load;
+using ac::arrive_expect;
 
 // tcgen05 shared-memory matrix descriptor, no swizzle.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -106,44 +112,6 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                  " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
                  "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ unsigned long long gtime() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-               : "=r"(done)
-               : "r"(bar), "r"(parity));
-  return done != 0;
-}
-
-// Wait for the phase of parity `parity` to complete.  Gives up after WAIT_NS,
-// or at once when `abort` is set (pass nullptr for a wait that must not be cut
-// short, such as a drain of work in flight).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtime();
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if (abort && *abort) return false;
-    if ((it & 63) == 0 && gtime() - t0 > WAIT_NS) return false;
-  }
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void arrive_expect(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 // ---------------------------------------------------------------------------
