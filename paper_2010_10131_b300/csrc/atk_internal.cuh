@@ -168,6 +168,17 @@ int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int ma
             double* U64_out, double* lambda_out, double* discarded_out, int* dev_status, char* scratch,
             size_t scratch_bytes, cudaStream_t st);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (never
+// lowers it; thread-safe).  Call outside stream capture.
+int raise_smem_limit(const void* fn, size_t bytes);
+// All eigenpairs of a small symmetric matrix on one CTA, float32
+// (tridiag_eig.cu): S n x n float64, 1 <= n <= 160; diag_out (n) ascending,
+// V_out n x n row-major with column j the eigenvector of diag_out[j].
+// tridiag_eig_prepare() sets the kernel's shared-memory limit for every n
+// (call it before capturing a launch into a graph).
+int tridiag_eig_prepare();
+int tridiag_eig_f32(const double* S, int n, float* diag_out, float* V_out, cudaStream_t st);
+
 // Float64 small dense linear algebra (smallla.cu).
 size_t smallla_scratch_bytes(int64_t n, int64_t R);
 // G (R x R) = A^T B, A and B n x R float64.

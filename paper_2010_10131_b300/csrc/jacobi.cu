@@ -24,7 +24,7 @@ namespace atk {
 // Raise a kernel's dynamic shared-memory limit to at least `bytes`, never
 // lower it: launches captured in cached graphs keep their sizes, so a later
 // call with a smaller block must not shrink the limit under them.
-static int raise_smem_limit(const void* fn, size_t bytes) {
+int raise_smem_limit(const void* fn, size_t bytes) {
   static std::mutex mu;
   static std::vector<std::pair<const void*, size_t>> seen;
   std::lock_guard<std::mutex> g(mu);
@@ -732,14 +732,12 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   b.part = (float*)ar.take(b.part_bytes);
   if (!b.part) { set_error("rr: scratch too small"); return ATK_EINVAL; }
   const View qv{n, m, 1};
-  const int mp = m + (m & 1);
-  const size_t jsm = small_smem<float>(mp);
   // Shared-memory limits of the one-CTA kernels, set outside the captured
   // launch sequences (for the widest block, once).
   {
     const size_t mmax = 156;
     ATK_TRY(raise_smem_limit((const void*)cholinv_f32_kernel, cholinv_smem((int)mmax)));
-    ATK_TRY(raise_smem_limit((const void*)jacobi_small_kernel<float>, small_smem<float>((int)mmax)));
+    ATK_TRY(tridiag_eig_prepare());
   }
   // The three launch sequences between host reads, each a cached graph:
   // setup (the float32 copy of S, a random block, one power step, shifted
@@ -766,8 +764,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
     ATK_TRY(run_graph(kit, st, [&](cudaStream_t s2) -> int {
       ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Z, b, s2));
       ATK_TRY(cross_f32(b.Q, qv, b.Z, m, b.G, b.part, b.part_bytes, s2));
-      jacobi_small_kernel<float><<<1, 512, jsm, s2>>>(b.G, m, mp, max_sweeps, b.diag, b.Vb, dev_status);
-      ATK_LAUNCHED();
+      ATK_TRY(tridiag_eig_f32(b.G, m, b.diag, b.Vb, s2));
       select_kernel<float><<<1, 1024, 0, s2>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
       ATK_LAUNCHED();
       ATK_TRY(f64_to_f32(b.W64, b.Wf, (int64_t)mm, s2));
