@@ -151,6 +151,27 @@ def test_eig_repeated_eigenvalues(atk):
     assert oracle.projector_distance(U.cpu().double().numpy(), Q[:, :4]) <= 1e-4
 
 
+@pytest.mark.parametrize("n,R", [(300, 24), (157, 148)])
+def test_eig_subspace_clustered_kept_eigenvalues(atk, n, R):
+    """Subspace path with exact clusters inside the kept set and a degenerate
+    noise floor: the Rayleigh-Ritz eigensolver must return an orthonormal
+    basis of each cluster (the tridiagonal solver re-orthogonalises inside
+    clusters), so the kept subspace and its energy are still unique.
+    (157, 148) is the widest projection the path builds (m = 156)."""
+    g = np.random.default_rng(11)
+    Q = np.linalg.qr(g.standard_normal((n, n)))[0]
+    k = R // 3
+    top = np.concatenate([np.full(k, 10.0), np.full(k, 7.0), np.full(R - 2 * k, 4.0)])
+    lam = np.concatenate([top, np.full(n - R, 1e-3)])
+    S = (Q * lam) @ Q.T
+    U, lamg, disc = atk.eig(_cuda(S), R, method=2)
+    U = U.cpu().double().numpy()
+    assert np.linalg.norm(U.T @ U - np.eye(R)) <= 1e-6
+    assert oracle.projector_distance(U, Q[:, :R]) <= 1e-4
+    np.testing.assert_allclose(np.sort(lamg.cpu().numpy()[:R])[::-1], top, rtol=1e-7)
+    assert abs(disc.item() - lam[R:].sum()) <= 1e-9 * lam[0] * n
+
+
 @pytest.mark.parametrize("lo,n,hi,R", [(1, 40, 300, 5), (6, 24, 50, 8), (64, 30, 1, 6)])
 def test_als_mode_matches_oracle(atk, lo, n, hi, R):
     dims = [lo, n, hi]
