@@ -189,6 +189,10 @@ int solve_spd_right_f64(double* X, int64_t m, int64_t R, const double* G, double
                         int* dev_status, cudaStream_t st);
 // One Newton-Schulz polar step in float64: U <- U (3I - U^T U) / 2.
 int polar_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_t st);
+// One Gram-Schmidt-ordered orthonormalisation step in float64: U <- U T with
+// U^T U = I + E and T = I - strict_upper(E) - diag(E) / 2; quadratic like the
+// polar step, but column i only ever receives columns j < i.
+int gs_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_t st);
 // CholeskyQR2 in float64: L (n x R) = Q R^, Q overwrites L, R^ (R x R) upper, diag > 0.
 int cholqr2_f64(double* L, int64_t n, int64_t R, double* Rhat, double* scratch, int* dev_status,
                 cudaStream_t st);

@@ -849,7 +849,12 @@ int ttm_f32(const float* y, const View& v, const float* U, int64_t R, float* out
   if (J == 0 || R <= 0) return ATK_OK;
   int bn = cross_bn(R);
   dim3 grid((unsigned)ceil_div(J, 128), (unsigned)ceil_div(R, bn));
-  if (bn == 128) ttm_co_kernel<128, 128, 8, 8><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
+  if ((int64_t)grid.x * grid.y < num_sms() / 2) {
+    // A small product (the n x m panels of the eigensolver): 64 x 64 tiles
+    // put four to eight times as many CTAs on the chip.
+    dim3 g64((unsigned)ceil_div(J, 64), (unsigned)ceil_div(R, 64));
+    ttm_co_kernel<64, 64, 2, 8><<<g64, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
+  } else if (bn == 128) ttm_co_kernel<128, 128, 8, 8><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
   else if (bn == 64) ttm_co_kernel<128, 64, 8, 4><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
   else if (bn == 32) ttm_co_kernel<128, 32, 8, 2><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
   else ttm_co_kernel<128, 16, 8, 1><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);

@@ -809,8 +809,14 @@ __global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R);
 // W = I + X for the k x k symmetric float64 matrix B: for every pair p < q,
 // the Jacobi rotation that zeroes b_pq in its own 2 x 2 problem, to first order
 // (W_pq = s, W_qp = -s).  Pairs whose angle would be large (a nearly
-// degenerate pair, |b_pq| > |b_pp - b_qq| / 10) are left alone; rotations
-// inside such a cluster do not change the subspaces this refinement serves.
+// degenerate pair, |b_pq| > |b_pp - b_qq| / 10) are left alone, and so are
+// pairs whose diagonal entries agree to 1e-7 relative (a degenerate cluster:
+// there b_pq and b_pp - b_qq are both at the level of the input's float32
+// errors squared, and the many rotations of up to 0.1 rad inside a large
+// cluster would add up to a W that two polar steps cannot orthonormalise).
+// Rotations inside a cluster do not change the subspaces this refinement
+// serves; the Rayleigh quotients of its vectors stay within the cluster's
+// width.
 __global__ void simrot_kernel(const double* __restrict__ B, int64_t k, double* __restrict__ W) {
   int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= k * k) return;
@@ -819,7 +825,8 @@ __global__ void simrot_kernel(const double* __restrict__ B, int64_t k, double* _
   int64_t p = i < j ? i : j, q = i < j ? j : i;
   double bpp = B[p + k * p], bqq = B[q + k * q], bpq = B[p + k * q];
   double s = 0.0;
-  if (bpq != 0.0 && fabs(bpq) * 10.0 <= fabs(bqq - bpp)) {
+  const double gap = fabs(bqq - bpp);
+  if (bpq != 0.0 && fabs(bpq) * 10.0 <= gap && gap >= 1e-7 * fmax(fabs(bpp), fabs(bqq))) {
     double tau = (bqq - bpp) / (2.0 * bpq);
     double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
     s = t / sqrt(1.0 + t * t);
@@ -891,7 +898,7 @@ constexpr int REFINE_ROTATION_STEPS = 2;
 constexpr int64_t REFINE_PART_EXTRA = 512 * 1024;
 
 size_t refine_bytes(int64_t n, int64_t k) {
-  return sizeof(double) * (size_t)(2 * n * k + 5 * k * k + k + 8 + n * k + REFINE_PART_EXTRA) + sizeof(int) * (size_t)k +
+  return sizeof(double) * (size_t)(2 * n * k + 6 * k * k + k + 8 + n * k + REFINE_PART_EXTRA) + sizeof(int) * (size_t)k +
          smallla_scratch_bytes(std::max(n, k), k) + 4096;
 }
 
@@ -899,7 +906,7 @@ size_t refine_bytes(int64_t n, int64_t k) {
 // roughly the leading eigenvectors of S in descending order), then the kept
 // R vectors.  Steps:
 //  1. one subspace-iteration step, Qb <- orth(S Qb): normalise the columns,
-//     then two Newton-Schulz polar steps.  Components outside the leading
+//     then orthonormalise in Gram-Schmidt order.  Components outside the leading
 //     k-space shrink by lambda_{k+1}/lambda_j.  The Ritz block of the float32
 //     subspace iteration needs this step too: its float32 products leave
 //     about 1e-6 of each direction outside the subspace, which adds up over
@@ -921,6 +928,7 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   double* Wt = (double*)ar.take(sizeof(double) * k * k);
   double* T = (double*)ar.take(sizeof(double) * k * k);
   double* T2 = (double*)ar.take(sizeof(double) * k * k);
+  float* Tf = (float*)ar.take(sizeof(float) * k * k);
   double* norms = (double*)ar.take(sizeof(double) * (k + 8));
   int* order = (int*)ar.take(sizeof(int) * k);
   double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
@@ -935,9 +943,26 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
     ATK_LAUNCHED();
     normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, 1e-5, Qb);
     ATK_LAUNCHED();
+    // Orthonormalise in Gram-Schmidt order (column j against the columns
+    // before it; Qb is sorted by descending Ritz value).  The subspace step
+    // multiplies the float32 leakage of a trailing, small-eigenvalue column
+    // into the leading subspace by lambda_1 / lambda_j (overlaps up to about
+    // 0.1); a symmetric orthonormalisation (the polar factor) would rotate
+    // that leakage back into the leading columns, Gram-Schmidt order leaves
+    // their span alone.  One CholeskyQR pass with a float32 factor (robust for
+    // any such overlap) takes the columns to float32 orthogonality, then two
+    // Gram-Schmidt-ordered quadratic steps to float64 level.
+    ATK_TRY(gemm_tn_f64(Qb, Qb, n, k, B, pol, st));
+    cholinv_f32_kernel<<<1, CHOL_THREADS, cholinv_smem((int)k), st>>>(B, (int)k, 0.f, Tf, nullptr);
+    ATK_LAUNCHED();
+    ATK_TRY(f32_to_f64(Tf, T, k * k, st));
+    ATK_TRY(gemm_f64_split(Qb, T, n, k, k, Z, gpart, gcap, st));
+    ATK_CUDA(cudaMemcpyAsync(Qb, Z, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
+    for (int it = 0; it < 2; ++it) ATK_TRY(gs_step_f64(Qb, n, k, pol, st));
+  } else {
+    ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
+    ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
   }
-  ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
-  ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
   // 2. Rayleigh-Ritz and simultaneous rotations
   ATK_TRY(gemm_f64_split(S, Qb, n, n, k, Z, gpart, gcap, st));
   ATK_TRY(gemm_tn_f64(Qb, Z, n, k, B, pol, st));
@@ -1069,6 +1094,7 @@ int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int ma
   }
   // The refinement and the float32 copy of U: no host synchronisation inside,
   // so one cached graph per (buffers, sizes).
+  if (k <= 156) ATK_TRY(raise_smem_limit((const void*)cholinv_f32_kernel, cholinv_smem((int)k)));
   const GraphKey key{{S, Qb, U64_out, lambda_out, discarded_out, U_out, rest, nullptr},
                      {n, k, R, (int64_t)rest_bytes}};
   return run_graph(key, st, [&](cudaStream_t s2) -> int {

@@ -266,6 +266,19 @@ __global__ void polar_coef_kernel(const double* __restrict__ G, int64_t R, doubl
   M[o] = ((o % R == o / R) ? 1.5 : 0.0) - 0.5 * G[o];
 }
 
+// Gram-Schmidt-ordered counterpart of the polar coefficient: with
+// G = U^T U = I + E, T = I - strict_upper(E) - diag(E) / 2 (upper triangular).
+// U T has column i built from columns j <= i only, and (U T)^T (U T) =
+// I + O(E^2): one step of an iteration that converges quadratically like
+// Newton-Schulz but, like Gram-Schmidt, never mixes a later column into an
+// earlier one.
+__global__ void gs_coef_kernel(const double* __restrict__ G, int64_t R, double* __restrict__ M) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= R * R) return;
+  const int64_t i = o % R, j = o / R;
+  M[o] = i == j ? 1.0 - 0.5 * (G[o] - 1.0) : (i < j ? -G[o] : 0.0);
+}
+
 // Rhat = C2^T C1^T (both factors lower), i.e. the product of the two upper factors.
 __global__ void rhat_kernel(const double* __restrict__ C1, const double* __restrict__ C2, int64_t R,
                             double* __restrict__ Rhat) {
@@ -311,6 +324,17 @@ int polar_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_
   if (!b.panel) { set_error("polar: scratch too small"); return ATK_EINVAL; }
   ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, b.part, st));
   polar_coef_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M1, R, b.M2);
+  ATK_LAUNCHED();
+  ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, b.part, part_cap(n, R), st)));
+  ATK_CUDA(cudaMemcpyAsync(U, b.panel, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
+  return ATK_OK;
+}
+
+int gs_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_t st) {
+  SmallBufs b = carve(scratch, n, R);
+  if (!b.panel) { set_error("gs_step: scratch too small"); return ATK_EINVAL; }
+  ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, b.part, st));
+  gs_coef_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M1, R, b.M2);
   ATK_LAUNCHED();
   ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, b.part, part_cap(n, R), st)));
   ATK_CUDA(cudaMemcpyAsync(U, b.panel, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
