@@ -468,8 +468,8 @@ int run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
 // n x m block:
 //  1. one power step from a random block, Q <- orth(S Q), orthonormalised by
 //     shifted CholeskyQR3;
-//  2. a Rayleigh-Ritz projection B = Q^T S Q diagonalised by the same
-//     one-CTA parallel-order Jacobi as above, giving Ritz vectors Q W;
+//  2. a Rayleigh-Ritz projection B = Q^T S Q diagonalised by the one-CTA
+//     tridiagonal eigensolver (tridiag_eig.cu), giving Ritz vectors Q W;
 //  3. further steps restarting from the Ritz vectors (S Q W = Z W is
 //     already at hand, two CholeskyQR passes suffice) until the predicted
 //     error after the float64 refinement,
@@ -499,6 +499,34 @@ __global__ void rand_fill_kernel(float* __restrict__ Q, int64_t count, uint64_t 
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   z ^= z >> 31;
   Q[i] = (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+}
+
+// Y += sigma X with sigma = rel * max_i S_ii (S n x n float32, every CTA
+// finds the maximum itself): the power steps use S + sigma I, which has the
+// same eigenvectors as S.  For an S of rank below the block width m (a mode
+// whose rank equals the product of the other ranks, or an exactly low-rank
+// tensor) S Q spans only rank(S) directions and the unshifted CholeskyQR
+// passes would break down; the shift keeps the block at full rank, the
+// surplus columns becoming null-space directions.  The Rayleigh-Ritz
+// projection and the residuals use S itself.
+constexpr float RR_POWER_SHIFT = 1e-5f;
+__global__ void shift_axpy_kernel(float* __restrict__ Y, const float* __restrict__ X, const float* __restrict__ S,
+                                  int64_t n, int64_t count, float rel) {
+  __shared__ float red[32];
+  float mx = 0.f;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, S[i * (n + 1)]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float sigma = rel * red[0];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) Y[i] = fmaf(sigma, X[i], Y[i]);
 }
 
 // Normalise each column of Y (n x m) to unit length; one warp per column.
@@ -752,6 +780,9 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
                                                                           0x5EEDULL + (uint64_t)n);
     ATK_LAUNCHED();
     ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Y, b, s2));  // Y = S Q
+    shift_axpy_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, s2>>>(b.Y, b.Q, b.Sf, n, (int64_t)nm,
+                                                                          RR_POWER_SHIFT);  // Y = (S + sigma I) Q
+    ATK_LAUNCHED();
     return cholqr3_f32(b.Y, b.T, b.Q, n, m, b, s2);
   }));
   const GraphKey kit{{scratch, dev_status, nullptr, nullptr, nullptr, nullptr, nullptr, (const void*)2},
@@ -792,6 +823,10 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
     // Next step from the Ritz vectors: S (Q W) = Z W is in T; its columns are
     // nearly orthogonal, so two plain CholeskyQR passes orthonormalise it.
     ATK_TRY(run_graph(knext, st, [&](cudaStream_t s2) -> int {
+      // T = S Q W is in T and Q W in Y: T <- (S + sigma I) Q W.
+      shift_axpy_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, s2>>>(b.T, b.Y, b.Sf, n, (int64_t)nm,
+                                                                            RR_POWER_SHIFT);
+      ATK_LAUNCHED();
       ATK_TRY(cholqr_pass_f32(b.T, b.Y, n, m, 0.f, b, s2));
       return cholqr_pass_f32(b.Y, b.Q, n, m, 0.f, b, s2);
     }));
@@ -801,9 +836,10 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
 
 // ----------------------------------------------------- float64 refinement
 __global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n,
-                                      int64_t R, const double* __restrict__ norms, double rel,
-                                      double* __restrict__ W);
-__global__ void colnorms_f64_kernel(const double* __restrict__ Z, int64_t n, int64_t R, double* __restrict__ norms);
+                                      int64_t R, const double* __restrict__ norms, const double* __restrict__ dots,
+                                      double rel, double min_ratio, double* __restrict__ W);
+__global__ void colnorms_f64_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n, int64_t R,
+                                    double* __restrict__ norms, double* __restrict__ dots);
 __global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R);
 
 // W = I + X for the k x k symmetric float64 matrix B: for every pair p < q,
@@ -898,7 +934,7 @@ constexpr int REFINE_ROTATION_STEPS = 2;
 constexpr int64_t REFINE_PART_EXTRA = 512 * 1024;
 
 size_t refine_bytes(int64_t n, int64_t k) {
-  return sizeof(double) * (size_t)(2 * n * k + 6 * k * k + k + 8 + n * k + REFINE_PART_EXTRA) + sizeof(int) * (size_t)k +
+  return sizeof(double) * (size_t)(2 * n * k + 6 * k * k + 2 * k + 8 + n * k + REFINE_PART_EXTRA) + sizeof(int) * (size_t)k +
          smallla_scratch_bytes(std::max(n, k), k) + 4096;
 }
 
@@ -929,7 +965,7 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   double* T = (double*)ar.take(sizeof(double) * k * k);
   double* T2 = (double*)ar.take(sizeof(double) * k * k);
   float* Tf = (float*)ar.take(sizeof(float) * k * k);
-  double* norms = (double*)ar.take(sizeof(double) * (k + 8));
+  double* norms = (double*)ar.take(sizeof(double) * (2 * k + 8));
   int* order = (int*)ar.take(sizeof(int) * k);
   double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
   const int64_t gcap = n * k + REFINE_PART_EXTRA;
@@ -939,9 +975,10 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   // 1. subspace step (subspace_step = false only orthonormalises Qb)
   if (subspace_step) {
     ATK_TRY(gemm_f64_split(S, Qb, n, n, k, Z, gpart, gcap, st));
-    colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, n, k, norms);
+    colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
     ATK_LAUNCHED();
-    normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, 1e-5, Qb);
+    normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k, 1e-5, 0.9,
+                                                                          Qb);
     ATK_LAUNCHED();
     // Orthonormalise in Gram-Schmidt order (column j against the columns
     // before it; Qb is sorted by descending Ritz value).  The subspace step
@@ -1001,23 +1038,41 @@ size_t eig_scratch_bytes(int64_t n, int arith) {
 }
 
 // norms[r] = ||Z[:, r]||; one warp per column.
-__global__ void colnorms_f64_kernel(const double* __restrict__ Z, int64_t n, int64_t R, double* __restrict__ norms) {
+// norms[r] = ||Z[:, r]|| and, when U is given, dots[r] = U[:, r]^T Z[:, r].
+// One warp per column.
+__global__ void colnorms_f64_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n, int64_t R,
+                                    double* __restrict__ norms, double* __restrict__ dots) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   if (warp >= R) return;
   const double* z = Z + (int64_t)warp * n;
-  double s = 0.0;
-  for (int64_t i = lane; i < n; i += 32) s += z[i] * z[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) norms[warp] = sqrt(s);
+  const double* u = U ? U + (int64_t)warp * n : nullptr;
+  double s = 0.0, d = 0.0;
+  for (int64_t i = lane; i < n; i += 32) {
+    s += z[i] * z[i];
+    if (u) d += u[i] * z[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+  }
+  if (lane == 0) {
+    norms[warp] = sqrt(s);
+    if (dots) dots[warp] = d;
+  }
 }
 
-// W[:, r] = Z[:, r] / ||Z[:, r]|| when that norm is above rel * max_r ||Z[:, r]||,
-// else U[:, r].  A column whose image under S is at rounding level lies in the
-// numerical null space.  Normalising S u would turn rounding noise into a copy
-// of a leading direction, so such a column keeps its vector.  One warp per column.
+// W[:, r] = Z[:, r] / ||Z[:, r]|| when that norm is above rel * max_r ||Z[:, r]||
+// and (dots given) the Rayleigh quotient U[:, r]^T Z[:, r] is at least
+// min_ratio ||Z[:, r]||, else U[:, r].  Z = S U.  A column whose image is at
+// rounding level lies in the numerical null space, and a column whose image is
+// mostly leakage into other eigendirections (||S u|| well above u^T S u: a
+// null-space or small-eigenvalue Ritz vector with float32 errors along the
+// leading directions) is not improved by S u; normalising would turn that
+// leakage into a near copy of a leading direction.  Such columns keep their
+// vectors.  One warp per column.
 __global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n,
-                                      int64_t R, const double* __restrict__ norms, double rel,
-                                      double* __restrict__ W) {
+                                      int64_t R, const double* __restrict__ norms, const double* __restrict__ dots,
+                                      double rel, double min_ratio, double* __restrict__ W) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   if (warp >= R) return;
   double mx = 0.0;
@@ -1026,7 +1081,7 @@ __global__ void normalize_cols_kernel(const double* __restrict__ Z, const double
   const double* z = Z + (int64_t)warp * n;
   double nz = norms[warp];
   double* w = W + (int64_t)warp * n;
-  if (nz > thr) {
+  if (nz > thr && (!dots || dots[warp] >= min_ratio * nz)) {
     for (int64_t i = lane; i < n; i += 32) w[i] = z[i] / nz;
   } else {
     const double* u = U + (int64_t)warp * n;
