@@ -857,7 +857,12 @@ int ttm_f32(const float* y, const View& v, const float* U, int64_t R, float* out
   } else if (bn == 128) ttm_co_kernel<128, 128, 8, 8><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
   else if (bn == 64) ttm_co_kernel<128, 64, 8, 4><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
   else if (bn == 32) ttm_co_kernel<128, 32, 8, 2><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
-  else ttm_co_kernel<128, 16, 8, 1><<<grid, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
+  else {
+    // R <= 16: 256 rows of c by 16 columns, 8 x 2 per thread, so each shared
+    // load feeds twice the FMAs of a 128 x 16 tile (which was load-bound).
+    dim3 g256((unsigned)ceil_div(J, 256), (unsigned)ceil_div(R, 16));
+    ttm_co_kernel<256, 16, 8, 2><<<g256, NT, 0, st>>>(y, v.lo, v.n, v.hi, U, R, out);
+  }
   ATK_LAUNCHED();
   return ATK_OK;
 }
