@@ -179,6 +179,40 @@ def test_eig_subspace_clustered_kept_eigenvalues(atk, n, R, lam_rtol, disc_rel):
     np.testing.assert_allclose(np.sort(lamg.cpu().numpy()[:R])[::-1], top, rtol=lam_rtol)
 
 
+@pytest.mark.parametrize("n,R", [(712, 32), (400, 40), (887, 66)])
+def test_eig_subspace_rank_equal_to_r(atk, n, R):
+    """S = Y Y^T with Y n x R: rank exactly R, below the subspace block width
+    m = R + p.  (This is the Gram of a mode whose rank equals the product of
+    the other ranks.)  The shifted power steps keep the block at full rank, so
+    the subspace path resolves it instead of breaking down (it used to fall
+    back to the full Jacobi, 60x slower); the kept subspace is range(Y)."""
+    g = np.random.default_rng(0)
+    Y = g.standard_normal((n, R)).astype(np.float32).astype(np.float64)
+    S = Y @ Y.T
+    U, lamg, disc = atk.eig(_cuda(S), R, method=2)
+    U = U.cpu().double().numpy()
+    Qy = np.linalg.qr(Y)[0]
+    assert np.linalg.norm(U.T @ U - np.eye(R)) <= 1e-6
+    assert oracle.projector_distance(U, Qy) <= 1e-4
+    ref = np.sort(np.linalg.eigvalsh(Y.T @ Y))[::-1]
+    np.testing.assert_allclose(lamg.cpu().numpy()[:R], ref, rtol=1e-7)
+    assert abs(disc.item()) <= 1e-9 * ref[0] * n
+
+
+def test_sthosvd_mode_rank_equal_to_product_of_others(atk):
+    """A plan whose last mode's rank is the product of the other ranks (its
+    Gram has rank exactly R_n): matches the oracle.  The last mode's kept
+    space is range(S), whose smallest eigenvalue is far below the largest
+    (lambda_R / lambda_1 about 1e-3 for a random core), so the float32 Gram
+    resolves it to about eps_32 lambda_1 / lambda_R: its projector bound is
+    1e-3 instead of the 1e-4 of well-separated spectra."""
+    dims, ranks = [40, 30, 120], [6, 5, 30]
+    core, facs, disc, ref, rel_g, rel_o = _e2e(atk, dims, ranks, [0, 0, 0], seed=5)
+    assert abs(rel_g - rel_o) <= 1e-5
+    for k, (U, Uo) in enumerate(zip(facs, ref["factors"])):
+        assert oracle.projector_distance(U, Uo) <= (1e-3 if k == 2 else 1e-4)
+
+
 @pytest.mark.parametrize("lo,n,hi,R", [(1, 40, 300, 5), (6, 24, 50, 8), (64, 30, 1, 6)])
 def test_als_mode_matches_oracle(atk, lo, n, hi, R):
     dims = [lo, n, hi]
