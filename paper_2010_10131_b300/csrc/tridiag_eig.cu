@@ -1,45 +1,70 @@
 // Eigen-decomposition of a small dense symmetric matrix on one CTA, float32:
 // the Rayleigh-Ritz projections of the subspace eigensolver (m = R + p <= 156)
-// need all their eigenpairs, and a one-CTA Jacobi spends about 80 rounds x
-// 10 sweeps of two barriers each on them.  Here the matrix is reduced to
-// tridiagonal form and the tridiagonal problem is solved by methods whose
-// steps are independent across eigenpairs:
+// need all their eigenpairs.  The matrix is reduced to tridiagonal form and
+// the tridiagonal problem is solved by methods whose steps are independent
+// across eigenpairs:
 //  1. Householder reduction A = Q T Q^T (Golub & Van Loan, Matrix
 //     Computations, 4th ed., Alg. 8.3.1): step j reflects column j below the
-//     diagonal with H_j = I - tau_j v_j v_j^T (v_j(0) = 1), p = tau A22 v,
-//     w = p - (tau/2)(p^T v) v, A22 <- A22 - v w^T - w v^T.  Two barriers per
-//     step: every thread derives the reflector of step j from the column's
-//     first entry and the sixteen per-warp partial sums of its squared norm,
-//     which the warps accumulate while they update that column in step j-1
-//     (summed in warp order, so the result is deterministic).  Column j keeps
-//     the unscaled x; v = x * scale_j below its leading 1.
+//     diagonal with H_j = I - tau_j v_j v_j^T (v_j(j+1) = 1), p = tau A22 v,
+//     w = p - (tau/2)(p^T v) v, A22 <- A22 - v w^T - w v^T.  A lives in
+//     registers for the whole reduction: warp w holds the rows i = w (mod 16),
+//     lane l the columns k = l (mod 32), so p is a register product plus a
+//     butterfly sum over the warp, and the update touches no shared memory.
+//     Two barriers per step: one after p and the per-warp partials of p^T v,
+//     one after the owners of column j+1 have published it (and the partial
+//     sums of its squared norm below row j+2, from which every thread derives
+//     the next reflector).
 //  2. Eigenvalues of T by multisection on the Sturm count (ibid., Sec. 8.4.1):
-//     G lanes per eigenvalue (G = 8, 4 or 2 as n allows) test G points of the
-//     bracket at once, down to an absolute width of 4 eps ||T||_1.
+//     one Sturm count per thread on a grid of 512 points across the
+//     Gershgorin interval brackets every eigenvalue to 1/513 of it; then G
+//     lanes per eigenvalue test 2G points of its bracket per step (two
+//     interleaved counts per lane), down to an absolute width of 4 eps ||T||_1.
 //  3. Eigenvectors of T by inverse iteration (ibid., Sec. 8.2.2), thread t
 //     for eigenvalue t: Gaussian elimination of T - lambda_t I without
 //     interchanges, pivots kept away from zero (the classical guard of
 //     tridiagonal inverse iteration), then two solves from a pseudo-random
-//     start with the same factors; within each cluster of eigenvalues closer
-//     than 1e-3 ||T||_1, modified Gram-Schmidt, so that near-equal
-//     eigenvalues get an orthonormal basis of their eigenspace.
-//  4. Back-transformation X <- H_0 H_1 ... H_{m-3} X, two barriers per
-//     reflector (the projections v^T X, then the rank-1 update).
+//     start with the same factors.  Within each cluster of
+//     eigenvalues closer than 1e-3 ||T||_1 the vectors are orthonormalised in
+//     eigenvalue order by classical Gram-Schmidt applied twice (one warp per
+//     cluster), so that near-equal eigenvalues get an orthonormal basis of
+//     their eigenspace.
+//  4. Back-transformation X <- H_0 H_1 ... H_{m-3} X: each warp holds eight
+//     eigenvectors in registers and applies the reflectors four at a time
+//     (their mutual inner products computed once), with register sums and
+//     two shuffles per projection and no barrier.
 // The eigenvectors are as accurate as float32 allows (about eps ||T|| / gap);
 // the float64 refinement that follows the subspace eigensolver polishes them.
+#include <algorithm>
+
 #include "atk_internal.cuh"
 
 namespace atk {
 
 constexpr int TE_THREADS = 512;
 constexpr int TE_WARPS = TE_THREADS / 32;
-constexpr int TE_NMAX = 160;     // largest matrix (the subspace eigensolver uses m <= 156)
-constexpr int TE_KREG = 5;       // columns per lane held in registers in the update (32 * 5 >= TE_NMAX)
-constexpr int TE_MAXSECT = 40;   // multisection steps (a cap; the width test ends them sooner)
+constexpr int TE_NMAX = 160;      // largest matrix (the subspace eigensolver uses m <= 156)
+constexpr int TE_GRID = TE_THREADS;  // points of the first multisection step
+constexpr int TE_MAXSECT = 40;    // multisection steps (a cap; the width test ends them sooner)
+constexpr unsigned TE_FULL = 0xffffffffu;
 
+// Shared memory: the per-warp partial sums and the grid counts, two vectors
+// of length TE_NMAX, the reflectors (row j = v_j, n x ldv with ldv = n
+// rounded up to 16), the eigenvector block X (n x (n+1)) and six vectors of
+// length n.
 size_t tridiag_eig_smem(int n) {
-  const int ld = n + 1;
-  return sizeof(float) * ((size_t)2 * n * ld + 8 * (size_t)n + 3 * TE_WARPS + 8);
+  const size_t ld = (size_t)n + 1, ldv = 16 * (((size_t)n + 15) / 16);
+  return sizeof(float) * (2 * TE_WARPS + 8 + TE_GRID + 2 * TE_NMAX + (size_t)n * ldv + n * ld + 6 * (size_t)n);
+}
+
+// Sum of v over the 32 lanes of the warp by an xor butterfly: lanes l and
+// l ^ o add the same two operands at every stage (addition commutes
+// exactly), so every lane ends with the same bits.
+template <int K>
+__device__ __forceinline__ void te_warp_sum(float (&v)[K]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(TE_FULL, v[k], o);
 }
 
 // Sturm count: the number of eigenvalues of T (diagonal d, squared
@@ -48,12 +73,34 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
   float q = d[0] - x;
   if (fabsf(q) < pivmin) q = -pivmin;
   int c = q < 0.f;
+#pragma unroll 4
   for (int i = 1; i < n; ++i) {
     q = d[i] - x - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     c += q < 0.f;
   }
   return c;
+}
+
+// The same recurrence at two points at once (two independent chains).
+__device__ __forceinline__ void sturm_count2(const float* d, const float* e2, int n, float x0, float x1,
+                                             float pivmin, int& c0, int& c1) {
+  float q0 = d[0] - x0, q1 = d[0] - x1;
+  if (fabsf(q0) < pivmin) q0 = -pivmin;
+  if (fabsf(q1) < pivmin) q1 = -pivmin;
+  int k0 = q0 < 0.f, k1 = q1 < 0.f;
+#pragma unroll 4
+  for (int i = 1; i < n; ++i) {
+    const float di = d[i], ei = e2[i - 1];
+    q0 = di - x0 - __fdividef(ei, q0);
+    q1 = di - x1 - __fdividef(ei, q1);
+    if (fabsf(q0) < pivmin) q0 = -pivmin;
+    if (fabsf(q1) < pivmin) q1 = -pivmin;
+    k0 += q0 < 0.f;
+    k1 += q1 < 0.f;
+  }
+  c0 = k0;
+  c1 = k1;
 }
 
 __device__ __forceinline__ float te_rand(uint32_t a, uint32_t b) {
@@ -64,154 +111,174 @@ __device__ __forceinline__ float te_rand(uint32_t a, uint32_t b) {
   return (float)(h & 0xFFFFFF) * (2.f / 16777216.f) - 1.f;
 }
 
-// S: n x n float64 (symmetric).  diag_out (n): eigenvalues, ascending.
-// V_out (n x n, row-major, column j = eigenvector of diag_out[j]).
-__global__ void __launch_bounds__(TE_THREADS) tridiag_eig_kernel(const double* __restrict__ S, int n,
-                                                                  float* __restrict__ diag_out,
-                                                                  float* __restrict__ V_out) {
+// Sum of the first K (a multiple of 4) per-warp partials, in a fixed order
+// (the same bits in every thread).
+template <int K>
+__device__ __forceinline__ float te_sum(const float* p) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < K / 4; ++q) {
+    const float4 v = p4[q];
+    s += v.x;
+    s += v.y;
+    s += v.z;
+    s += v.w;
+  }
+  return s;
+}
+
+// S: n x n float64 (symmetric), n <= 16 NT.  diag_out (n): eigenvalues,
+// ascending.  V_out (n x n, row-major, column j = eigenvector of diag_out[j]).
+template <int NT>
+__global__ void __launch_bounds__(TE_THREADS, 1) tridiag_eig_kernel(const double* __restrict__ S, int n,
+                                                                     float* __restrict__ diag_out,
+                                                                     float* __restrict__ V_out) {
+  // Reduction layout: WH warps; in warp w, lane (rs = lane / 16, cg = lane %
+  // 16) holds A(i, k) for the rows i = w + WH (rs + 2 s), s < NS, and the
+  // columns k = cg + 16 t, t < NT.  The other phases work on NB = ceil(n/32)
+  // chunks of 32 rows.
+  constexpr int WH = NT <= 6 ? 8 : 16;
+  constexpr int NS = (8 * NT + WH - 1) / WH;
+  constexpr int NB = (NT + 1) / 2;
   extern __shared__ __align__(16) float tsm[];
   const int ld = n + 1;
-  float* A = tsm;             // n x ld, row-major; column j keeps x_j below the diagonal
-  float* X = A + n * ld;      // n x ld, row-major; column t = eigenvector t
-  float* d = X + n * ld;      // diagonal of T
-  float* e = d + n;           // off-diagonal of T: e[j] = T(j+1, j)
-  float* e2 = e + n;          // e^2
-  float* tau = e2 + n;        // reflector scalars
-  float* scl = tau + n;       // v_j(i) = x_j(i) * scl[j] for i >= j+2
-  float* p = scl + n;         // work vector
-  float* lam = p + n;         // eigenvalues, ascending
-  float* part = lam + n;      // [2][TE_WARPS] partial squared norms of the next column
-  float* kpart = part + 2 * TE_WARPS;  // [TE_WARPS] partial sums of p^T v
-  __shared__ float red[4];
+  const int ldv = 16 * ((n + 15) / 16);
+  float* part = tsm;                  // [TE_WARPS] partial squared norms of the next column
+  float* kpart = part + TE_WARPS;     // [TE_WARPS] partial sums of p^T v
+  float* red = kpart + TE_WARPS;      // [8] interval ends and norm
+  int* cnt = reinterpret_cast<int*>(red + 8);  // [TE_GRID] Sturm counts of the grid
+  float* xb = reinterpret_cast<float*>(cnt + TE_GRID);  // [TE_NMAX] column j+1, zero above row j+2
+  float* pb = xb + TE_NMAX;           // [TE_NMAX] p, zero outside the trailing block
+  float* Vr = pb + TE_NMAX;           // n x ldv: row j = v_j, zero beyond n
+  float* X = Vr + n * ldv;            // n x ld, row-major; column t = eigenvector t
+  float* d = X + n * ld;              // diagonal of T
+  float* e = d + n;                   // off-diagonal of T: e[j] = T(j+1, j)
+  float* e2 = e + n;                  // e^2
+  float* tau = e2 + n;                // reflector scalars
+  float* lam = tau + n;               // eigenvalues, ascending
+  float* flag = lam + n;              // cluster starts
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
-  for (int idx = tid; idx < n * n; idx += TE_THREADS) A[(idx / n) * ld + idx % n] = (float)S[idx];
-  __syncthreads();
-  // Partial norms of column 0 below its first subdiagonal entry.
-  {
-    float sg = 0.f;
-    for (int i = 2 + tid; i < n; i += TE_THREADS) sg = fmaf(A[i * ld], A[i * ld], sg);
-    for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
-    if (lane == 0) part[warp] = sg;
-  }
-  __syncthreads();
+  const int rs = lane / 16, cg = lane % 16;
+  const bool hw = warp < WH;          // this warp takes part in the reduction
 
-  // 1. Householder reduction to tridiagonal form.
-  for (int j = 0; j + 2 < n; ++j) {
-    const float* pj = part + (j & 1) * TE_WARPS;
-    float sig = 0.f;
+  // 1. Householder reduction.
+  float a[NS][NT];
 #pragma unroll
-    for (int w = 0; w < TE_WARPS; ++w) sig += pj[w];
-    const float alpha = A[(j + 1) * ld + j];
-    float t = 0.f, beta = alpha, scale = 0.f;
-    if (sig > 0.f) {
-      const float mu = sqrtf(fmaf(alpha, alpha, sig));
-      beta = alpha <= 0.f ? mu : -mu;
-      t = __fdividef(beta - alpha, beta);
-      scale = __fdividef(1.f, alpha - beta);
-    }
-    if (tid == 0) {
-      e[j] = beta;
-      tau[j] = t;
-      scl[j] = scale;
-    }
-    float* pn = part + ((j + 1) & 1) * TE_WARPS;
-    if (t == 0.f) {
-      // Column j is already reduced: carry the next column's norm forward.
-      float sg = 0.f;
-      for (int i = j + 3 + tid; i < n; i += TE_THREADS) sg = fmaf(A[i * ld + j + 1], A[i * ld + j + 1], sg);
-      for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
-      if (lane == 0) pn[warp] = sg;
-      __syncthreads();
-      continue;
-    }
-    // p = tau A22 v, four lanes per row; each warp also sums its p_i v_i.
-    {
-      float pv = 0.f;
-      const int sub = tid % 4;
-      const unsigned gmask = 0xFu << (lane & ~3);
-      for (int i = j + 1 + tid / 4; i < n; i += TE_THREADS / 4) {
-        // v(j+1) = 1; the entries k >= j+2 hold the unscaled x, so their sum
-        // is scaled once at the end.
-        float s0 = 0.f, s1 = 0.f, lead = 0.f;
-        int k = j + 1 + sub;
-        if (sub == 0) {
-          lead = A[i * ld + k];
-          k += 4;
-        }
-#pragma unroll 4
-        for (; k + 4 < n; k += 8) {
-          s0 = fmaf(A[i * ld + k], A[k * ld + j], s0);
-          s1 = fmaf(A[i * ld + k + 4], A[(k + 4) * ld + j], s1);
-        }
-        if (k < n) s1 = fmaf(A[i * ld + k], A[k * ld + j], s1);
-        float s = fmaf(scale, s0 + s1, lead);
-        s += __shfl_xor_sync(gmask, s, 1);
-        s += __shfl_xor_sync(gmask, s, 2);
-        if (sub == 0) {
-          p[i] = t * s;
-          pv = fmaf(t * s, i == j + 1 ? 1.f : A[i * ld + j] * scale, pv);
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
-      if (lane == 0) kpart[warp] = pv;
-    }
-    __syncthreads();
-    // K = (tau/2) p^T v from the per-warp partials (warp order); then
-    // A22 -= v w^T + w v^T with w = p - K v, lane-owned columns held in
-    // registers; the warps add up the squared norm of the updated column j+1
-    // below row j+2.
-    float kk = 0.f;
+  for (int s = 0; s < NS; ++s)
 #pragma unroll
-    for (int w = 0; w < TE_WARPS; ++w) kk += kpart[w];
-    kk *= 0.5f * t;
-    float vk[TE_KREG], wk[TE_KREG];
-#pragma unroll
-    for (int q = 0; q < TE_KREG; ++q) {
-      const int k = j + 1 + lane + 32 * q;
-      const float v = k < n ? (k == j + 1 ? 1.f : A[k * ld + j] * scale) : 0.f;
-      vk[q] = v;
-      wk[q] = k < n ? fmaf(-kk, v, p[k]) : 0.f;
+    for (int t = 0; t < NT; ++t) {
+      const int i = warp + WH * (rs + 2 * s), k = cg + 16 * t;
+      a[s][t] = (hw && i < n && k < n) ? (float)S[(size_t)i * n + k] : 0.f;
     }
+  // Publish column c of the partly reduced A below row c (zero above it,
+  // and zero beyond n) and this warp's partial squared norm below row c+1.
+  // Column c sits in slot c / 16 of the lanes with cg = c % 16.
+  auto publish = [&](int c) {
     float sg = 0.f;
-    // Two rows per pass: all ten loads are issued before any store.
-    for (int i0 = j + 1 + warp; i0 < n; i0 += 2 * TE_WARPS) {
-      const int i1 = i0 + TE_WARPS;
-      const bool has1 = i1 < n;
-      const float vi0 = i0 == j + 1 ? 1.f : A[i0 * ld + j] * scale;
-      const float wi0 = fmaf(-kk, vi0, p[i0]);
-      const float vi1 = has1 ? A[i1 * ld + j] * scale : 0.f;
-      const float wi1 = has1 ? fmaf(-kk, vi1, p[i1]) : 0.f;
-      float a0[TE_KREG], a1[TE_KREG];
+    if (cg == c % 16) {
+      const int tc = c / 16;
 #pragma unroll
-      for (int q = 0; q < TE_KREG; ++q) {
-        const int k = j + 1 + lane + 32 * q;
-        a0[q] = k < n ? A[i0 * ld + k] : 0.f;
-        a1[q] = (k < n && has1) ? A[i1 * ld + k] : 0.f;
-      }
+      for (int s = 0; s < NS; ++s) {
+        float v = a[s][0];
 #pragma unroll
-      for (int q = 0; q < TE_KREG; ++q) {
-        const int k = j + 1 + lane + 32 * q;
-        if (k < n) {
-          const float v0 = fmaf(-vi0, wk[q], fmaf(-wi0, vk[q], a0[q]));
-          A[i0 * ld + k] = v0;
-          if (q == 0 && lane == 0 && i0 >= j + 3) sg = fmaf(v0, v0, sg);
-          if (has1) {
-            const float v1 = fmaf(-vi1, wk[q], fmaf(-wi1, vk[q], a1[q]));
-            A[i1 * ld + k] = v1;
-            if (q == 0 && lane == 0 && i1 >= j + 3) sg = fmaf(v1, v1, sg);
-          }
-        }
+        for (int t = 1; t < NT; ++t) v = t == tc ? a[s][t] : v;  // selects keep a[][] in registers
+        const int i = warp + WH * (rs + 2 * s);
+        xb[i] = i > c ? v : 0.f;
+        if (i > c + 1) sg = fmaf(v, v, sg);
       }
     }
-    if (lane == 0) pn[warp] = sg;
+    sg += __shfl_xor_sync(TE_FULL, sg, 16);
+    if (lane == c % 16) part[warp] = sg;
+  };
+  if (hw) publish(0);
+  __syncthreads();
+  for (int j = 0; j + 2 < n; ++j) {
+    float t = 0.f, vk[NT], vi[NS], p[NS];
+    if (hw) {
+      const float sig = te_sum<WH>(part);
+      const float alpha = xb[j + 1];
+      float beta = alpha, scale = 0.f;
+      if (sig > 0.f) {
+        const float mu = sqrtf(fmaf(alpha, alpha, sig));
+        beta = alpha <= 0.f ? mu : -mu;
+        t = __fdividef(beta - alpha, beta);
+        scale = __fdividef(1.f, alpha - beta);
+      }
+      if (tid == 0) {
+        e[j] = beta;
+        tau[j] = t;
+      }
+      // v_j(r) = 1 at r = j+1, x(r) * scale below, 0 elsewhere (xb is zero
+      // at r <= j and beyond n).
+      auto vval = [&](int r) -> float { return r == j + 1 ? 1.f : xb[r] * scale; };
+      if (tid < ldv) Vr[j * ldv + tid] = t != 0.f ? vval(tid) : 0.f;
+      if (t != 0.f) {  // uniform: every thread has the same sig
+#pragma unroll
+        for (int u = 0; u < NT; ++u) vk[u] = vval(cg + 16 * u);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) vi[s] = vval(warp + WH * (rs + 2 * s));
+        // p = tau A v: register products, then a butterfly over the 16 lanes
+        // of the row group (columns <= j carry v = 0 and are skipped).
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          float acc = 0.f;
+#pragma unroll
+          for (int u = 0; u < NT; ++u)
+            if (16 * u + 15 > j) acc = fmaf(a[s][u], vk[u], acc);
+          p[s] = acc;
+        }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1)
+#pragma unroll
+          for (int s = 0; s < NS; ++s) p[s] += __shfl_xor_sync(TE_FULL, p[s], o);
+        // Rows <= j are outside the trailing block (their entries are stale).
+        float pv = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          const int i = warp + WH * (rs + 2 * s);
+          p[s] = i > j ? t * p[s] : 0.f;
+          pv = fmaf(p[s], vi[s], pv);
+          if (cg == s) pb[i] = p[s];
+        }
+        pv += __shfl_xor_sync(TE_FULL, pv, 16);
+        if (lane == 0) kpart[warp] = pv;
+      }
+    }
+    __syncthreads();
+    if (hw) {
+      if (t != 0.f) {
+        // w = p - K v, K = (tau/2) p^T v; A -= v w^T + w v^T.  Outside the
+        // trailing block v, p and w vanish, so the update leaves it unchanged.
+        const float kk = 0.5f * t * te_sum<WH>(kpart);
+        float wk[NT];
+#pragma unroll
+        for (int u = 0; u < NT; ++u) wk[u] = fmaf(-kk, vk[u], pb[cg + 16 * u]);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          const float wi = fmaf(-kk, vi[s], p[s]);
+          if (warp + WH * (2 * s + 1) > j)  // uniform over the warp: some row of slot s is in the block
+#pragma unroll
+            for (int u = 0; u < NT; ++u)
+              if (16 * u + 15 > j) a[s][u] = fmaf(-vi[s], wk[u], fmaf(-wi, vk[u], a[s][u]));
+        }
+      }
+      publish(j + 1);
+    }
     __syncthreads();
   }
-  for (int i = tid; i < n; i += TE_THREADS) d[i] = A[i * ld + i];
-  if (tid == 0 && n >= 2) e[n - 2] = A[(n - 1) * ld + (n - 2)];
-  if (tid == 0 && n >= 2) {
-    tau[n - 2] = 0.f;
-    scl[n - 2] = 0.f;
+  // T: the diagonal and the last off-diagonal entry from the registers.
+  if (hw) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int u = 0; u < NT; ++u) {
+        const int i = warp + WH * (rs + 2 * s), k = cg + 16 * u;
+        if (i < n && k == i) d[i] = a[s][u];
+        if (n >= 2 && i == n - 1 && k == n - 2) e[n - 2] = a[s][u];
+      }
   }
+  if (tid == 0 && n >= 2) tau[n - 2] = 0.f;
   __syncthreads();
   for (int i = tid; i + 1 < n; i += TE_THREADS) e2[i] = e[i] * e[i];
   // Gershgorin interval and the one-norm of T (warp 0).
@@ -224,9 +291,9 @@ __global__ void __launch_bounds__(TE_THREADS) tridiag_eig_kernel(const double* _
       nrm = fmaxf(nrm, fabsf(d[i]) + r);
     }
     for (int o = 16; o > 0; o >>= 1) {
-      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-      nrm = fmaxf(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+      lo = fminf(lo, __shfl_xor_sync(TE_FULL, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(TE_FULL, hi, o));
+      nrm = fmaxf(nrm, __shfl_xor_sync(TE_FULL, nrm, o));
     }
     if (lane == 0) {
       const float pad = 2.f * 1.1920929e-7f * nrm + 1e-30f;
@@ -239,35 +306,52 @@ __global__ void __launch_bounds__(TE_THREADS) tridiag_eig_kernel(const double* _
   const float nrm = red[2];
   const float pivmin = 1e-30f * fmaxf(1.f, nrm * nrm);
 
-  // 2. Multisection: G lanes per eigenvalue split its bracket into G + 1
-  // parts per step (a group never straddles a warp).
+  // 2. Multisection.  Grid point p (0 <= p <= TE_GRID + 1) is lo + hg p, with
+  // count 0 at p = 0 and n at p = TE_GRID + 1 (the padded Gershgorin ends).
+  const float glo = red[0], ghi = red[1];
+  const float hg = (ghi - glo) / (float)(TE_GRID + 1);
+  cnt[tid] = sturm_count(d, e2, n, glo + hg * (float)(tid + 1), pivmin);
+  __syncthreads();
   {
     const int G = n <= TE_THREADS / 8 ? 8 : (n <= TE_THREADS / 4 ? 4 : (n <= TE_THREADS / 2 ? 2 : 1));
     const float width = 4.f * 1.1920929e-7f * nrm + 1e-30f;
     const int g = tid % G;
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane / G * G));
+    const unsigned gmask = G == 32 ? TE_FULL : (((1u << G) - 1u) << (lane / G * G));
     for (int t = tid / G; t < n; t += TE_THREADS / G) {  // the G lanes of a group share t
-      float a = red[0], b = red[1];
-      for (int it = 0; it < TE_MAXSECT; ++it) {
-        const float h = (b - a) / (float)(G + 1);
-        const float x = a + h * (float)(g + 1);
-        const bool above = sturm_count(d, e2, n, x, pivmin) > t;
-        const unsigned bal = __ballot_sync(gmask, above) >> (lane / G * G);
-        // First test point past eigenvalue t: the new bracket ends there.
-        const int f = bal ? __ffs(bal) - 1 : G;
-        const float na = f == 0 ? a : a + h * (float)f;
-        const float nb = f == G ? b : a + h * (float)(f + 1);
-        a = na;
-        b = nb;
-        if (!(b - a > width)) break;
+      // Smallest grid point whose count exceeds t (counts taken as they are).
+      int plo = 0, phi = TE_GRID + 1;
+      while (phi - plo > 1) {
+        const int mid = (plo + phi) / 2;
+        if (cnt[mid - 1] > t) phi = mid; else plo = mid;
       }
-      if (g == 0) lam[t] = 0.5f * (a + b);
+      float a0 = plo == 0 ? glo : glo + hg * (float)plo;
+      float b0 = phi == TE_GRID + 1 ? ghi : glo + hg * (float)phi;
+      for (int it = 0; it < TE_MAXSECT && b0 - a0 > width; ++it) {
+        // Points 1 .. 2G of the bracket; lane g tests 2g+1 and 2g+2.
+        const float h = (b0 - a0) / (float)(2 * G + 1);
+        int c0, c1;
+        sturm_count2(d, e2, n, a0 + h * (float)(2 * g + 1), a0 + h * (float)(2 * g + 2), pivmin, c0, c1);
+        const unsigned sh = lane / G * G;
+        const unsigned any = (__ballot_sync(gmask, c0 > t || c1 > t) >> sh);
+        const unsigned b0s = (__ballot_sync(gmask, c0 > t) >> sh);
+        // First test point past eigenvalue t: the new bracket ends there.
+        int f = 2 * G + 1;
+        if (any) {
+          const int gf = __ffs(any) - 1;
+          f = 2 * gf + ((b0s >> gf) & 1u ? 1 : 2);
+        }
+        const float na = f == 1 ? a0 : a0 + h * (float)(f - 1);
+        const float nb = f == 2 * G + 1 ? b0 : a0 + h * (float)f;
+        a0 = na;
+        b0 = nb;
+      }
+      if (g == 0) lam[t] = 0.5f * (a0 + b0);
     }
   }
   __syncthreads();
 
   // 3. Inverse iteration, thread t for eigenvalue t; the solution goes to
-  // column t of X.  Factors of T - lambda I: reciprocal pivots r_i and
+  // column t of X.  Factors of T - lambda I = L U: reciprocal pivots r_i and
   // multipliers m_i = e_{i-1} r_{i-1}.
   const float guard = 1.1920929e-7f * nrm + 1e-30f;
   for (int t = tid; t < n; t += TE_THREADS) {
@@ -275,13 +359,13 @@ __global__ void __launch_bounds__(TE_THREADS) tridiag_eig_kernel(const double* _
     float r[TE_NMAX], ml[TE_NMAX];
     float qi = d[0] - lm;
     if (fabsf(qi) < guard) qi = qi < 0.f ? -guard : guard;
-    r[0] = 1.f / qi;
+    r[0] = __fdividef(1.f, qi);
     ml[0] = 0.f;
     for (int i = 1; i < n; ++i) {
       const float mlt = e[i - 1] * r[i - 1];
       qi = d[i] - lm - mlt * e[i - 1];
       if (fabsf(qi) < guard) qi = qi < 0.f ? -guard : guard;
-      r[i] = 1.f / qi;
+      r[i] = __fdividef(1.f, qi);
       ml[i] = mlt;
     }
     for (int i = 0; i < n; ++i) X[i * ld + t] = te_rand((uint32_t)t, (uint32_t)i);
@@ -302,76 +386,188 @@ __global__ void __launch_bounds__(TE_THREADS) tridiag_eig_kernel(const double* _
       const float inv = ss > 0.f && ss < INFINITY ? rsqrtf(ss) : 0.f;
       for (int i = 0; i < n; ++i) X[i * ld + t] *= inv;
     }
+    flag[t] = (t == 0 || lam[t] - lam[t - 1] > 1e-3f * nrm) ? 1.f : 0.f;
   }
   __syncthreads();
-  // Modified Gram-Schmidt inside clusters (warp 0, lanes over the rows).
-  if (warp == 0) {
-    const float ortol = 1e-3f * nrm;
-    int c0 = 0;
-    for (int t = 1; t < n; ++t) {
-      if (lam[t] - lam[t - 1] > ortol) {
-        c0 = t;
-        continue;
+  // Classical Gram-Schmidt twice inside each cluster, in eigenvalue order;
+  // cluster number q goes to warp q mod 16.  Lane l holds rows l + 32 b.
+  {
+    int q = 0;
+    for (int base = 0; base < n; base += 32) {
+      const unsigned starts = __ballot_sync(TE_FULL, base + lane < n && flag[base + lane] != 0.f);
+      unsigned rest = starts;
+      while (rest) {
+        const int c0 = base + __ffs(rest) - 1;
+        rest &= rest - 1;
+        // The cluster ends at the next start (possibly in a later chunk).
+        int c1 = c0 + 1;
+        if (rest) {
+          c1 = base + __ffs(rest) - 1;
+        } else {
+          c1 = n;
+          for (int nb = base + 32; nb < n; nb += 32) {
+            const unsigned s2 = __ballot_sync(TE_FULL, nb + lane < n && flag[nb + lane] != 0.f);
+            if (s2) {
+              c1 = nb + __ffs(s2) - 1;
+              break;
+            }
+          }
+        }
+        if (c1 - c0 > 1 && q % TE_WARPS == warp) {
+          for (int t = c0 + 1; t < c1; ++t) {
+            float xt[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) xt[b] = lane + 32 * b < n ? X[(lane + 32 * b) * ld + t] : 0.f;
+            for (int pass = 0; pass < 2; ++pass) {
+              float acc[NB];
+#pragma unroll
+              for (int b = 0; b < NB; ++b) acc[b] = 0.f;
+              // Four projections per round (their sums share the butterfly).
+              for (int s0 = c0; s0 < t; s0 += 4) {
+                float xs[4][NB], dot[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  dot[u] = 0.f;
+#pragma unroll
+                  for (int b = 0; b < NB; ++b) {
+                    xs[u][b] = (s0 + u < t && lane + 32 * b < n) ? X[(lane + 32 * b) * ld + s0 + u] : 0.f;
+                    dot[u] = fmaf(xs[u][b], xt[b], dot[u]);
+                  }
+                }
+                te_warp_sum<4>(dot);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                  for (int b = 0; b < NB; ++b) acc[b] = fmaf(dot[u], xs[u][b], acc[b]);
+              }
+#pragma unroll
+              for (int b = 0; b < NB; ++b) xt[b] -= acc[b];
+            }
+            float ss[1] = {0.f};
+#pragma unroll
+            for (int b = 0; b < NB; ++b) ss[0] = fmaf(xt[b], xt[b], ss[0]);
+            te_warp_sum<1>(ss);
+            const float inv = ss[0] > 0.f ? rsqrtf(ss[0]) : 0.f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+              if (lane + 32 * b < n) X[(lane + 32 * b) * ld + t] = xt[b] * inv;
+            __syncwarp();
+          }
+        }
+        ++q;
       }
-      for (int s = c0; s < t; ++s) {
-        float dot = 0.f;
-        for (int i = lane; i < n; i += 32) dot = fmaf(X[i * ld + s], X[i * ld + t], dot);
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        for (int i = lane; i < n; i += 32) X[i * ld + t] = fmaf(-dot, X[i * ld + s], X[i * ld + t]);
-        __syncwarp();
-      }
-      float ss = 0.f;
-      for (int i = lane; i < n; i += 32) ss = fmaf(X[i * ld + t], X[i * ld + t], ss);
-      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
-      for (int i = lane; i < n; i += 32) X[i * ld + t] *= inv;
-      __syncwarp();
     }
   }
   __syncthreads();
 
-  // 4. Back-transformation: for j = n-3 .. 0, X <- X - tau_j v_j (v_j^T X).
-  for (int j = n - 3; j >= 0; --j) {
-    const float t = tau[j];
-    if (t == 0.f) continue;  // uniform
-    const float sc = scl[j];
-    {
-      const int sub = tid % 4;
-      const unsigned gmask = 0xFu << (lane & ~3);
-      for (int c = tid / 4; c < n; c += TE_THREADS / 4) {
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll 4
-        for (int i = j + 1 + sub; i < n; i += 8) {
-          s0 = fmaf(i == j + 1 ? 1.f : A[i * ld + j] * sc, X[i * ld + c], s0);
-          if (i + 4 < n) s1 = fmaf(A[(i + 4) * ld + j] * sc, X[(i + 4) * ld + c], s1);
-        }
-        float s = s0 + s1;
-        s += __shfl_xor_sync(gmask, s, 1);
-        s += __shfl_xor_sync(gmask, s, 2);
-        if (sub == 0) p[c] = t * s;
-      }
-    }
-    __syncthreads();
-    float pc[TE_KREG];
-#pragma unroll
-    for (int q = 0; q < TE_KREG; ++q) pc[q] = lane + 32 * q < n ? p[lane + 32 * q] : 0.f;
-    for (int i = j + 1 + warp; i < n; i += TE_WARPS) {
-      const float vi = i == j + 1 ? 1.f : A[i * ld + j] * sc;
-      float x[TE_KREG];  // the row's loads before its stores
-#pragma unroll
-      for (int q = 0; q < TE_KREG; ++q) x[q] = lane + 32 * q < n ? X[i * ld + lane + 32 * q] : 0.f;
-#pragma unroll
-      for (int q = 0; q < TE_KREG; ++q)
-        if (lane + 32 * q < n) X[i * ld + lane + 32 * q] = fmaf(-vi, pc[q], x[q]);
-    }
-    __syncthreads();
+  // 4. Back-transformation, H_{n-3} first and H_0 last, four reflectors at
+  // a time.  For a block k_q = n-3-4b-q (q = 0..3, applied in that order)
+  // the projections of the partly transformed x follow from those of x:
+  // d_q = v_q^T x - sum_{p<q} tau_p d_p (v_q^T v_p), and then
+  // x <- x - sum_q tau_q d_q v_q.  The couplings v_q^T v_p come first (one
+  // warp per dot; cpl reuses the grid counts).  A warp takes a tile of 8
+  // eigenvectors (c = 8 tile + lane % 8); the four lane groups g = lane / 8
+  // hold the rows r = rpl g + m, m < rpl = ldv / 4, of its vector, so each
+  // projection is a register sum plus two butterfly steps.  Reflector rows
+  // are zero beyond n (and entirely for tau = 0).
+  float* cpl = reinterpret_cast<float*>(cnt);  // [6 * blocks]
+  const int nblk = (n - 2 + 3) / 4;
+  for (int qd = warp; qd < 6 * nblk; qd += TE_WARPS) {
+    const int idx = qd % 6, q1 = idx < 1 ? 1 : (idx < 3 ? 2 : 3), q2 = idx - q1 * (q1 - 1) / 2;
+    const int k1 = n - 3 - 4 * (qd / 6) - q1, k2 = n - 3 - 4 * (qd / 6) - q2;
+    float acc[1] = {0.f};
+    if (k1 >= 0)
+      for (int r = lane; r < ldv; r += 32) acc[0] = fmaf(Vr[k1 * ldv + r], Vr[k2 * ldv + r], acc[0]);
+    te_warp_sum<1>(acc);
+    if (lane == 0) cpl[qd] = acc[0];
   }
+  __syncthreads();
+  {
+    constexpr int RMAX = 8 * NB;  // rpl <= RMAX
+    const int rpl = ldv / 4, g = lane / 8, r0 = rpl * g;
+    for (int tile = warp; tile * 8 < n; tile += TE_WARPS) {
+      const int c = 8 * tile + lane % 8;
+      float xv[RMAX];
+#pragma unroll
+      for (int m = 0; m < RMAX; ++m) xv[m] = (m < rpl && c < n && r0 + m < n) ? X[(r0 + m) * ld + c] : 0.f;
+      for (int b = 0; b < nblk; ++b) {
+        const int kb = n - 3 - 4 * b;
+        float tq[4], gq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          tq[q] = kb - q >= 0 ? tau[kb - q] : 0.f;
+          gq[q] = 0.f;
+        }
+#pragma unroll
+        for (int m4 = 0; m4 < RMAX / 4; ++m4)
+          if (4 * m4 < rpl)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (kb - q >= 0) {
+                const float4 v = reinterpret_cast<const float4*>(Vr + (kb - q) * ldv + r0)[m4];
+                gq[q] = fmaf(v.x, xv[4 * m4], gq[q]);
+                gq[q] = fmaf(v.y, xv[4 * m4 + 1], gq[q]);
+                gq[q] = fmaf(v.z, xv[4 * m4 + 2], gq[q]);
+                gq[q] = fmaf(v.w, xv[4 * m4 + 3], gq[q]);
+              }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          gq[q] += __shfl_xor_sync(TE_FULL, gq[q], 8);
+          gq[q] += __shfl_xor_sync(TE_FULL, gq[q], 16);
+        }
+        const float* cb = cpl + 6 * b;
+        float dq[4];
+        dq[0] = gq[0];
+        dq[1] = fmaf(-tq[0] * dq[0], cb[0], gq[1]);
+        dq[2] = fmaf(-tq[1] * dq[1], cb[2], fmaf(-tq[0] * dq[0], cb[1], gq[2]));
+        dq[3] = fmaf(-tq[2] * dq[2], cb[5], fmaf(-tq[1] * dq[1], cb[4], fmaf(-tq[0] * dq[0], cb[3], gq[3])));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dq[q] *= -tq[q];
+#pragma unroll
+        for (int m4 = 0; m4 < RMAX / 4; ++m4)
+          if (4 * m4 < rpl)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (kb - q >= 0) {
+                const float4 v = reinterpret_cast<const float4*>(Vr + (kb - q) * ldv + r0)[m4];
+                xv[4 * m4] = fmaf(dq[q], v.x, xv[4 * m4]);
+                xv[4 * m4 + 1] = fmaf(dq[q], v.y, xv[4 * m4 + 1]);
+                xv[4 * m4 + 2] = fmaf(dq[q], v.z, xv[4 * m4 + 2]);
+                xv[4 * m4 + 3] = fmaf(dq[q], v.w, xv[4 * m4 + 3]);
+              }
+      }
+#pragma unroll
+      for (int m = 0; m < RMAX; ++m)
+        if (m < rpl && c < n && r0 + m < n) X[(r0 + m) * ld + c] = xv[m];
+    }
+  }
+  __syncthreads();
   for (int i = tid; i < n; i += TE_THREADS) diag_out[i] = lam[i];
   for (int idx = tid; idx < n * n; idx += TE_THREADS) V_out[idx] = X[(idx / n) * ld + idx % n];
 }
 
+namespace {
+using TeKernel = void (*)(const double*, int, float*, float*);
+// Column slots per lane: n <= 16 NT.
+int te_slots(int n) {
+  const int nt = (n + 15) / 16;
+  return nt <= 2 ? 2 : nt <= 4 ? 4 : nt <= 6 ? nt : nt <= 8 ? 8 : 10;
+}
+TeKernel te_kernel(int n) {
+  switch (te_slots(n)) {
+    case 2: return tridiag_eig_kernel<2>;
+    case 4: return tridiag_eig_kernel<4>;
+    case 5: return tridiag_eig_kernel<5>;
+    case 6: return tridiag_eig_kernel<6>;
+    case 8: return tridiag_eig_kernel<8>;
+    default: return tridiag_eig_kernel<10>;
+  }
+}
+}  // namespace
+
 int tridiag_eig_prepare() {
-  return raise_smem_limit((const void*)tridiag_eig_kernel, tridiag_eig_smem(TE_NMAX));
+  for (int n : {32, 64, 80, 96, 128, TE_NMAX}) ATK_TRY(raise_smem_limit((const void*)te_kernel(n), tridiag_eig_smem(n)));
+  return ATK_OK;
 }
 
 int tridiag_eig_f32(const double* S, int n, float* diag_out, float* V_out, cudaStream_t st) {
@@ -379,7 +575,7 @@ int tridiag_eig_f32(const double* S, int n, float* diag_out, float* V_out, cudaS
     set_error("tridiag_eig: need 1 <= n <= 160");
     return ATK_EUNSUPPORTED;
   }
-  tridiag_eig_kernel<<<1, TE_THREADS, tridiag_eig_smem(n), st>>>(S, n, diag_out, V_out);
+  te_kernel(n)<<<1, TE_THREADS, tridiag_eig_smem(n), st>>>(S, n, diag_out, V_out);
   ATK_LAUNCHED();
   return ATK_OK;
 }
