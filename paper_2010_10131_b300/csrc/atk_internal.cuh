@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 
 #include "atucker.h"
 
@@ -62,6 +63,17 @@ void count_launches(long long k);
 
 // Device status word bits (written by kernels, read by atucker_plan_sync).
 enum : int { DEV_NOCONV = 1, DEV_TIMEOUT = 2, DEV_CHOL = 4 };
+
+// ------------------------------------------------------- compile-time loop
+// f(std::integral_constant<int, P>{}) for P = B .. E-1: a loop whose index is
+// a constant in the body, so register arrays indexed by it stay in registers.
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
 
 // ------------------------------------------------------------ float-float sum
 // Fixed-order sum of float32 terms carried as an unevaluated pair hi + lo
@@ -178,6 +190,11 @@ int raise_smem_limit(const void* fn, size_t bytes);
 // (call it before capturing a launch into a graph).
 int tridiag_eig_prepare();
 int tridiag_eig_f32(const double* S, int n, float* diag_out, float* V_out, cudaStream_t st);
+// Mout (m x m column-major, upper triangular) = L^{-T} for L L^T = G + shift
+// max(diag G) I, G m x m float64, 1 <= m <= 160 (cholinv.cu).  A pivot at or
+// below 1e-12 max(diag G) is raised to that floor and sets *breakdown
+// (nullable).
+int cholinv_f32(const double* G, int m, float shift, float* Mout, int* breakdown, cudaStream_t st);
 
 // Float64 small dense linear algebra (smallla.cu).
 size_t smallla_scratch_bytes(int64_t n, int64_t R);

@@ -542,104 +542,6 @@ __global__ void colnorm_f32_kernel(float* __restrict__ Y, int64_t n, int64_t m) 
   for (int64_t i = lane; i < n; i += 32) y[i] *= inv;
 }
 
-// One CTA: Cholesky L L^T = G + shift * max(diag G) * I (G m x m SPD, float64
-// in, float32 work in shared memory) and the triangular inverse X = L^{-1},
-// written as Mout = X^T (m x m column-major, upper triangular) so that the
-// CholeskyQR update Y L^{-T} is the plain product Y Mout.  A pivot at or below
-// a tiny floor (rank-deficient block) is raised to the floor, so the factor
-// stays finite, and *breakdown (nullable) is set.
-// Both run right-looking in the same m steps, one barrier each.  Step j
-// reads the unscaled column j of L (final after step j-1) and row j of the
-// forward-substitution workspace W (W = I at the start, X[j, :] = W[j, :] /
-// l_jj), and every row i > j is updated by its four owner threads:
-// L[i, k] -= l_ij l_kj for j < k <= i and W[i, c] -= l_ij X[j, c] for c <= j.
-// L itself is never scaled (only its unscaled columns are read, times
-// 1/l_jj); row j of W becomes X[j, :] in step j+1, when nothing reads it any
-// more.  Each thread loads a batch of its operands before it stores any
-// result, so the shared-memory loads overlap instead of waiting on the
-// previous store.
-constexpr int CHOL_THREADS = 512;
-__global__ void __launch_bounds__(CHOL_THREADS) cholinv_f32_kernel(const double* __restrict__ G, int m, float shift,
-                                                                    float* __restrict__ Mout,
-                                                                    int* __restrict__ breakdown) {
-  extern __shared__ float sm[];
-  const int ld = m + 1;
-  float* L = sm;           // column-major, L[i + ld k]
-  float* W = sm + m * ld;  // row-major, W[t * ld + c]
-  __shared__ float dmax_s;
-  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
-  for (int idx = tid; idx < m * m; idx += CHOL_THREADS) {
-    const int r = idx % m, c = idx / m;
-    L[r + ld * c] = (float)G[idx];
-    W[c * ld + r] = (r == c) ? 1.f : 0.f;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    float d = 0.f;
-    for (int j = lane; j < m; j += 32) d = fmaxf(d, L[j + ld * j]);
-    for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
-    if (lane == 0) dmax_s = d;
-  }
-  __syncthreads();
-  const float dmax = dmax_s;
-  for (int j = tid; j < m; j += CHOL_THREADS) L[j + ld * j] += shift * dmax;
-  __syncthreads();
-  const float floor_v = 1e-12f * dmax + 1e-30f;
-  float inv_prev = 0.f;
-  const int sub = tid % 4;
-  constexpr int CB = 8;  // operands loaded per batch
-  for (int j = 0; j < m; ++j) {
-    const float d = L[j + ld * j];
-    if (tid == 0 && !(d > floor_v) && breakdown) atomicOr(breakdown, 1);
-    const float inv = 1.f / sqrtf(d > floor_v ? d : floor_v);
-    if (j > 0)
-      for (int c = tid; c < j; c += CHOL_THREADS) W[(j - 1) * ld + c] *= inv_prev;
-    for (int i = j + 1 + tid / 4; i < m; i += CHOL_THREADS / 4) {
-      const float lij = L[i + ld * j] * inv;
-      for (int k0 = j + 1 + sub; k0 <= i; k0 += 4 * CB) {
-        float a[CB], b[CB];
-#pragma unroll
-        for (int u = 0; u < CB; ++u) {
-          const int k = k0 + 4 * u;
-          if (k <= i) {
-            a[u] = L[k + ld * j];
-            b[u] = L[i + ld * k];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < CB; ++u) {
-          const int k = k0 + 4 * u;
-          if (k <= i) L[i + ld * k] = fmaf(-lij, a[u] * inv, b[u]);
-        }
-      }
-      for (int c0 = sub; c0 <= j; c0 += 4 * CB) {
-        float a[CB], b[CB];
-#pragma unroll
-        for (int u = 0; u < CB; ++u) {
-          const int c = c0 + 4 * u;
-          if (c <= j) {
-            a[u] = W[j * ld + c];
-            b[u] = W[i * ld + c];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < CB; ++u) {
-          const int c = c0 + 4 * u;
-          if (c <= j) W[i * ld + c] = fmaf(-lij, a[u] * inv, b[u]);
-        }
-      }
-    }
-    inv_prev = inv;
-    __syncthreads();
-  }
-  for (int c = tid; c < m; c += CHOL_THREADS) W[(m - 1) * ld + c] *= inv_prev;
-  __syncthreads();
-  for (int idx = tid; idx < m * m; idx += CHOL_THREADS) {
-    const int i = idx % m, r = idx / m;
-    Mout[idx] = r >= i ? W[r * ld + i] : 0.f;
-  }
-}
-inline size_t cholinv_smem(int m) { return (size_t)2 * m * (m + 1) * sizeof(float); }
 
 // res[j] = ||Z[:, j] - theta_j Q[:, j]|| for j < R; one warp per column.
 __global__ void ritz_residual_kernel(const float* __restrict__ Z, const float* __restrict__ Q,
@@ -683,7 +585,7 @@ namespace {
 struct RRBufs {
   float *Sf, *Q, *Y, *Z, *T, *LinvT, *Vb, *diag, *Wf;  // LinvT = L^{-T} of the last CholeskyQR pass
   double *G, *W64, *theta, *res, *summary, *Cd;  // Cd: n x m float64 product S Q
-  int* breakdown;  // set by cholinv_f32_kernel when a pivot hits its floor
+  int* breakdown;  // set by cholinv_f32 when a pivot hits its floor
   float* part;  // split-K partials of the m x m products
   size_t part_bytes;
 };
@@ -714,8 +616,7 @@ int cholqr_pass_f32(float* Y, float* Q, int64_t n, int m, float shift, RRBufs& b
   colnorm_f32_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Y, n, m);
   ATK_LAUNCHED();
   ATK_TRY(gram_f32(Y, v, b.G, b.part, b.part_bytes, st));
-  cholinv_f32_kernel<<<1, CHOL_THREADS, cholinv_smem(m), st>>>(b.G, m, shift, b.LinvT, b.breakdown);
-  ATK_LAUNCHED();
+  ATK_TRY(cholinv_f32(b.G, m, shift, b.LinvT, b.breakdown, st));
   return ttm_f32(Y, v, b.LinvT, m, Q, st);  // Q = Y L^{-T}
 }
 // Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Zhang, Yamamoto, SISC 2020):
@@ -760,13 +661,9 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   b.part = (float*)ar.take(b.part_bytes);
   if (!b.part) { set_error("rr: scratch too small"); return ATK_EINVAL; }
   const View qv{n, m, 1};
-  // Shared-memory limits of the one-CTA kernels, set outside the captured
-  // launch sequences (for the widest block, once).
-  {
-    const size_t mmax = 156;
-    ATK_TRY(raise_smem_limit((const void*)cholinv_f32_kernel, cholinv_smem((int)mmax)));
-    ATK_TRY(tridiag_eig_prepare());
-  }
+  // Shared-memory limit of the one-CTA eigensolver, set outside the captured
+  // launch sequences.
+  ATK_TRY(tridiag_eig_prepare());
   // The three launch sequences between host reads, each a cached graph:
   // setup (the float32 copy of S, a random block, one power step, shifted
   // CholeskyQR3), one Rayleigh-Ritz step up to its summary, and the two
@@ -934,8 +831,8 @@ constexpr int REFINE_ROTATION_STEPS = 2;
 constexpr int64_t REFINE_PART_EXTRA = 512 * 1024;
 
 size_t refine_bytes(int64_t n, int64_t k) {
-  return sizeof(double) * (size_t)(2 * n * k + 6 * k * k + 2 * k + 8 + n * k + REFINE_PART_EXTRA) + sizeof(int) * (size_t)k +
-         smallla_scratch_bytes(std::max(n, k), k) + 4096;
+  return sizeof(double) * (size_t)(2 * n * k + 6 * k * k + 2 * k + 8 + n * k + REFINE_PART_EXTRA) +
+         sizeof(int) * (size_t)k + smallla_scratch_bytes(std::max(n, k), k) + 4096;
 }
 
 // Float64 refinement of an approximate leading block Qb (n x k, columns
@@ -989,9 +886,10 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
     // their span alone.  One CholeskyQR pass with a float32 factor (robust for
     // any such overlap) takes the columns to float32 orthogonality, then two
     // Gram-Schmidt-ordered quadratic steps to float64 level.
+    // k <= 156 here (k = m <= 156 on the subspace path, k = R <= 128 after
+    // the full Jacobi), within the one-CTA factor's limit of 160.
     ATK_TRY(gemm_tn_f64(Qb, Qb, n, k, B, pol, st));
-    cholinv_f32_kernel<<<1, CHOL_THREADS, cholinv_smem((int)k), st>>>(B, (int)k, 0.f, Tf, nullptr);
-    ATK_LAUNCHED();
+    ATK_TRY(cholinv_f32(B, (int)k, 0.f, Tf, nullptr, st));
     ATK_TRY(f32_to_f64(Tf, T, k * k, st));
     ATK_TRY(gemm_f64_split(Qb, T, n, k, k, Z, gpart, gcap, st));
     ATK_CUDA(cudaMemcpyAsync(Qb, Z, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
@@ -1149,7 +1047,6 @@ int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int ma
   }
   // The refinement and the float32 copy of U: no host synchronisation inside,
   // so one cached graph per (buffers, sizes).
-  if (k <= 156) ATK_TRY(raise_smem_limit((const void*)cholinv_f32_kernel, cholinv_smem((int)k)));
   const GraphKey key{{S, Qb, U64_out, lambda_out, discarded_out, U_out, rest, nullptr},
                      {n, k, R, (int64_t)rest_bytes}};
   return run_graph(key, st, [&](cudaStream_t s2) -> int {

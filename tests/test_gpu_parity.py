@@ -76,15 +76,17 @@ def _spd_with_gap(n, R, seed):
 
 
 def _rr_used(n, R, arith, method):
-    p = max(8, min(R, 32))
+    # The library's choice: block width m = R + p, p = clamp(R / 2, 8, 16),
+    # m <= 156; the subspace path needs m >= R + 8 (and, for AUTO, 2 m <= n).
+    p = max(8, min(16, R // 2))
     m = min(n, R + p, 156)
-    return arith == 0 and ((method == 0 and 2 * m <= n) or (method == 2 and m < n))
+    return arith == 0 and m >= R + 8 and ((method == 0 and 2 * m <= n) or (method == 2 and m < n))
 
 
 @pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("arith", [0, 1])
 @pytest.mark.parametrize("n,R", [(2, 1), (5, 2), (33, 8), (96, 8), (128, 16), (130, 16), (200, 20), (640, 64),
-                                 (1000, 128)])
+                                 (1000, 128), (150, 40), (200, 72), (240, 100)])
 def test_eig_matches_oracle(atk, n, R, arith, method):
     if arith == 1 and n > 200:
         pytest.skip("float64 rotations at n >= 640 are slow on B300 (covered at 200)")
