@@ -44,16 +44,17 @@ constexpr int TE_THREADS = 512;
 constexpr int TE_WARPS = TE_THREADS / 32;
 constexpr int TE_NMAX = 160;      // largest matrix (the subspace eigensolver uses m <= 156)
 constexpr int TE_GRID = TE_THREADS;  // points of the first multisection step
+constexpr int TE_VBUF = TE_NMAX + 4;  // length of the two column buffers (a multiple of 4)
 constexpr int TE_MAXSECT = 40;    // multisection steps (a cap; the width test ends them sooner)
 constexpr unsigned TE_FULL = 0xffffffffu;
 
 // Shared memory: the per-warp partial sums and the grid counts, two vectors
-// of length TE_NMAX, the reflectors (row j = v_j, n x ldv with ldv = n
+// of length TE_VBUF, the reflectors (row j = v_j, n x ldv with ldv = n
 // rounded up to 16), the eigenvector block X (n x (n+1)) and six vectors of
 // length n.
 size_t tridiag_eig_smem(int n) {
   const size_t ld = (size_t)n + 1, ldv = 16 * (((size_t)n + 15) / 16);
-  return sizeof(float) * (2 * TE_WARPS + 8 + TE_GRID + 2 * TE_NMAX + (size_t)n * ldv + n * ld + 6 * (size_t)n);
+  return sizeof(float) * (2 * TE_WARPS + 8 + TE_GRID + 2 * TE_VBUF + (size_t)n * ldv + n * ld + 6 * (size_t)n);
 }
 
 // Sum of v over the 32 lanes of the warp by an xor butterfly: lanes l and
@@ -67,40 +68,53 @@ __device__ __forceinline__ void te_warp_sum(float (&v)[K]) {
     for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(TE_FULL, v[k], o);
 }
 
-// Sturm count: the number of eigenvalues of T (diagonal d, squared
-// off-diagonal e2) below x, from the signs of the pivots of T - x I.
-__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int n, float x, float pivmin) {
-  float q = d[0] - x;
-  if (fabsf(q) < pivmin) q = -pivmin;
-  int c = q < 0.f;
+// Reciprocal estimate (one hardware approximation; denormals flush to zero,
+// so a denormal pivot acts as a zero one).
+__device__ __forceinline__ float te_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Sturm count: the number of eigenvalues of T below x, from the signs of the
+// pivots q_i = (d_i - x) - e_{i-1}^2 / q_{i-1} of T - x I; de[i] = (d_i,
+// e_{i-1}^2).  No pivot guard: a zero pivot makes the next one -inf and the
+// one after it finite again (IEEE arithmetic; the squared off-diagonal
+// entries are kept >= a tiny positive floor, so 0 * inf never occurs).  The
+// sign bit is counted, so q = -0 counts as negative and the +inf after it
+// as positive, like q = +0 followed by -inf.  The next (d, e^2) pair is
+// loaded one step ahead; de has n + 1 entries (the last one a pad).
+__device__ __forceinline__ int sturm_count(const float2* __restrict__ de, int n, float x) {
+  float q = de[0].x - x;
+  unsigned c = __float_as_uint(q) >> 31;
+  float2 v = de[1];
 #pragma unroll 4
   for (int i = 1; i < n; ++i) {
-    q = d[i] - x - __fdividef(e2[i - 1], q);
-    if (fabsf(q) < pivmin) q = -pivmin;
-    c += q < 0.f;
+    const float2 vn = de[i + 1];  // de[n] is a pad entry
+    q = fmaf(-v.y, te_rcp(q), v.x - x);
+    c += __float_as_uint(q) >> 31;
+    v = vn;
   }
-  return c;
+  return (int)c;
 }
 
 // The same recurrence at two points at once (two independent chains).
-__device__ __forceinline__ void sturm_count2(const float* d, const float* e2, int n, float x0, float x1,
-                                             float pivmin, int& c0, int& c1) {
-  float q0 = d[0] - x0, q1 = d[0] - x1;
-  if (fabsf(q0) < pivmin) q0 = -pivmin;
-  if (fabsf(q1) < pivmin) q1 = -pivmin;
-  int k0 = q0 < 0.f, k1 = q1 < 0.f;
+__device__ __forceinline__ void sturm_count2(const float2* __restrict__ de, int n, float x0, float x1, int& c0,
+                                             int& c1) {
+  float q0 = de[0].x - x0, q1 = de[0].x - x1;
+  unsigned k0 = __float_as_uint(q0) >> 31, k1 = __float_as_uint(q1) >> 31;
+  float2 v = de[1];
 #pragma unroll 4
   for (int i = 1; i < n; ++i) {
-    const float di = d[i], ei = e2[i - 1];
-    q0 = di - x0 - __fdividef(ei, q0);
-    q1 = di - x1 - __fdividef(ei, q1);
-    if (fabsf(q0) < pivmin) q0 = -pivmin;
-    if (fabsf(q1) < pivmin) q1 = -pivmin;
-    k0 += q0 < 0.f;
-    k1 += q1 < 0.f;
+    const float2 vn = de[i + 1];  // de[n] is a pad entry
+    q0 = fmaf(-v.y, te_rcp(q0), v.x - x0);
+    q1 = fmaf(-v.y, te_rcp(q1), v.x - x1);
+    k0 += __float_as_uint(q0) >> 31;
+    k1 += __float_as_uint(q1) >> 31;
+    v = vn;
   }
-  c0 = k0;
-  c1 = k1;
+  c0 = (int)k0;
+  c1 = (int)k1;
 }
 
 __device__ __forceinline__ float te_rand(uint32_t a, uint32_t b) {
@@ -148,9 +162,9 @@ __global__ void __launch_bounds__(TE_THREADS, 1) tridiag_eig_kernel(const double
   float* kpart = part + TE_WARPS;     // [TE_WARPS] partial sums of p^T v
   float* red = kpart + TE_WARPS;      // [8] interval ends and norm
   int* cnt = reinterpret_cast<int*>(red + 8);  // [TE_GRID] Sturm counts of the grid
-  float* xb = reinterpret_cast<float*>(cnt + TE_GRID);  // [TE_NMAX] column j+1, zero above row j+2
-  float* pb = xb + TE_NMAX;           // [TE_NMAX] p, zero outside the trailing block
-  float* Vr = pb + TE_NMAX;           // n x ldv: row j = v_j, zero beyond n
+  float* xb = reinterpret_cast<float*>(cnt + TE_GRID);  // [TE_VBUF] column j+1, zero above row j+2
+  float* pb = xb + TE_VBUF;           // [TE_VBUF] p, zero outside the trailing block
+  float* Vr = pb + TE_VBUF;           // n x ldv: row j = v_j, zero beyond n
   float* X = Vr + n * ldv;            // n x ld, row-major; column t = eigenvector t
   float* d = X + n * ld;              // diagonal of T
   float* e = d + n;                   // off-diagonal of T: e[j] = T(j+1, j)
@@ -171,102 +185,116 @@ __global__ void __launch_bounds__(TE_THREADS, 1) tridiag_eig_kernel(const double
       const int i = warp + WH * (rs + 2 * s), k = cg + 16 * t;
       a[s][t] = (hw && i < n && k < n) ? (float)S[(size_t)i * n + k] : 0.f;
     }
-  // Publish column c of the partly reduced A below row c (zero above it,
-  // and zero beyond n) and this warp's partial squared norm below row c+1.
-  // Column c sits in slot c / 16 of the lanes with cg = c % 16.
-  auto publish = [&](int c) {
+  // Column 0 below the diagonal (slot 0 of the lanes with cg = 0; xb is zero
+  // at row 0 and beyond n) and the partial squared norms below row 1.
+  if (hw) {
     float sg = 0.f;
-    if (cg == c % 16) {
-      const int tc = c / 16;
+    if (cg == 0)
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        float v = a[s][0];
-#pragma unroll
-        for (int t = 1; t < NT; ++t) v = t == tc ? a[s][t] : v;  // selects keep a[][] in registers
         const int i = warp + WH * (rs + 2 * s);
-        xb[i] = i > c ? v : 0.f;
-        if (i > c + 1) sg = fmaf(v, v, sg);
+        xb[i] = i > 0 ? a[s][0] : 0.f;
+        if (i > 1) sg = fmaf(a[s][0], a[s][0], sg);
       }
-    }
     sg += __shfl_xor_sync(TE_FULL, sg, 16);
-    if (lane == c % 16) part[warp] = sg;
-  };
-  if (hw) publish(0);
-  __syncthreads();
-  for (int j = 0; j + 2 < n; ++j) {
-    float t = 0.f, vk[NT], vi[NS], p[NS];
-    if (hw) {
-      const float sig = te_sum<WH>(part);
-      const float alpha = xb[j + 1];
-      float beta = alpha, scale = 0.f;
-      if (sig > 0.f) {
-        const float mu = sqrtf(fmaf(alpha, alpha, sig));
-        beta = alpha <= 0.f ? mu : -mu;
-        t = __fdividef(beta - alpha, beta);
-        scale = __fdividef(1.f, alpha - beta);
-      }
-      if (tid == 0) {
-        e[j] = beta;
-        tau[j] = t;
-      }
-      // v_j(r) = 1 at r = j+1, x(r) * scale below, 0 elsewhere (xb is zero
-      // at r <= j and beyond n).
-      auto vval = [&](int r) -> float { return r == j + 1 ? 1.f : xb[r] * scale; };
-      if (tid < ldv) Vr[j * ldv + tid] = t != 0.f ? vval(tid) : 0.f;
-      if (t != 0.f) {  // uniform: every thread has the same sig
-#pragma unroll
-        for (int u = 0; u < NT; ++u) vk[u] = vval(cg + 16 * u);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) vi[s] = vval(warp + WH * (rs + 2 * s));
-        // p = tau A v: register products, then a butterfly over the 16 lanes
-        // of the row group (columns <= j carry v = 0 and are skipped).
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          float acc = 0.f;
-#pragma unroll
-          for (int u = 0; u < NT; ++u)
-            if (16 * u + 15 > j) acc = fmaf(a[s][u], vk[u], acc);
-          p[s] = acc;
-        }
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1)
-#pragma unroll
-          for (int s = 0; s < NS; ++s) p[s] += __shfl_xor_sync(TE_FULL, p[s], o);
-        // Rows <= j are outside the trailing block (their entries are stale).
-        float pv = 0.f;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          const int i = warp + WH * (rs + 2 * s);
-          p[s] = i > j ? t * p[s] : 0.f;
-          pv = fmaf(p[s], vi[s], pv);
-          if (cg == s) pb[i] = p[s];
-        }
-        pv += __shfl_xor_sync(TE_FULL, pv, 16);
-        if (lane == 0) kpart[warp] = pv;
-      }
-    }
-    __syncthreads();
-    if (hw) {
-      if (t != 0.f) {
-        // w = p - K v, K = (tau/2) p^T v; A -= v w^T + w v^T.  Outside the
-        // trailing block v, p and w vanish, so the update leaves it unchanged.
-        const float kk = 0.5f * t * te_sum<WH>(kpart);
-        float wk[NT];
-#pragma unroll
-        for (int u = 0; u < NT; ++u) wk[u] = fmaf(-kk, vk[u], pb[cg + 16 * u]);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          const float wi = fmaf(-kk, vi[s], p[s]);
-          if (warp + WH * (2 * s + 1) > j)  // uniform over the warp: some row of slot s is in the block
-#pragma unroll
-            for (int u = 0; u < NT; ++u)
-              if (16 * u + 15 > j) a[s][u] = fmaf(-vi[s], wk[u], fmaf(-wi, vk[u], a[s][u]));
-        }
-      }
-      publish(j + 1);
-    }
-    __syncthreads();
+    if (lane == 0) part[warp] = sg;
   }
+  __syncthreads();
+  // Steps j = 16 P - 1 .. 16 P + 14 publish the columns c = j + 1 of slot P,
+  // so P is a compile-time constant in their body: the publishing needs no
+  // selects, and the slots that lie entirely above or left of the trailing
+  // block are skipped without a branch (column slots t < P, row slots s < S0:
+  // there v, p and w vanish, and xb and pb already hold the zeros read).
+  static_for<0, NT + 1>([&](auto PC) {
+    constexpr int P = decltype(PC)::value;
+    if constexpr (P < NT) {
+      constexpr int S0 = WH == 8 ? P : P / 2;
+      const int jhi = min(16 * P + 15, n - 2);
+      for (int j = P == 0 ? 0 : 16 * P - 1; j < jhi; ++j) {
+        float t = 0.f, vk[NT], vi[NS], p[NS];
+        if (hw) {
+          const float sig = te_sum<WH>(part);
+          const float alpha = xb[j + 1];
+          float beta = alpha, scale = 0.f;
+          if (sig > 0.f) {
+            const float mu = sqrtf(fmaf(alpha, alpha, sig));
+            beta = alpha <= 0.f ? mu : -mu;
+            t = __fdividef(beta - alpha, beta);
+            scale = __fdividef(1.f, alpha - beta);
+          }
+          if (tid == 0) {
+            e[j] = beta;
+            tau[j] = t;
+          }
+          // v_j(r) = 1 at r = j+1, x(r) * scale below, 0 elsewhere (xb is
+          // zero at r <= j and beyond n).
+          auto vval = [&](int r) -> float { return r == j + 1 ? 1.f : xb[r] * scale; };
+          if (tid < ldv) Vr[j * ldv + tid] = t != 0.f ? vval(tid) : 0.f;
+          if (t != 0.f) {  // uniform: every thread has the same sig
+#pragma unroll
+            for (int u = P; u < NT; ++u) vk[u] = vval(cg + 16 * u);
+#pragma unroll
+            for (int s = S0; s < NS; ++s) vi[s] = vval(warp + WH * (rs + 2 * s));
+            // p = tau A v: register products, then a butterfly over the 16
+            // lanes of the row group.
+#pragma unroll
+            for (int s = S0; s < NS; ++s) {
+              float acc = 0.f;
+#pragma unroll
+              for (int u = P; u < NT; ++u) acc = fmaf(a[s][u], vk[u], acc);
+              p[s] = acc;
+            }
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1)
+#pragma unroll
+              for (int s = S0; s < NS; ++s) p[s] += __shfl_xor_sync(TE_FULL, p[s], o);
+            // Rows <= j are outside the trailing block (their entries are stale).
+            float pv = 0.f;
+#pragma unroll
+            for (int s = S0; s < NS; ++s) {
+              const int i = warp + WH * (rs + 2 * s);
+              p[s] = i > j ? t * p[s] : 0.f;
+              pv = fmaf(p[s], vi[s], pv);
+              if (cg == s) pb[i] = p[s];
+            }
+            pv += __shfl_xor_sync(TE_FULL, pv, 16);
+            if (lane == 0) kpart[warp] = pv;
+          }
+        }
+        __syncthreads();
+        if (hw) {
+          if (t != 0.f) {
+            // w = p - K v, K = (tau/2) p^T v; A -= v w^T + w v^T.  Outside
+            // the trailing block v, p and w vanish.
+            const float kk = 0.5f * t * te_sum<WH>(kpart);
+            float wk[NT];
+#pragma unroll
+            for (int u = P; u < NT; ++u) wk[u] = fmaf(-kk, vk[u], pb[cg + 16 * u]);
+#pragma unroll
+            for (int s = S0; s < NS; ++s) {
+              const float wi = fmaf(-kk, vi[s], p[s]);
+#pragma unroll
+              for (int u = P; u < NT; ++u) a[s][u] = fmaf(-vi[s], wk[u], fmaf(-wi, vk[u], a[s][u]));
+            }
+          }
+          // Column c = j+1 (slot P) below the diagonal, with the partial
+          // squared norm below row c+1.
+          const int c = j + 1;
+          float sg = 0.f;
+          if (cg == c % 16)
+#pragma unroll
+            for (int s = S0; s < NS; ++s) {
+              const int i = warp + WH * (rs + 2 * s);
+              xb[i] = i > c ? a[s][P] : 0.f;
+              if (i > c + 1) sg = fmaf(a[s][P], a[s][P], sg);
+            }
+          sg += __shfl_xor_sync(TE_FULL, sg, 16);
+          if (lane == c % 16) part[warp] = sg;
+        }
+        __syncthreads();
+      }
+    }
+  });
   // T: the diagonal and the last off-diagonal entry from the registers.
   if (hw) {
 #pragma unroll
@@ -304,13 +332,22 @@ __global__ void __launch_bounds__(TE_THREADS, 1) tridiag_eig_kernel(const double
   }
   __syncthreads();
   const float nrm = red[2];
-  const float pivmin = 1e-30f * fmaxf(1.f, nrm * nrm);
+  // (d_i, e_{i-1}^2) interleaved for the Sturm counts, plus a zero pad entry
+  // at n, in the space of xb and pb (free after the reduction; 2 TE_VBUF >=
+  // 2 (n + 1) floats); e^2 is floored at 1e-30 max(1, ||T||^2).
+  float2* de = reinterpret_cast<float2*>(xb);
+  {
+    const float e2min = 1e-30f * fmaxf(1.f, nrm * nrm);
+    for (int i = tid; i <= n; i += TE_THREADS)
+      de[i] = i < n ? make_float2(d[i], i > 0 ? fmaxf(e2[i - 1], e2min) : 0.f) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
 
   // 2. Multisection.  Grid point p (0 <= p <= TE_GRID + 1) is lo + hg p, with
   // count 0 at p = 0 and n at p = TE_GRID + 1 (the padded Gershgorin ends).
   const float glo = red[0], ghi = red[1];
   const float hg = (ghi - glo) / (float)(TE_GRID + 1);
-  cnt[tid] = sturm_count(d, e2, n, glo + hg * (float)(tid + 1), pivmin);
+  cnt[tid] = sturm_count(de, n, glo + hg * (float)(tid + 1));
   __syncthreads();
   {
     const int G = n <= TE_THREADS / 8 ? 8 : (n <= TE_THREADS / 4 ? 4 : (n <= TE_THREADS / 2 ? 2 : 1));
@@ -330,7 +367,7 @@ __global__ void __launch_bounds__(TE_THREADS, 1) tridiag_eig_kernel(const double
         // Points 1 .. 2G of the bracket; lane g tests 2g+1 and 2g+2.
         const float h = (b0 - a0) / (float)(2 * G + 1);
         int c0, c1;
-        sturm_count2(d, e2, n, a0 + h * (float)(2 * g + 1), a0 + h * (float)(2 * g + 2), pivmin, c0, c1);
+        sturm_count2(de, n, a0 + h * (float)(2 * g + 1), a0 + h * (float)(2 * g + 2), c0, c1);
         const unsigned sh = lane / G * G;
         const unsigned any = (__ballot_sync(gmask, c0 > t || c1 > t) >> sh);
         const unsigned b0s = (__ballot_sync(gmask, c0 > t) >> sh);
