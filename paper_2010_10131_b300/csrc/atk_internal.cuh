@@ -199,8 +199,7 @@ int cholinv_f32(const double* G, int m, float shift, float* Mout, int* breakdown
 // Float64 small dense linear algebra (smallla.cu).
 size_t smallla_scratch_bytes(int64_t n, int64_t R);
 // G (R x R) = A^T B, A and B n x R float64.
-int gemm_tn_f64(const double* A, const double* B, int64_t n, int64_t R, double* G, double* scratch,
-                cudaStream_t st);
+int gemm_tn_f64(const double* A, const double* B, int64_t n, int64_t R, double* G, cudaStream_t st);
 // In place: X (m x R) <- X G^{-1}, G symmetric positive definite (R x R).
 int solve_spd_right_f64(double* X, int64_t m, int64_t R, const double* G, double* chol_scratch,
                         int* dev_status, cudaStream_t st);
@@ -213,11 +212,10 @@ int gs_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_t s
 // CholeskyQR2 in float64: L (n x R) = Q R^, Q overwrites L, R^ (R x R) upper, diag > 0.
 int cholqr2_f64(double* L, int64_t n, int64_t R, double* Rhat, double* scratch, int* dev_status,
                 cudaStream_t st);
-// C (m x p) = A (m x k) B (k x p), column-major float64, split over k into
-// at most part_cap / (m p) partial products (part: float64 scratch that
-// overlaps none of A, B, C) so that small outputs still cover the chip.
-int gemm_f64_split(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, double* part,
-                   int64_t part_cap, cudaStream_t st);
+// C (m x p) = A (m x k) B (k x p), column-major float64 (C overlaps neither
+// A nor B); split over k so that small outputs still cover the chip, the
+// splits summed in a fixed order inside the launch.
+int gemm_f64(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, cudaStream_t st);
 int f64_to_f32(const double* src, float* dst, int64_t count, cudaStream_t st);
 int f32_to_f64(const float* src, double* dst, int64_t count, cudaStream_t st);
 // Square of the Frobenius norm of a float32 tensor, accumulated in float64.

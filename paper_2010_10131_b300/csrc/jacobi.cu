@@ -826,12 +826,9 @@ __global__ void identity_kernel(double* __restrict__ W, int64_t k) {
 }
 
 constexpr int REFINE_ROTATION_STEPS = 2;
-// Split-K partials of the float64 products: one n x k output plus enough for
-// about two 32 x 32 tiles per SM of any smaller output.
-constexpr int64_t REFINE_PART_EXTRA = 512 * 1024;
 
 size_t refine_bytes(int64_t n, int64_t k) {
-  return sizeof(double) * (size_t)(2 * n * k + 6 * k * k + 2 * k + 8 + n * k + REFINE_PART_EXTRA) +
+  return sizeof(double) * (size_t)(2 * n * k + 6 * k * k + 2 * k + 8) +
          sizeof(int) * (size_t)k + smallla_scratch_bytes(std::max(n, k), k) + 4096;
 }
 
@@ -865,13 +862,11 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   double* norms = (double*)ar.take(sizeof(double) * (2 * k + 8));
   int* order = (int*)ar.take(sizeof(int) * k);
   double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
-  const int64_t gcap = n * k + REFINE_PART_EXTRA;
-  double* gpart = (double*)ar.take(sizeof(double) * gcap);
-  if (!pol || !gpart) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
+  if (!pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
   const unsigned gk = (unsigned)ceil_div(k * k, 256);
   // 1. subspace step (subspace_step = false only orthonormalises Qb)
   if (subspace_step) {
-    ATK_TRY(gemm_f64_split(S, Qb, n, n, k, Z, gpart, gcap, st));
+    ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
     colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
     ATK_LAUNCHED();
     normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k, 1e-5, 0.9,
@@ -888,10 +883,10 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
     // Gram-Schmidt-ordered quadratic steps to float64 level.
     // k <= 156 here (k = m <= 156 on the subspace path, k = R <= 128 after
     // the full Jacobi), within the one-CTA factor's limit of 160.
-    ATK_TRY(gemm_tn_f64(Qb, Qb, n, k, B, pol, st));
+    ATK_TRY(gemm_tn_f64(Qb, Qb, n, k, B, st));
     ATK_TRY(cholinv_f32(B, (int)k, 0.f, Tf, nullptr, st));
     ATK_TRY(f32_to_f64(Tf, T, k * k, st));
-    ATK_TRY(gemm_f64_split(Qb, T, n, k, k, Z, gpart, gcap, st));
+    ATK_TRY(gemm_f64(Qb, T, n, k, k, Z, st));
     ATK_CUDA(cudaMemcpyAsync(Qb, Z, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
     for (int it = 0; it < 2; ++it) ATK_TRY(gs_step_f64(Qb, n, k, pol, st));
   } else {
@@ -899,8 +894,8 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
     ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
   }
   // 2. Rayleigh-Ritz and simultaneous rotations
-  ATK_TRY(gemm_f64_split(S, Qb, n, n, k, Z, gpart, gcap, st));
-  ATK_TRY(gemm_tn_f64(Qb, Z, n, k, B, pol, st));
+  ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
+  ATK_TRY(gemm_tn_f64(Qb, Z, n, k, B, st));
   identity_kernel<<<gk, 256, 0, st>>>(Wt, k);
   ATK_LAUNCHED();
   for (int step = 0; step < REFINE_ROTATION_STEPS && k > 1; ++step) {
@@ -908,15 +903,15 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
     ATK_LAUNCHED();
     ATK_TRY(polar_step_f64(W, k, k, pol, st));
     ATK_TRY(polar_step_f64(W, k, k, pol, st));
-    ATK_TRY(gemm_f64_split(B, W, k, k, k, T, gpart, gcap, st));
-    ATK_TRY(gemm_tn_f64(W, T, k, k, B, pol, st));
-    ATK_TRY(gemm_f64_split(Wt, W, k, k, k, T2, gpart, gcap, st));
+    ATK_TRY(gemm_f64(B, W, k, k, k, T, st));
+    ATK_TRY(gemm_tn_f64(W, T, k, k, B, st));
+    ATK_TRY(gemm_f64(Wt, W, k, k, k, T2, st));
     std::swap(Wt, T2);
   }
   // 3. kept vectors
   order_diag_kernel<<<1, 256, 0, st>>>(B, (int)k, (int)R, S, n, order, lambda_out, discarded_out);
   ATK_LAUNCHED();
-  ATK_TRY(gemm_f64_split(Qb, Wt, n, k, k, QW, gpart, gcap, st));
+  ATK_TRY(gemm_f64(Qb, Wt, n, k, k, QW, st));
   gather_cols_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(QW, order, n, R, U64);
   ATK_LAUNCHED();
   ATK_TRY(polar_step_f64(U64, n, R, pol, st));

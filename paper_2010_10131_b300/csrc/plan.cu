@@ -90,7 +90,7 @@ static int als_mode_run(const float* y, const View& v, int64_t R, const double* 
   ATK_CUDA(cudaMemcpyAsync(b.L, L0, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
   for (int k = 0; k < sweeps; ++k) {
     // R_k = (Y^T L_k)(L_k^T L_k)^{-1} = Y^T L~ with L~ = L_k (L_k^T L_k)^{-1}.
-    ATK_TRY(gemm_tn_f64(b.L, b.L, n, R, b.G, ss, st));
+    ATK_TRY(gemm_tn_f64(b.L, b.L, n, R, b.G, st));
     ATK_CUDA(cudaMemcpyAsync(b.Lt, b.L, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
     ATK_TRY(solve_spd_right_f64(b.Lt, n, R, b.G, ss, b.dev_status, st));
     ATK_TRY(f64_to_f32(b.Lt, b.Lt32, n * R, st));

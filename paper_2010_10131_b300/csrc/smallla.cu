@@ -7,6 +7,8 @@
 // only about 8 GFLOP/s.  So the products take float64 operands and results
 // but compute in float-float on the float32 pipe, spread over many CTAs;
 // only the O(R^3) factorisations run in float64 on a single CTA.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "atk_internal.cuh"
@@ -30,9 +32,11 @@ namespace atk {
 //
 // A CTA of 256 threads computes a 32 x 32 tile, 2 x 2 values per thread,
 // through 16-deep k tiles staged in shared memory (double-buffered).  With
-// splits > 1 each split of k writes a float64 partial tile (part[s] is
-// m x p) and dgemm_reduce_kernel sums the splits in order.
-constexpr int DG_T = 32, DG_K = 16, DG_THREADS = 256;
+// splits > 1 the splits of k for one tile form a thread-block cluster: each
+// CTA leaves its float64 partial tile in its shared memory, and after a
+// cluster barrier every CTA sums a share of the tile's elements over the
+// splits in rank order (a fixed order) through distributed shared memory.
+constexpr int DG_T = 32, DG_K = 16, DG_THREADS = 256, DG_MAXSPLIT = 8;
 
 struct FF {
   float hi, lo;
@@ -58,9 +62,10 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(DG_THREADS) dgemm_kernel(const double* __restrict__ A, int64_t lda,
                                                           const double* __restrict__ B, int64_t ldb, int64_t m,
                                                           int64_t k, int64_t p, int64_t kc, double* __restrict__ C,
-                                                          int64_t ldc, double* __restrict__ part) {
+                                                          int64_t ldc) {
   __shared__ float Ah[2][DG_K][DG_T + 1], Al[2][DG_K][DG_T + 1];
   __shared__ float Bh[2][DG_K][DG_T + 1], Bl[2][DG_K][DG_T + 1];
+  __shared__ double ptile[DG_T * DG_T];  // this split's partial tile, column-major
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
   const int64_t i0 = (int64_t)blockIdx.x * DG_T, c0 = (int64_t)blockIdx.y * DG_T;
   const int64_t kb = (int64_t)blockIdx.z * kc, ke = min(k, kb + kc);
@@ -122,73 +127,73 @@ __global__ void __launch_bounds__(DG_THREADS) dgemm_kernel(const double* __restr
       __syncthreads();
     }
   }
+  const int splits = (int)gridDim.z;
+  if (splits == 1) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int64_t gi = i0 + ty + 16 * u, gc = c0 + tx + 16 * v;
+        if (gi < m && gc < p) C[gi + ldc * gc] = (double)sh[u][v] + (double)sl[u][v];
+      }
+    return;
+  }
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const int64_t gi = i0 + ty + 16 * u, gc = c0 + tx + 16 * v;
-      if (gi < m && gc < p) {
-        const double r = (double)sh[u][v] + (double)sl[u][v];
-        if (part) part[((int64_t)blockIdx.z * p + gc) * m + gi] = r;
-        else C[gi + ldc * gc] = r;
-      }
-    }
-}
-
-__global__ void dgemm_reduce_kernel(const double* __restrict__ part, int splits, int64_t m, int64_t p,
-                                    double* __restrict__ C, int64_t ldc) {
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= m * p) return;
-  const int64_t i = o % m, c = o / m;
-  double s = 0.0;
-  for (int sp = 0; sp < splits; ++sp) s += part[(int64_t)sp * m * p + o];
-  C[i + ldc * c] = s;
+    for (int v = 0; v < 2; ++v) ptile[(ty + 16 * u) + DG_T * (tx + 16 * v)] = (double)sh[u][v] + (double)sl[u][v];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();  // every split's partial tile is written
+  for (int e = (int)cl.block_rank() * DG_THREADS + t; e < DG_T * DG_T; e += splits * DG_THREADS) {
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += cl.map_shared_rank(ptile, sp)[e];
+    const int64_t gi = i0 + e % DG_T, gc = c0 + e / DG_T;
+    if (gi < m && gc < p) C[gi + ldc * gc] = s;
+  }
+  cl.sync();  // the partial tiles stay in place until every CTA has read them
 }
 
 // op(A) op(B) with a split count for about two CTAs per SM (the grid has to
 // cover the chip: the tiles are small), limited by the k tiles and by the
-// partial buffer (part_cap doubles; nullptr = no split).
-// part must not overlap A, B or C.
+// cluster size (at most DG_MAXSPLIT splits, one cluster per output tile).
 template <bool TA, bool TB>
 static int dgemm(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int64_t k, int64_t p,
-                 double* C, int64_t ldc, double* part, int64_t part_cap, cudaStream_t st) {
+                 double* C, int64_t ldc, cudaStream_t st) {
   if (m <= 0 || p <= 0) return ATK_OK;
   const int64_t tiles = ceil_div(m, DG_T) * ceil_div(p, DG_T);
   int64_t splits = std::max<int64_t>(1, ceil_div(2 * (int64_t)num_sms(), tiles));
-  splits = std::min<int64_t>(splits, std::max<int64_t>(1, ceil_div(k, DG_K)));
-  if (!part) splits = 1;
-  else splits = std::min<int64_t>(splits, std::max<int64_t>(1, part_cap / (m * p)));
+  splits = std::min<int64_t>({splits, std::max<int64_t>(1, ceil_div(k, DG_K)), (int64_t)DG_MAXSPLIT});
   const int64_t kc = ceil_div(ceil_div(std::max<int64_t>(k, 1), splits), DG_K) * DG_K;
   splits = std::max<int64_t>(1, ceil_div(std::max<int64_t>(k, 1), kc));
-  dim3 grid((unsigned)ceil_div(m, DG_T), (unsigned)ceil_div(p, DG_T), (unsigned)splits);
-  dgemm_kernel<TA, TB><<<grid, DG_THREADS, 0, st>>>(A, lda, B, ldb, m, k, p, kc, C, ldc,
-                                                   splits > 1 ? part : nullptr);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ceil_div(m, DG_T), (unsigned)ceil_div(p, DG_T), (unsigned)splits);
+  cfg.blockDim = dim3(DG_THREADS);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = (unsigned)splits;
+  cfg.attrs = attr;
+  cfg.numAttrs = splits > 1 ? 1 : 0;
+  ATK_CUDA(cudaLaunchKernelEx(&cfg, dgemm_kernel<TA, TB>, A, lda, B, ldb, m, k, p, kc, C, ldc));
   ATK_LAUNCHED();
-  if (splits > 1) {
-    dgemm_reduce_kernel<<<(unsigned)ceil_div(m * p, 256), 256, 0, st>>>(part, (int)splits, m, p, C, ldc);
-    ATK_LAUNCHED();
-  }
   return ATK_OK;
 }
 
-constexpr int GT_CHUNK = 16;  // rows of A per CTA in A^T B
-
 size_t smallla_scratch_bytes(int64_t n, int64_t R) {
-  int64_t chunks = ceil_div(std::max<int64_t>(n, 1), GT_CHUNK);
-  // partials + three R x R matrices + an n x R panel, plus alignment slack
-  return sizeof(double) * (size_t)(chunks * R * R + 4 * R * R + 2 * n * R) + 4096;
+  // four R x R matrices + an n x R panel, plus alignment slack
+  return sizeof(double) * (size_t)(4 * R * R + 2 * n * R) + 4096;
 }
 
-// Doubles available for split partials at the head of the scratch.
-static int64_t part_cap(int64_t n, int64_t R) { return ceil_div(std::max<int64_t>(n, 1), GT_CHUNK) * R * R; }
-
-int gemm_tn_f64(const double* A, const double* B, int64_t n, int64_t R, double* G, double* scratch, cudaStream_t st) {
+int gemm_tn_f64(const double* A, const double* B, int64_t n, int64_t R, double* G, cudaStream_t st) {
   if (n == 0) {
     ATK_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * R * R, st));
     return ATK_OK;
   }
-  // G = A^T B, split over the n rows into partials at the head of the scratch.
-  return dgemm<true, false>(A, n, B, n, R, n, R, G, R, scratch, part_cap(n, R), st);
+  // G = A^T B, split over the n rows.
+  return dgemm<true, false>(A, n, B, n, R, n, R, G, R, st);
 }
 
 // One CTA: Cholesky G = C C^T (C lower), Cinv = C^{-1} (lower) and, if
@@ -255,9 +260,8 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict_
   }
 }
 
-int gemm_f64_split(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, double* part,
-                   int64_t part_cap, cudaStream_t st) {
-  return dgemm<false, false>(A, m, B, k, m, k, p, C, m, part, part_cap, st);
+int gemm_f64(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, cudaStream_t st) {
+  return dgemm<false, false>(A, m, B, k, m, k, p, C, m, st);
 }
 
 __global__ void polar_coef_kernel(const double* __restrict__ G, int64_t R, double* __restrict__ M) {
@@ -292,13 +296,11 @@ __global__ void rhat_kernel(const double* __restrict__ C1, const double* __restr
 
 namespace {
 struct SmallBufs {
-  double *part, *M1, *M2, *M3, *M4, *panel;
+  double *M1, *M2, *M3, *M4, *panel;
 };
 SmallBufs carve(double* scratch, int64_t n, int64_t R) {
   Arena ar{(char*)scratch, smallla_scratch_bytes(n, R), 0};
-  int64_t chunks = ceil_div(std::max<int64_t>(n, 1), GT_CHUNK);
   SmallBufs b;
-  b.part = (double*)ar.take(sizeof(double) * chunks * R * R);
   b.M1 = (double*)ar.take(sizeof(double) * R * R);
   b.M2 = (double*)ar.take(sizeof(double) * R * R);
   b.M3 = (double*)ar.take(sizeof(double) * R * R);
@@ -314,7 +316,7 @@ int solve_spd_right_f64(double* X, int64_t m, int64_t R, const double* G, double
   if (!b.panel) { set_error("solve_spd: scratch too small"); return ATK_EINVAL; }
   chol_inv_kernel<<<1, 256, 0, st>>>(G, (int)R, b.M1, b.M2, b.M3, dev_status);
   ATK_LAUNCHED();
-  ATK_TRY((dgemm<false, false>(X, m, b.M3, R, m, R, R, b.panel, m, b.part, part_cap(m, R), st)));
+  ATK_TRY((dgemm<false, false>(X, m, b.M3, R, m, R, R, b.panel, m, st)));
   ATK_CUDA(cudaMemcpyAsync(X, b.panel, sizeof(double) * m * R, cudaMemcpyDeviceToDevice, st));
   return ATK_OK;
 }
@@ -322,10 +324,10 @@ int solve_spd_right_f64(double* X, int64_t m, int64_t R, const double* G, double
 int polar_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_t st) {
   SmallBufs b = carve(scratch, n, R);
   if (!b.panel) { set_error("polar: scratch too small"); return ATK_EINVAL; }
-  ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, b.part, st));
+  ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, st));
   polar_coef_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M1, R, b.M2);
   ATK_LAUNCHED();
-  ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, b.part, part_cap(n, R), st)));
+  ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, st)));
   ATK_CUDA(cudaMemcpyAsync(U, b.panel, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
   return ATK_OK;
 }
@@ -333,10 +335,10 @@ int polar_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_
 int gs_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_t st) {
   SmallBufs b = carve(scratch, n, R);
   if (!b.panel) { set_error("gs_step: scratch too small"); return ATK_EINVAL; }
-  ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, b.part, st));
+  ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, st));
   gs_coef_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M1, R, b.M2);
   ATK_LAUNCHED();
-  ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, b.part, part_cap(n, R), st)));
+  ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, st)));
   ATK_CUDA(cudaMemcpyAsync(U, b.panel, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
   return ATK_OK;
 }
@@ -345,15 +347,15 @@ int cholqr2_f64(double* L, int64_t n, int64_t R, double* Rhat, double* scratch, 
   SmallBufs b = carve(scratch, n, R);
   if (!b.panel) { set_error("cholqr2: scratch too small"); return ATK_EINVAL; }
   // Pass 1: L^T L = C1 C1^T, Q1 = L C1^{-T}.
-  ATK_TRY(gemm_tn_f64(L, L, n, R, b.M1, b.part, st));
+  ATK_TRY(gemm_tn_f64(L, L, n, R, b.M1, st));
   chol_inv_kernel<<<1, 256, 0, st>>>(b.M1, (int)R, b.M2, b.M3, nullptr, dev_status);
   ATK_LAUNCHED();
-  ATK_TRY((dgemm<false, true>(L, n, b.M3, R, n, R, R, b.panel, n, b.part, part_cap(n, R), st)));
+  ATK_TRY((dgemm<false, true>(L, n, b.M3, R, n, R, R, b.panel, n, st)));
   // Pass 2 on Q1: Q1^T Q1 = C2 C2^T, Q = Q1 C2^{-T}.
-  ATK_TRY(gemm_tn_f64(b.panel, b.panel, n, R, b.M1, b.part, st));
+  ATK_TRY(gemm_tn_f64(b.panel, b.panel, n, R, b.M1, st));
   chol_inv_kernel<<<1, 256, 0, st>>>(b.M1, (int)R, b.M4, b.M3, nullptr, dev_status);
   ATK_LAUNCHED();
-  ATK_TRY((dgemm<false, true>(b.panel, n, b.M3, R, n, R, R, L, n, b.part, part_cap(n, R), st)));
+  ATK_TRY((dgemm<false, true>(b.panel, n, b.M3, R, n, R, R, L, n, st)));
   rhat_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M2, b.M4, R, Rhat);
   ATK_LAUNCHED();
   return ATK_OK;
