@@ -14,6 +14,7 @@
 //    is a persistent cooperative kernel with a bounded grid barrier between
 //    phases.
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <vector>
 
@@ -219,61 +220,64 @@ __global__ void __launch_bounds__(256) jacobi_block_kernel(BlockJacobiArgs args,
 // row), write U (n x R column-major, float64), all eigenvalues (descending)
 // and the discarded sum.  One CTA.  V is row-major with leading dimension ldv.
 template <typename T>
-__global__ void __launch_bounds__(1024) select_kernel(const T* __restrict__ diag, int64_t dstride,
-                                                      const T* __restrict__ V, int ldv, int n, int R,
-                                                      double* __restrict__ U, double* __restrict__ lam_out,
-                                                      double* __restrict__ disc_out) {
+__global__ void __launch_bounds__(256) select_kernel(const T* __restrict__ diag, int64_t dstride,
+                                                     const T* __restrict__ V, int ldv, int n, int R,
+                                                     double* __restrict__ U, double* __restrict__ lam_out,
+                                                     double* __restrict__ disc_out) {
   __shared__ int order[1024];
-  __shared__ double lam[1024];
-  __shared__ double red[1024];
+  __shared__ T lam[1024];
+  __shared__ double wsum[8];
   // Sort key: the eigenvalue, with NaN ordered below everything, ties broken by
   // index.  That is a total order, so the ranks below are a permutation of
   // 0..n-1 whatever the input holds, and every gathered column stays in range.
+  // The comparisons run in T (float32 keys need no float64 pipe).
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = (double)diag[(int64_t)i * dstride];
-    lam[i] = isnan(v) ? -INFINITY : v;
-    order[i] = i;
+    const T v = diag[(int64_t)i * dstride];
+    lam[i] = isnan(v) ? -(T)INFINITY : v;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double li = lam[i];
+    const T li = lam[i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      double lj = lam[j];
+      const T lj = lam[j];
       rank += (lj > li) || (lj == li && j < i);
     }
     order[rank] = i;
   }
   __syncthreads();
   if (lam_out)
-    for (int r = threadIdx.x; r < n; r += blockDim.x) lam_out[r] = lam[order[r]];
-  // Discarded energy: fixed-order tree sum of the eigenvalues beyond R.
-  double loc = 0.0;
-  for (int r = R + threadIdx.x; r < n; r += blockDim.x) loc += lam[order[r]];
-  red[threadIdx.x] = loc;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && disc_out) *disc_out = red[0];
-  // One warp per selected column.
+    for (int r = threadIdx.x; r < n; r += blockDim.x) lam_out[r] = (double)lam[order[r]];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  if (disc_out) {
+    // Discarded energy: per-thread strided sums, then a fixed-order tree.
+    double loc = 0.0;
+    for (int r = R + threadIdx.x; r < n; r += blockDim.x) loc += (double)lam[order[r]];
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
+    if (lane == 0) wsum[warp] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += wsum[w];
+      *disc_out = s;
+    }
+  }
+  // One warp per selected column; the sign rule compares in T.
   for (int r = warp; r < R; r += nw) {
-    int col = order[r];
-    double best = -1.0;
+    const int col = order[r];
+    T best = (T)-1;
     int arg = 0;
     for (int i = lane; i < n; i += 32) {
-      double a = fabs((double)V[(int64_t)i * ldv + col]);
+      const T a = fabs(V[(int64_t)i * ldv + col]);
       if (a > best) { best = a; arg = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_down_sync(0xffffffffu, best, o);
-      int oa = __shfl_down_sync(0xffffffffu, arg, o);
+      const T ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oa = __shfl_down_sync(0xffffffffu, arg, o);
       if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
     }
     arg = __shfl_sync(0xffffffffu, arg, 0);
-    double sg = ((double)V[(int64_t)arg * ldv + col] < 0.0) ? -1.0 : 1.0;
+    const double sg = (V[(int64_t)arg * ldv + col] < (T)0) ? -1.0 : 1.0;
     for (int i = lane; i < n; i += 32) U[i + (int64_t)n * r] = sg * (double)V[(int64_t)i * ldv + col];
   }
 }
@@ -345,7 +349,7 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
     ATK_TRY(raise_smem_limit((const void*)jacobi_small_kernel<T>, sm));
     jacobi_small_kernel<T><<<1, 256, sm, st>>>(S, (int)n, m, max_sweeps, diag, V, dev_status);
     ATK_LAUNCHED();
-    select_kernel<T><<<1, 1024, 0, st>>>(diag, 1, V, (int)n, (int)n, (int)R, U64, lam_out, nullptr);
+    select_kernel<T><<<1, 256, 0, st>>>(diag, 1, V, (int)n, (int)n, (int)R, U64, lam_out, nullptr);
     ATK_LAUNCHED();
     return ATK_OK;
   }
@@ -388,7 +392,7 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
   void* kargs[] = {(void*)&args, (void*)&A, (void*)&V, (void*)&W, (void*)&fro};
   ATK_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_block_kernel<T>, dim3(grid), dim3(256), kargs, sm, st));
   count_launch();
-  select_kernel<T><<<1, 1024, 0, st>>>(A, (int64_t)m + 1, V, m, (int)n, (int)R, U64, lam_out, nullptr);
+  select_kernel<T><<<1, 256, 0, st>>>(A, (int64_t)m + 1, V, m, (int)n, (int)R, U64, lam_out, nullptr);
   ATK_LAUNCHED();
   return ATK_OK;
 }
@@ -565,9 +569,16 @@ __global__ void ritz_residual_kernel(const float* __restrict__ Z, const float* _
 // broke down since the last summary (the flag is cleared).
 __global__ void ritz_summary_kernel(const double* __restrict__ res, const double* __restrict__ theta, int R, int m,
                                     int* __restrict__ breakdown, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
+  // One warp: the lanes take strided residuals (independent loads), then a
+  // max over the warp; NaN wins (a NaN residual must reach the host).
+  const int lane = threadIdx.x;
   double w = 0.0;
-  for (int j = 0; j < R; ++j) w = (res[j] > w || res[j] != res[j]) ? res[j] : w;
+  for (int j = lane; j < R; j += 32) w = (res[j] > w || res[j] != res[j]) ? res[j] : w;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ow = __shfl_xor_sync(0xffffffffu, w, o);
+    w = (ow > w || ow != ow) ? ow : w;
+  }
+  if (lane != 0) return;
   out[0] = w;
   out[1] = theta[0];
   out[2] = theta[R - 1];
@@ -693,7 +704,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
       ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Z, b, s2));
       ATK_TRY(cross_f32(b.Q, qv, b.Z, m, b.G, b.part, b.part_bytes, s2));
       ATK_TRY(tridiag_eig_f32(b.G, m, b.diag, b.Vb, s2));
-      select_kernel<float><<<1, 1024, 0, s2>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
+      select_kernel<float><<<1, 256, 0, s2>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
       ATK_LAUNCHED();
       ATK_TRY(f64_to_f32(b.W64, b.Wf, (int64_t)mm, s2));
       ATK_TRY(ttm_f32(b.Q, qv, b.Wf, m, b.Y, s2));
@@ -775,39 +786,47 @@ __global__ void __launch_bounds__(256) order_diag_kernel(const double* __restric
                                                          const double* __restrict__ S, int64_t n,
                                                          int* __restrict__ order, double* __restrict__ lam_out,
                                                          double* __restrict__ disc_out) {
-  __shared__ double key[1024];
+  // Ranks by an integer key that orders like the float64 value (sign-folded
+  // bit pattern; NaN lowest), so the k^2 comparisons stay off the float64
+  // pipe; ties by index.
+  __shared__ long long key[1024];
   __shared__ int ord[1024];
-  __shared__ double red[256];
+  __shared__ double wsum[8], lam_s[128];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double v = B[i + (int64_t)k * i];
-    key[i] = isnan(v) ? -INFINITY : v;
-    ord[i] = i;
+    const double v = B[i + (int64_t)k * i];
+    const long long b = __double_as_longlong(v);
+    key[i] = isnan(v) ? LLONG_MIN : (b >= 0 ? b : (long long)((unsigned long long)b ^ 0x7fffffffffffffffULL));
   }
   __syncthreads();
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double li = key[i];
+    const long long li = key[i];
     int rank = 0;
     for (int j = 0; j < k; ++j) rank += (key[j] > li) || (key[j] == li && j < i);
     ord[rank] = i;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < k; r += blockDim.x) order[r] = ord[r];
+  // trace(S): per-thread strided sums, then a fixed-order tree.
   double part = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) part += S[i + n * i];
-  red[threadIdx.x] = part;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) wsum[warp] = part;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const double l = B[ord[r] + (int64_t)k * ord[r]];
+    lam_s[r] = l;
+    if (lam_out) lam_out[r] = l;
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  if (warp == 0 && disc_out) {
     double kept = 0.0;
-    for (int r = 0; r < R; ++r) {
-      double l = B[ord[r] + (int64_t)k * ord[r]];
-      kept += l;
-      if (lam_out) lam_out[r] = l;
+    for (int r = lane; r < R; r += 32) kept += lam_s[r];
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if (lane == 0) {
+      double tr = 0.0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) tr += wsum[w];
+      *disc_out = tr - kept;
     }
-    if (disc_out) *disc_out = red[0] - kept;
   }
 }
 
@@ -969,13 +988,15 @@ __global__ void normalize_cols_kernel(const double* __restrict__ Z, const double
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   if (warp >= R) return;
   double mx = 0.0;
-  for (int64_t r = 0; r < R; ++r) mx = fmax(mx, norms[r]);
+  for (int64_t r = lane; r < R; r += 32) mx = fmax(mx, norms[r]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const double thr = rel * mx;
   const double* z = Z + (int64_t)warp * n;
   double nz = norms[warp];
   double* w = W + (int64_t)warp * n;
   if (nz > thr && (!dots || dots[warp] >= min_ratio * nz)) {
-    for (int64_t i = lane; i < n; i += 32) w[i] = z[i] / nz;
+    const double inv = 1.0 / nz;
+    for (int64_t i = lane; i < n; i += 32) w[i] = z[i] * inv;
   } else {
     const double* u = U + (int64_t)warp * n;
     for (int64_t i = lane; i < n; i += 32) w[i] = u[i];
