@@ -66,7 +66,12 @@ def gram_flops(dims, ranks, solver, mode_order=None):
 
 
 class ClockSampler:
-    """nvidia-smi clocks during the timed region."""
+    """nvidia-smi clocks during the timed region.
+
+    The sampler starts first and the region begins only after its first
+    sample; the samples kept run from the last one before the region to the
+    first one after it (20 ms apart), so even a region of a few tens of ms
+    is covered."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -76,14 +81,22 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = self.last = 0
+
+    def _wait_lines(self, count, timeout):
+        t_end = time.time() + timeout
+        while len(self.lines) < count and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.002)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self._wait_lines(1, 5.0)
+            self.first = max(0, len(self.lines) - 1)
         except OSError:
             self.proc = None
         return self
@@ -94,6 +107,8 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         if self.proc:
+            self._wait_lines(len(self.lines) + 1, 1.0)
+            self.last = len(self.lines)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -103,7 +118,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.first:self.last]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
