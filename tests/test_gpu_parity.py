@@ -86,7 +86,8 @@ def _rr_used(n, R, arith, method):
 @pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("arith", [0, 1])
 @pytest.mark.parametrize("n,R", [(2, 1), (5, 2), (33, 8), (96, 8), (128, 16), (130, 16), (200, 20), (640, 64),
-                                 (1000, 128), (150, 40), (200, 72), (240, 100)])
+                                 (1000, 128), (150, 40), (200, 72), (240, 100), (70, 22), (140, 49),
+                                 (200, 81), (260, 113)])
 def test_eig_matches_oracle(atk, n, R, arith, method):
     if arith == 1 and n > 200:
         pytest.skip("float64 rotations at n >= 640 are slow on B300 (covered at 200)")
