@@ -58,7 +58,23 @@ __device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, f
   sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
 
-template <bool TA, bool TB>
+// BX transforms op(B) = G (k x p, k = p) as it is staged, so the coefficient
+// matrix of an orthonormalisation step never goes through memory:
+//  - DG_POLAR: M = (3I - G) / 2, the Newton-Schulz polar coefficient.
+//  - DG_GS: with G = U^T U = I + E, M = I - strict_upper(E) - diag(E) / 2
+//    (upper triangular).  U M has column i built from columns j <= i only,
+//    and (U M)^T (U M) = I + O(E^2): one step of an iteration that converges
+//    quadratically like Newton-Schulz but, like Gram-Schmidt, never mixes a
+//    later column into an earlier one.
+enum { DG_PLAIN = 0, DG_POLAR = 1, DG_GS = 2 };
+template <int BX>
+__device__ __forceinline__ double dg_bx(double g, int64_t i, int64_t j) {
+  if (BX == DG_POLAR) return (i == j ? 1.5 : 0.0) - 0.5 * g;
+  if (BX == DG_GS) return i == j ? 1.0 - 0.5 * (g - 1.0) : (i < j ? -g : 0.0);
+  return g;
+}
+
+template <bool TA, bool TB, int BX = DG_PLAIN>
 __global__ void __launch_bounds__(DG_THREADS) dgemm_kernel(const double* __restrict__ A, int64_t lda,
                                                           const double* __restrict__ B, int64_t ldb, int64_t m,
                                                           int64_t k, int64_t p, int64_t kc, double* __restrict__ C,
@@ -88,7 +104,7 @@ __global__ void __launch_bounds__(DG_THREADS) dgemm_kernel(const double* __restr
       b_at(e, kb2, cc);
       const int64_t gi = i0 + ii, gk = k0 + kk, gc = c0 + cc, gk2 = k0 + kb2;
       ra[e] = (gi < m && gk < ke) ? (TA ? A[gk + lda * gi] : A[gi + lda * gk]) : 0.0;
-      rb[e] = (gc < p && gk2 < ke) ? (TB ? B[gc + ldb * gk2] : B[gk2 + ldb * gc]) : 0.0;
+      rb[e] = (gc < p && gk2 < ke) ? dg_bx<BX>(TB ? B[gc + ldb * gk2] : B[gk2 + ldb * gc], gk2, gc) : 0.0;
     }
   };
   auto store = [&](int buf) {
@@ -157,7 +173,7 @@ __global__ void __launch_bounds__(DG_THREADS) dgemm_kernel(const double* __restr
 // op(A) op(B) with a split count for about two CTAs per SM (the grid has to
 // cover the chip: the tiles are small), limited by the k tiles and by the
 // cluster size (at most DG_MAXSPLIT splits, one cluster per output tile).
-template <bool TA, bool TB>
+template <bool TA, bool TB, int BX = DG_PLAIN>
 static int dgemm(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int64_t k, int64_t p,
                  double* C, int64_t ldc, cudaStream_t st) {
   if (m <= 0 || p <= 0) return ATK_OK;
@@ -177,7 +193,7 @@ static int dgemm(const double* A, int64_t lda, const double* B, int64_t ldb, int
   attr[0].val.clusterDim.z = (unsigned)splits;
   cfg.attrs = attr;
   cfg.numAttrs = splits > 1 ? 1 : 0;
-  ATK_CUDA(cudaLaunchKernelEx(&cfg, dgemm_kernel<TA, TB>, A, lda, B, ldb, m, k, p, kc, C, ldc));
+  ATK_CUDA(cudaLaunchKernelEx(&cfg, dgemm_kernel<TA, TB, BX>, A, lda, B, ldb, m, k, p, kc, C, ldc));
   ATK_LAUNCHED();
   return ATK_OK;
 }
@@ -264,25 +280,6 @@ int gemm_f64(const double* A, const double* B, int64_t m, int64_t k, int64_t p, 
   return dgemm<false, false>(A, m, B, k, m, k, p, C, m, st);
 }
 
-__global__ void polar_coef_kernel(const double* __restrict__ G, int64_t R, double* __restrict__ M) {
-  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= R * R) return;
-  M[o] = ((o % R == o / R) ? 1.5 : 0.0) - 0.5 * G[o];
-}
-
-// Gram-Schmidt-ordered counterpart of the polar coefficient: with
-// G = U^T U = I + E, T = I - strict_upper(E) - diag(E) / 2 (upper triangular).
-// U T has column i built from columns j <= i only, and (U T)^T (U T) =
-// I + O(E^2): one step of an iteration that converges quadratically like
-// Newton-Schulz but, like Gram-Schmidt, never mixes a later column into an
-// earlier one.
-__global__ void gs_coef_kernel(const double* __restrict__ G, int64_t R, double* __restrict__ M) {
-  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= R * R) return;
-  const int64_t i = o % R, j = o / R;
-  M[o] = i == j ? 1.0 - 0.5 * (G[o] - 1.0) : (i < j ? -G[o] : 0.0);
-}
-
 // Rhat = C2^T C1^T (both factors lower), i.e. the product of the two upper factors.
 __global__ void rhat_kernel(const double* __restrict__ C1, const double* __restrict__ C2, int64_t R,
                             double* __restrict__ Rhat) {
@@ -325,9 +322,7 @@ int polar_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_
   SmallBufs b = carve(scratch, n, R);
   if (!b.panel) { set_error("polar: scratch too small"); return ATK_EINVAL; }
   ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, st));
-  polar_coef_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M1, R, b.M2);
-  ATK_LAUNCHED();
-  ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, st)));
+  ATK_TRY((dgemm<false, false, DG_POLAR>(U, n, b.M1, R, n, R, R, b.panel, n, st)));
   ATK_CUDA(cudaMemcpyAsync(U, b.panel, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
   return ATK_OK;
 }
@@ -336,9 +331,7 @@ int gs_step_f64(double* U, int64_t n, int64_t R, double* scratch, cudaStream_t s
   SmallBufs b = carve(scratch, n, R);
   if (!b.panel) { set_error("gs_step: scratch too small"); return ATK_EINVAL; }
   ATK_TRY(gemm_tn_f64(U, U, n, R, b.M1, st));
-  gs_coef_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M1, R, b.M2);
-  ATK_LAUNCHED();
-  ATK_TRY((dgemm<false, false>(U, n, b.M2, R, n, R, R, b.panel, n, st)));
+  ATK_TRY((dgemm<false, false, DG_GS>(U, n, b.M1, R, n, R, R, b.panel, n, st)));
   ATK_CUDA(cudaMemcpyAsync(U, b.panel, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
   return ATK_OK;
 }
