@@ -7,7 +7,7 @@ Every step here is a call into the CUDA library: features come from
 plans created with solver ``AUTO`` run the library's host-side inference
 (``atucker_selector_predict``).  This module only marshals data.
 
-Labels are measured by this build: for each shape, every mode is timed under
+Labels are measured with the library's own kernels: for each shape, every mode is timed under
 every class (CUDA events around each mode inside the plan), and the network
 learns, per class, y = log2(t_class / t_fastest) (capped at 4, i.e. 16x).  The
 selector takes the class with the smallest prediction.
