@@ -147,7 +147,7 @@ def test_gpu_adam_steps_follow_oracle():
 def test_trained_selector_beats_the_method_without_it():
     """Trained on the committed timing sets with the library's kernels, the
     selector's choices on the 64 held-out shapes cost less time (as measured by
-    this build, per mode) than the fixed policies: every mode EIG (the method
+    the library, per mode) than the fixed policies: every mode EIG (the method
     without a selector), every mode ALS, every mode full Jacobi."""
     _gpu()
     from paper_2010_10131_b300 import selector
