@@ -7,13 +7,13 @@
 //     Computations, 4th ed., Alg. 8.3.1): step j reflects column j below the
 //     diagonal with H_j = I - tau_j v_j v_j^T (v_j(j+1) = 1), p = tau A22 v,
 //     w = p - (tau/2)(p^T v) v, A22 <- A22 - v w^T - w v^T.  A lives in
-//     registers for the whole reduction: warp w holds the rows i = w (mod 16),
-//     lane l the columns k = l (mod 32), so p is a register product plus a
-//     butterfly sum over the warp, and the update touches no shared memory.
-//     Two barriers per step: one after p and the per-warp partials of p^T v,
-//     one after the owners of column j+1 have published it (and the partial
-//     sums of its squared norm below row j+2, from which every thread derives
-//     the next reflector).
+//     registers for the whole reduction: WH warps (8 for m <= 96, else 16),
+//     lane (rs, cg) of warp w holding the rows w + WH (rs + 2 s) and the
+//     columns cg + 16 t, so p is a register product plus a butterfly over 16
+//     lanes, and the update touches no shared memory.  Two barriers per step:
+//     one after p and the per-warp partials of p^T v, one after the owners of
+//     column j+1 have published it (and the partial sums of its squared norm
+//     below row j+2, from which every thread derives the next reflector).
 //  2. Eigenvalues of T by multisection on the Sturm count (ibid., Sec. 8.4.1):
 //     one Sturm count per thread on a grid of 512 points across the
 //     Gershgorin interval brackets every eigenvalue to 1/513 of it; then G
