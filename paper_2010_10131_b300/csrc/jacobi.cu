@@ -743,9 +743,9 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
 }
 
 // ----------------------------------------------------- float64 refinement
-__global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n,
-                                      int64_t R, const double* __restrict__ norms, const double* __restrict__ dots,
-                                      double rel, double min_ratio, double* __restrict__ W);
+__global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* U, int64_t n, int64_t R,
+                                      const double* __restrict__ norms, const double* __restrict__ dots, double rel,
+                                      double min_ratio, double* W);
 __global__ void colnorms_f64_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n, int64_t R,
                                     double* __restrict__ norms, double* __restrict__ dots);
 __global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R);
@@ -981,10 +981,11 @@ __global__ void colnorms_f64_kernel(const double* __restrict__ Z, const double* 
 // null-space or small-eigenvalue Ritz vector with float32 errors along the
 // leading directions) is not improved by S u; normalising would turn that
 // leakage into a near copy of a leading direction.  Such columns keep their
-// vectors.  One warp per column.
-__global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n,
-                                      int64_t R, const double* __restrict__ norms, const double* __restrict__ dots,
-                                      double rel, double min_ratio, double* __restrict__ W) {
+// vectors.  One warp per column; W may be U (each element is read and then
+// written by the same thread).
+__global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* U, int64_t n, int64_t R,
+                                      const double* __restrict__ norms, const double* __restrict__ dots, double rel,
+                                      double min_ratio, double* W) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   if (warp >= R) return;
   double mx = 0.0;
