@@ -82,8 +82,14 @@ typedef enum {
  *   ATK_FP8E4M3  each mode-n row i scaled by the power of two
  *                s_i = 2^floor(log2(448 / max |row i|)), rounded to e4m3; the
  *                product is divided by s_i s_j exactly afterwards
+ *   ATK_FP32C    float32 on the CUDA cores with compensated sums: every
+ *                product made exact (p + e with e = fma(a, b, -p)) and the
+ *                running sum carried as a float-float pair (TwoSum), about
+ *                48 bits per partial sum at about nine times the float32 cost
  * The eigensolver, TTM, ALS and orthonormalisation are unchanged. */
-typedef enum { ATK_FP32 = 0, ATK_TF32 = 1, ATK_BF16 = 2, ATK_BF16X3 = 3, ATK_FP8E4M3 = 4 } atucker_precision;
+typedef enum {
+  ATK_FP32 = 0, ATK_TF32 = 1, ATK_BF16 = 2, ATK_BF16X3 = 3, ATK_FP8E4M3 = 4, ATK_FP32C = 5
+} atucker_precision;
 
 /* Arithmetic of the Jacobi rotations in the eigensolver.  Either way, the
  * Gram arrives in float64, and eigenvalue sums and the final
@@ -110,7 +116,18 @@ typedef enum {
   ATK_OPT_SYNC = 2,       /* 1: atucker_sthosvd synchronises and returns the device status (default 0) */
   ATK_OPT_JACOBI_MAX_SWEEPS = 3, /* sweep cap of the Jacobi eigensolver (default 40) */
   ATK_OPT_TIMING = 4,     /* 1: record CUDA events around each phase (see atucker_plan_timings) */
-  ATK_OPT_EIG_METHOD = 5  /* atucker_eig_method; default ATK_EIG_AUTO */
+  ATK_OPT_EIG_METHOD = 5, /* atucker_eig_method; default ATK_EIG_AUTO */
+  /* Precise Gram for a cut that float32 does not resolve (float32 rotations).
+   * When the Gram's largest eigenvalue times LEVEL (64 eps_32) exceeds the
+   * gap between the R-th and the next Rayleigh quotient, a float32 Gram
+   * cannot decide which vectors lie on either side of the cut: its rounding
+   * reaches eps_32 times the largest partial sum.  The mode's Gram is then
+   * recomputed in ATK_FP32C and solved again.  0: never; 1 (default): every
+   * EIG mode but the first processed one (that mode reads the caller's
+   * tensor, whose entries are of comparable size, so its float32 roundings
+   * stay independent and small; later modes read the shrinking core, whose
+   * energy sits in few entries); 2: every EIG mode. */
+  ATK_OPT_GRAM_REFINE = 6
 } atucker_option;
 
 typedef struct atucker_plan_s* atucker_plan_t;
@@ -312,7 +329,7 @@ int atucker_plan_classes(atucker_plan_t plan, int* class_out);
 int atucker_plan_mode_timings(atucker_plan_t plan, double* ms_out, int count);
 
 /* ---------------------------------------------------------------------------
- * Learned per-mode selector (the paper's adaptive solver selection, Sec. IV-C,
+ * Learned per-mode selector (the paper's adaptive solver selection, Sec. IV,
  * with an MLP in place of the decision tree).
  *
  * Features of mode n when it is processed (Table I's ten, plus two):

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: imported by ``tests/`` (and nothing on the product
 path).  It shares no code with the CUDA library.
 
-The selector (the paper's adaptive solver selection, Sec. IV-C, with a small
+The selector (the paper's adaptive solver selection, Sec. IV, with a small
 network in place of its decision tree) maps 12 mode features to one score per
 class with a multilayer perceptron:
 

@@ -15,7 +15,7 @@ import re
 
 __all__ = [
     "lib", "abi_symbols", "AtuckerError", "Plan", "Batch", "sthosvd", "gram", "ttm", "eig", "als_mode",
-    "EIG", "ALS", "FP32", "TF32", "BF16", "BF16X3", "FP8E4M3", "EIG_ROT_FP32", "EIG_ROT_FP64",
+    "EIG", "ALS", "FP32", "TF32", "BF16", "BF16X3", "FP8E4M3", "FP32C", "EIG_ROT_FP32", "EIG_ROT_FP64",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -25,9 +25,9 @@ HEADER = os.path.join(_ROOT, "include", "atucker.h")
 
 OK, EINVAL, ERANK, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 EIG, ALS = 0, 1
-FP32, TF32, BF16, BF16X3, FP8E4M3 = 0, 1, 2, 3, 4
+FP32, TF32, BF16, BF16X3, FP8E4M3, FP32C = 0, 1, 2, 3, 4, 5
 EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
-OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD = 1, 2, 3, 4, 5
+OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD, OPT_GRAM_REFINE = 1, 2, 3, 4, 5, 6
 EIG_AUTO, EIG_FULL_JACOBI, EIG_SUBSPACE = 0, 1, 2
 BATCH_OPT_VARIANT, BATCH_OPT_GRAPH, BATCH_OPT_SYNC, BATCH_OPT_JACOBI_MAX_SWEEPS = 1, 2, 3, 4
 AUTO = -1
@@ -158,7 +158,7 @@ class Plan:
 
     def __init__(self, dims, ranks, mode_order=None, solver=None, precision: int = FP32, als_sweeps: int = 5,
                  seed: int = 0, stream=None, eig_arith: int | None = None, sync: bool = False,
-                 eig_method: int | None = None, classes=None):
+                 eig_method: int | None = None, classes=None, gram_refine: int | None = None):
         """solver: per-mode EIG / ALS / AUTO (learned selector); classes: per-mode
         atucker_mode_class values instead (atucker_plan_create_classes)."""
         self.dims = [int(d) for d in dims]
@@ -183,6 +183,8 @@ class Plan:
             _check(lib().atucker_plan_set_option(self._h, OPT_SYNC, 1), "set_option")
         if eig_method is not None:
             _check(lib().atucker_plan_set_option(self._h, OPT_EIG_METHOD, int(eig_method)), "set_option")
+        if gram_refine is not None:
+            _check(lib().atucker_plan_set_option(self._h, OPT_GRAM_REFINE, int(gram_refine)), "set_option")
 
     @property
     def core_numel(self):
@@ -300,12 +302,13 @@ def run_many_host(plans, xs_host, cores_host, factors_host, discarded_host=None)
 
 def sthosvd(x, dims, ranks, mode_order=None, solver=None, als_sweeps: int = 5, seed: int = 0,
             eig_arith: int | None = None, with_discarded: bool = False, eig_method: int | None = None,
-            precision: int = FP32):
+            precision: int = FP32, gram_refine: int | None = None):
     """Decompose the column-major tensor x (flat CUDA float32).
 
     Returns (core_flat, [U^(n)], discarded or None)."""
     torch = _torch()
-    p = Plan(dims, ranks, mode_order, solver, precision, als_sweeps, seed, eig_arith=eig_arith, eig_method=eig_method)
+    p = Plan(dims, ranks, mode_order, solver, precision, als_sweeps, seed, eig_arith=eig_arith, eig_method=eig_method,
+             gram_refine=gram_refine)
     disc = torch.zeros(len(dims), device=x.device, dtype=torch.float64) if with_discarded else None
     core, fac = p.run(x, discarded=disc)
     p.sync()

@@ -166,6 +166,12 @@ size_t cross_scratch_bytes(const View& v, int64_t R);
 int cross_f32(const float* y, const View& v, const float* P, int64_t R, double* C, float* scratch,
               size_t scratch_bytes, cudaStream_t st);
 
+// Compensated Gram (gram_cmp.cu): exact float32 products summed as
+// float-float pairs (about 48 bits per partial sum); the split count adapts
+// to scratch_bytes (at least one split must fit).
+size_t gram_cmp_scratch_bytes(const View& v);
+int gram_cmp(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st);
+
 // Tensor-core Gram (tc_ops.cu): precision is ATK_TF32, ATK_BF16, ATK_BF16X3 or
 // ATK_FP8E4M3.  Bounded waits report DEV_TIMEOUT through *status.
 size_t tc_gram_scratch_bytes(const View& v, int precision);
@@ -176,9 +182,12 @@ int tc_gram(const float* y, const View& v, int precision, double* S, float* scra
 size_t eig_scratch_bytes(int64_t n, int arith);
 // method: ATK_EIG_AUTO (Rayleigh-Ritz when R + p <= n/2, else full Jacobi),
 // ATK_EIG_FULL_JACOBI, ATK_EIG_SUBSPACE.
+// With `unresolved` given, a level-0 cut that float32 arithmetic on S does
+// not resolve sets *unresolved = 1 and returns at once (the caller recomputes
+// S more precisely and calls again); otherwise the deflation levels run.
 int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, float* U_out,
             double* U64_out, double* lambda_out, double* discarded_out, int* dev_status, char* scratch,
-            size_t scratch_bytes, cudaStream_t st);
+            size_t scratch_bytes, cudaStream_t st, int* unresolved = nullptr);
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (never
 // lowers it; thread-safe).  Call outside stream capture.

@@ -474,24 +474,33 @@ int run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
 //     shifted CholeskyQR3;
 //  2. a Rayleigh-Ritz projection B = Q^T S Q diagonalised by the one-CTA
 //     tridiagonal eigensolver (tridiag_eig.cu), giving Ritz vectors Q W;
-//  3. further steps restarting from the Ritz vectors (S Q W = Z W is
-//     already at hand, two CholeskyQR passes suffice) until the predicted
-//     error after the float64 refinement,
-//       (theta_m / theta_R) * max_{j<R} ||S q_j - theta_j q_j|| / (theta_R - theta_m),
+//  3. power steps from the Ritz vectors (S Q W = Z W is already at hand, two
+//     CholeskyQR passes suffice) and further Rayleigh-Ritz projections until
+//     the predicted error after the float64 refinement,
+//       (theta_m / theta_K) * max_{j<K} ||S q_j - theta_j q_j|| / (theta_K - theta_m),
 //     drops below RR_TARGET.  That is a Davis-Kahan bound on the angle
-//     between q_R and the leading space, times the contraction of the
-//     refinement's subspace step.
-// When theta_m / theta_R > RR_SLOW_RATIO (the R-th eigenvalue sits in a
-// cluster, so subspace iteration would crawl) or RR_MAXIT projections pass,
-// the full Jacobi runs instead.  Every product runs on the contraction engine
-// of fp32_ops.cu: the n x m block is the mode-2 view (lo = n, I = m, hi = 1)
-// of an n x m column-major matrix.
-constexpr int RR_MAXIT = 16;
+//     between q_K and the leading space, times the contraction of the
+//     refinement's subspace step.  K is R, or fewer: Ritz values below
+//     RR_RESOLVE eps_32 theta_1 are not resolved by float32 products at all,
+//     so they take no part in the test (eig_top resolves them on a deflated
+//     matrix).  Between two projections the path takes as many power steps
+//     as the observed rate theta_m / theta_K predicts (at most RR_POWER_CHUNK).
+// When theta_m / theta_K > RR_MAX_RATE (the cut sits inside a cluster that
+// the block does not cover) or RR_MAX_POWER power steps pass, the full
+// Jacobi runs instead.  Every product runs on the contraction engine of
+// fp32_ops.cu: the n x m block is the mode-2 view (lo = n, I = m, hi = 1) of
+// an n x m column-major matrix.
+constexpr int RR_MAX_POWER = 160;
+constexpr int RR_POWER_CHUNK = 8;
 constexpr double RR_TARGET = 1e-6;
-constexpr double RR_SLOW_RATIO = 0.5;
+constexpr double RR_MAX_RATE = 0.92;
+constexpr float RR_RESOLVE = 32.f * 1.1920929e-7f;
 
-int rr_width(int64_t n, int64_t R) {
-  int64_t p = std::max<int64_t>(8, std::min<int64_t>(16, R / 2));
+// Block width m = R + p.  The default guard p = clamp(R / 2, 8, 16) suits a
+// spectrum with a gap at the cut; `wide` (the deflated levels of eig_top,
+// where the cut lies in a slowly decaying tail) takes p = max(32, R).
+int rr_width(int64_t n, int64_t R, bool wide) {
+  int64_t p = wide ? std::max<int64_t>(32, R) : std::max<int64_t>(8, std::min<int64_t>(16, R / 2));
   return (int)std::min<int64_t>(std::min<int64_t>(n, R + p), 156);
 }
 
@@ -564,16 +573,24 @@ __global__ void ritz_residual_kernel(const float* __restrict__ Z, const float* _
   if (lane == 0) res[j] = sqrt(s);
 }
 
-// out[0] = max_j res[j] (NaN if any residual is NaN), out[1] = theta[0],
-// out[2] = theta[R-1], out[3] = theta[m-1], out[4] = 1 if a CholeskyQR pass
-// broke down since the last summary (the flag is cleared).
+// K = the number of leading Ritz values (theta descending) at or above
+// RR_RESOLVE theta_0, at most R.  out[0] = max_{j<K} res[j] (NaN if any is
+// NaN), out[1] = theta[0], out[2] = theta[K-1], out[3] = theta[m-1], out[4] =
+// 1 if a CholeskyQR pass broke down since the last summary (the flag is
+// cleared), out[5] = K.
 __global__ void ritz_summary_kernel(const double* __restrict__ res, const double* __restrict__ theta, int R, int m,
                                     int* __restrict__ breakdown, double* __restrict__ out) {
-  // One warp: the lanes take strided residuals (independent loads), then a
-  // max over the warp; NaN wins (a NaN residual must reach the host).
+  // One warp: K by a warp count (theta is sorted), then strided residuals
+  // (independent loads) and a max over the warp; NaN wins (a NaN residual
+  // must reach the host).
   const int lane = threadIdx.x;
+  const double floor_ = (double)RR_RESOLVE * theta[0];
+  int cnt = 0;
+  for (int j = lane; j < R; j += 32) cnt += theta[j] >= floor_ ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  const int K = cnt > 0 ? cnt : 1;
   double w = 0.0;
-  for (int j = lane; j < R; j += 32) w = (res[j] > w || res[j] != res[j]) ? res[j] : w;
+  for (int j = lane; j < K; j += 32) w = (res[j] > w || res[j] != res[j]) ? res[j] : w;
   for (int o = 16; o > 0; o >>= 1) {
     const double ow = __shfl_xor_sync(0xffffffffu, w, o);
     w = (ow > w || ow != ow) ? ow : w;
@@ -581,9 +598,10 @@ __global__ void ritz_summary_kernel(const double* __restrict__ res, const double
   if (lane != 0) return;
   out[0] = w;
   out[1] = theta[0];
-  out[2] = theta[R - 1];
+  out[2] = theta[K - 1];
   out[3] = theta[m - 1];
   out[4] = *breakdown ? 1.0 : 0.0;
+  out[5] = (double)K;
   *breakdown = 0;
 }
 
@@ -642,13 +660,12 @@ int cholqr3_f32(float* Y, float* T, float* Q, int64_t n, int m, RRBufs& b, cudaS
 }
 }  // namespace
 
-// Leading Ritz block of S by subspace iteration + Rayleigh-Ritz + Jacobi.
-// On success writes Qblk (n x m float64, m = rr_width(n, R), Ritz vectors in
-// descending Ritz-value order, orthonormal to float32 accuracy) and returns
-// ATK_OK; returns ATK_ENOCONV to request the full Jacobi.
-int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, int* dev_status, char* scratch,
-           size_t scratch_bytes, cudaStream_t st) {
-  const int m = rr_width(n, R);
+// Leading Ritz block of S by subspace iteration + Rayleigh-Ritz.  On
+// success writes Qblk (n x m float64, Ritz vectors in descending Ritz-value
+// order, orthonormal to float32 accuracy) and returns ATK_OK; returns
+// ATK_ENOCONV to request the full Jacobi.
+int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double* Qblk, int* dev_status,
+           char* scratch, size_t scratch_bytes, cudaStream_t st) {
   Arena ar{scratch, scratch_bytes, 0};
   RRBufs b;
   size_t nm = (size_t)n * m, mm = (size_t)m * m;
@@ -675,10 +692,10 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
   // Shared-memory limit of the one-CTA eigensolver, set outside the captured
   // launch sequences.
   ATK_TRY(tridiag_eig_prepare());
-  // The three launch sequences between host reads, each a cached graph:
-  // setup (the float32 copy of S, a random block, one power step, shifted
-  // CholeskyQR3), one Rayleigh-Ritz step up to its summary, and the two
-  // CholeskyQR passes that start the next step.
+  // The launch sequences between host reads, each a cached graph: setup (the
+  // float32 copy of S, a random block, one power step, shifted CholeskyQR3),
+  // one Rayleigh-Ritz step up to its summary, the power step from the Ritz
+  // vectors, and a plain power step.
   const GraphKey kpre{{S, scratch, nullptr, nullptr, nullptr, nullptr, nullptr, (const void*)1},
                       {n, R, m, (int64_t)scratch_bytes}};
   ATK_TRY(run_graph(kpre, st, [&](cudaStream_t s2) -> int {
@@ -697,7 +714,10 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
                      {n, R, m, (int64_t)max_sweeps}};
   const GraphKey knext{{scratch, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (const void*)3},
                        {n, R, m, (int64_t)scratch_bytes}};
-  for (int it = 0; it < RR_MAXIT; ++it) {
+  const GraphKey kpow{{scratch, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (const void*)4},
+                      {n, R, m, (int64_t)scratch_bytes}};
+  int power = 0;
+  for (;;) {
     // Rayleigh-Ritz: Z = S Q, B = Q^T Z = W diag(theta) W^T; Ritz vectors
     // Y = Q W (descending theta) and S Q W = Z W; residuals and summary.
     ATK_TRY(run_graph(kit, st, [&](cudaStream_t s2) -> int {
@@ -715,20 +735,30 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
       ATK_LAUNCHED();
       return ATK_OK;
     }));
-    double h[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double h[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     ATK_CUDA(cudaMemcpyAsync(h, b.summary, sizeof(h), cudaMemcpyDeviceToHost, st));
     ATK_CUDA(cudaStreamSynchronize(st));
-    const double res = h[0], thR = h[2], thm = fmax(h[3], 0.0);
+    const double res = h[0], thK = h[2], thm = fmax(h[3], 0.0);
     if (h[4] != 0.0) return ATK_ENOCONV;  // rank-deficient basis in float32: full Jacobi
-    if (!(res == res) || !(thR == thR) || !(h[1] == h[1]) || res > 1e300) return ATK_ENOCONV;  // non-finite
-    if (!(thR > 0.0) || thm > RR_SLOW_RATIO * thR) return ATK_ENOCONV;     // clustered: full Jacobi
-    const double predicted = (thm / thR) * res / (thR - thm);
+    if (!(res == res) || !(thK == thK) || !(h[1] == h[1]) || res > 1e300) return ATK_ENOCONV;  // non-finite
+    if (!(thK > 0.0)) return ATK_ENOCONV;
+    const double rate = thm / thK;
+    if (rate > RR_MAX_RATE) return ATK_ENOCONV;  // the cut sits in a cluster wider than the guard
+    const double predicted = rate * res / (thK - thm);
     if (predicted <= RR_TARGET) {
       f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Y, Qblk, n * (int64_t)m);
       ATK_LAUNCHED();
       return ATK_OK;
     }
-    // Next step from the Ritz vectors: S (Q W) = Z W is in T; its columns are
+    // Power steps to the predicted convergence (each multiplies the error by
+    // about `rate`), at most RR_POWER_CHUNK before the next projection.
+    int steps = 1;
+    if (rate > 0.0 && predicted > 0.0)
+      steps = (int)std::ceil(std::log(RR_TARGET / predicted) / std::log(rate));
+    steps = std::max(1, std::min(steps, RR_POWER_CHUNK));
+    if (power + steps > RR_MAX_POWER) return ATK_ENOCONV;
+    power += steps;
+    // First step from the Ritz vectors: S (Q W) = Z W is in T; its columns are
     // nearly orthogonal, so two plain CholeskyQR passes orthonormalise it.
     ATK_TRY(run_graph(knext, st, [&](cudaStream_t s2) -> int {
       // T = S Q W is in T and Q W in Y: T <- (S + sigma I) Q W.
@@ -738,8 +768,18 @@ int rr_top(const double* S, int64_t n, int64_t R, int max_sweeps, double* Qblk, 
       ATK_TRY(cholqr_pass_f32(b.T, b.Y, n, m, 0.f, b, s2));
       return cholqr_pass_f32(b.Y, b.Q, n, m, 0.f, b, s2);
     }));
+    // Further steps from Q: the block stays close to the Ritz vectors, so
+    // S Q keeps nearly orthogonal columns and two passes still suffice.
+    for (int k = 1; k < steps; ++k)
+      ATK_TRY(run_graph(kpow, st, [&](cudaStream_t s2) -> int {
+        ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.T, b, s2));
+        shift_axpy_kernel<<<(unsigned)ceil_div((int64_t)nm, 256), 256, 0, s2>>>(b.T, b.Q, b.Sf, n, (int64_t)nm,
+                                                                              RR_POWER_SHIFT);
+        ATK_LAUNCHED();
+        ATK_TRY(cholqr_pass_f32(b.T, b.Y, n, m, 0.f, b, s2));
+        return cholqr_pass_f32(b.Y, b.Q, n, m, 0.f, b, s2);
+      }));
   }
-  return ATK_ENOCONV;
 }
 
 // ----------------------------------------------------- float64 refinement
@@ -780,12 +820,14 @@ __global__ void simrot_kernel(const double* __restrict__ B, int64_t k, double* _
 }
 
 // order[0..k) = indices of diag(B) sorted descending (NaN lowest, ties by
-// index), lam[r] = B[order[r], order[r]] for r < R, disc = trace(S) - sum lam.
+// index), lam[r] = B[order[r], order[r]] for r < R, disc = trace(S) - sum lam,
+// and (nullable) lam_sorted[r] = B[order[r], order[r]] for every r < k.
 // One CTA, k <= 1024.
 __global__ void __launch_bounds__(256) order_diag_kernel(const double* __restrict__ B, int k, int R,
                                                          const double* __restrict__ S, int64_t n,
                                                          int* __restrict__ order, double* __restrict__ lam_out,
-                                                         double* __restrict__ disc_out) {
+                                                         double* __restrict__ disc_out,
+                                                         double* __restrict__ lam_sorted) {
   // Ranks by an integer key that orders like the float64 value (sign-folded
   // bit pattern; NaN lowest), so the k^2 comparisons stay off the float64
   // pipe; ties by index.
@@ -806,7 +848,10 @@ __global__ void __launch_bounds__(256) order_diag_kernel(const double* __restric
     ord[rank] = i;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < k; r += blockDim.x) order[r] = ord[r];
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    order[r] = ord[r];
+    if (lam_sorted) lam_sorted[r] = B[ord[r] + (int64_t)k * ord[r]];
+  }
   // trace(S): per-thread strided sums, then a fixed-order tree.
   double part = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) part += S[i + n * i];
@@ -854,12 +899,15 @@ size_t refine_bytes(int64_t n, int64_t k) {
 // Float64 refinement of an approximate leading block Qb (n x k, columns
 // roughly the leading eigenvectors of S in descending order), then the kept
 // R vectors.  Steps:
-//  1. one subspace-iteration step, Qb <- orth(S Qb): normalise the columns,
-//     then orthonormalise in Gram-Schmidt order.  Components outside the leading
-//     k-space shrink by lambda_{k+1}/lambda_j.  The Ritz block of the float32
-//     subspace iteration needs this step too: its float32 products leave
-//     about 1e-6 of each direction outside the subspace, which adds up over
-//     R = 128 columns to a projector error above 1e-4.
+//  1. subspace_steps subspace-iteration steps, Qb <- orth(S Qb): normalise
+//     the columns, then orthonormalise in Gram-Schmidt order.  Components
+//     outside the leading k-space shrink by lambda_{k+1}/lambda_j per step.
+//     The Ritz block of the float32 subspace iteration needs one step: its
+//     float32 products leave about 1e-6 of each direction outside the
+//     subspace, which adds up over R = 128 columns to a projector error above
+//     1e-4.  A column whose image is below keep_rel times the largest image
+//     (the numerical null space of S) or mostly leakage keeps its vector.
+//     With no step, Qb is only orthonormalised (two polar steps).
 //  2. Rayleigh-Ritz in float64: B = Qb^T S Qb.  The Ritz block is nearly
 //     diagonal; REFINE_ROTATION_STEPS (2) simultaneous Jacobi steps (W from
 //     simrot_kernel, orthonormalised by two polar steps, B <- W^T B W) take
@@ -868,7 +916,8 @@ size_t refine_bytes(int64_t n, int64_t k) {
 //     The kept eigenvalues are diag(B), the float64 Rayleigh quotients, and the
 //     discarded energy is trace(S) minus their sum.
 int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, double* U64, double* lambda_out,
-               double* discarded_out, char* scratch, size_t scratch_bytes, cudaStream_t st, bool subspace_step) {
+               double* discarded_out, double* lam_sorted, char* scratch, size_t scratch_bytes, cudaStream_t st,
+               int subspace_steps, double keep_rel) {
   Arena ar{scratch, scratch_bytes, 0};
   double* Z = (double*)ar.take(sizeof(double) * n * k);
   double* QW = (double*)ar.take(sizeof(double) * n * k);
@@ -883,13 +932,13 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
   if (!pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
   const unsigned gk = (unsigned)ceil_div(k * k, 256);
-  // 1. subspace step (subspace_step = false only orthonormalises Qb)
-  if (subspace_step) {
+  // 1. subspace steps (none: only orthonormalise Qb)
+  for (int step = 0; step < subspace_steps; ++step) {
     ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
     colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
     ATK_LAUNCHED();
-    normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k, 1e-5, 0.9,
-                                                                          Qb);
+    normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k, keep_rel,
+                                                                          0.9, Qb);
     ATK_LAUNCHED();
     // Orthonormalise in Gram-Schmidt order (column j against the columns
     // before it; Qb is sorted by descending Ritz value).  The subspace step
@@ -908,7 +957,8 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
     ATK_TRY(gemm_f64(Qb, T, n, k, k, Z, st));
     ATK_CUDA(cudaMemcpyAsync(Qb, Z, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
     for (int it = 0; it < 2; ++it) ATK_TRY(gs_step_f64(Qb, n, k, pol, st));
-  } else {
+  }
+  if (subspace_steps == 0) {
     ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
     ATK_TRY(polar_step_f64(Qb, n, k, pol, st));
   }
@@ -928,7 +978,7 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
     std::swap(Wt, T2);
   }
   // 3. kept vectors
-  order_diag_kernel<<<1, 256, 0, st>>>(B, (int)k, (int)R, S, n, order, lambda_out, discarded_out);
+  order_diag_kernel<<<1, 256, 0, st>>>(B, (int)k, (int)R, S, n, order, lambda_out, discarded_out, lam_sorted);
   ATK_LAUNCHED();
   ATK_TRY(gemm_f64(Qb, Wt, n, k, k, QW, st));
   gather_cols_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(QW, order, n, R, U64);
@@ -939,14 +989,22 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   return ATK_OK;
 }
 
-size_t eig_scratch_bytes(int64_t n, int arith) {
+// Scratch of one level (eig_level): the Ritz block, then the largest of the
+// solvers' and the refinement's needs.
+static size_t level_scratch_bytes(int64_t n, int arith) {
   size_t jac = arith == ATK_EIG_ROT_FP64 ? eig_bytes_t<double>(n) : eig_bytes_t<float>(n);
-  // refinement: Z (n x R) + the float64 small-LA scratch, for R up to n
-  size_t ref = (size_t)n * std::min<int64_t>(n, 128) * 8 + smallla_scratch_bytes(n, std::min<int64_t>(n, 128)) + 1024;
   size_t rr = rr_bytes(n, 156);
   const int64_t kmax = std::min<int64_t>(n, 156);
   // the Ritz block is carved first and outlives the solver that fills it
-  return (size_t)n * kmax * 8 + 512 + std::max(std::max(jac, ref), std::max(rr, refine_bytes(n, kmax)));
+  return (size_t)n * kmax * 8 + 512 + std::max(std::max(jac, rr), refine_bytes(n, kmax));
+}
+
+size_t eig_scratch_bytes(int64_t n, int arith) {
+  // sorted Rayleigh quotients, the combined and the per-level vector blocks
+  // and the two deflation products (n x 128 each), U^T S U (128 x 128) and
+  // the deflated matrix (n x n), then one level's scratch
+  return 8 * (size_t)(160 + 4 * n * std::min<int64_t>(n, 128) + 128 * 128 + n * n) + 8 * 256 +
+         level_scratch_bytes(n, arith);
 }
 
 // norms[r] = ||Z[:, r]||; one warp per column.
@@ -1026,51 +1084,182 @@ __global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R) {
     for (int64_t i = lane; i < n; i += 32) u[i] = -u[i];
 }
 
-// Eigen-decomposition + selection + float64 polar orthonormalisation.
-// U64_out (n x R float64) is the orthonormalised basis; U_out its float32 copy.
-int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, float* U_out,
-            double* U64_out, double* lambda_out, double* discarded_out, int* dev_status, char* scratch,
-            size_t scratch_bytes, cudaStream_t st) {
-  if (n <= 0 || R <= 0 || R > n || n > 1024) { set_error("eig: need 1 <= R <= n <= 1024"); return ATK_EUNSUPPORTED; }
-  const int m = rr_width(n, R);
+// One level of the eigensolver: the R leading eigenvectors of the symmetric
+// S by the subspace path or the full Jacobi, then the float64 refinement of
+// the leading block of k = rr_width(n, R, wide) vectors (R of them plus the
+// guard vectors, which make the gap at the cut visible).  Writes U64 (n x R,
+// descending Rayleigh quotients), lambda_out / discarded_out as
+// atucker_eig documents (nullable), lam_sorted[0..k) the sorted float64
+// Rayleigh quotients of the whole block.  The refined block stays in the
+// level's scratch for further steps: lv->Qb (n x k) and the scratch after it.
+struct Level {
+  double* Qb;
+  int64_t k;
+  char* rest;
+  size_t rest_bytes;
+};
+static int eig_level(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, bool wide,
+                     double* U64, double* lambda_out, double* discarded_out, double* lam_sorted, int* dev_status,
+                     char* scratch, size_t scratch_bytes, cudaStream_t st, Level* lv) {
+  const int m = rr_width(n, R, wide);
   const bool rr = arith == ATK_EIG_ROT_FP32 && m >= R + 8 &&
                   ((method == ATK_EIG_AUTO && 2 * m <= n) || (method == ATK_EIG_SUBSPACE && m < n));
   Arena ar{scratch, scratch_bytes, 0};
-  const int64_t kmax = rr ? m : R;
-  double* Qb = (double*)ar.take(sizeof(double) * n * kmax);
+  const int64_t k = m;  // both paths refine the leading m vectors
+  double* Qb = (double*)ar.take(sizeof(double) * n * k);
   if (!Qb) { set_error("eig: scratch too small"); return ATK_EINVAL; }
   char* rest = scratch + ar.used;
   const size_t rest_bytes = scratch_bytes - ar.used;
+  *lv = Level{Qb, k, rest, rest_bytes};
   int s = ATK_ENOCONV;
-  int64_t k = R;
   if (rr) {
-    s = rr_top(S, n, R, max_sweeps, Qb, dev_status, rest, rest_bytes, st);
+    s = rr_top(S, n, R, m, max_sweeps, Qb, dev_status, rest, rest_bytes, st);
     if (s != ATK_OK && s != ATK_ENOCONV) return s;
-    if (s == ATK_OK) {
-      k = m;
-      if (lambda_out && n > R) {
-        // Only the kept eigenvalues exist on this path; the tail is marked NaN.
-        ATK_CUDA(cudaMemsetAsync(lambda_out + R, 0xFF, sizeof(double) * (n - R), st));
-      }
+    if (s == ATK_OK && lambda_out && n > R) {
+      // Only the kept eigenvalues exist on this path; the tail is marked NaN.
+      ATK_CUDA(cudaMemsetAsync(lambda_out + R, 0xFF, sizeof(double) * (n - R), st));
     }
   }
   if (s != ATK_OK) {
-    // Full Jacobi: the R leading vectors (and all eigenvalues) of the whole Gram.
+    // Full Jacobi: the k leading vectors (and all eigenvalues) of the whole matrix.
     s = arith == ATK_EIG_ROT_FP64
-            ? eig_top_t<double>(S, n, R, max_sweeps, Qb, lambda_out, nullptr, dev_status, rest, rest_bytes, st)
-            : eig_top_t<float>(S, n, R, max_sweeps, Qb, lambda_out, nullptr, dev_status, rest, rest_bytes, st);
+            ? eig_top_t<double>(S, n, k, max_sweeps, Qb, lambda_out, nullptr, dev_status, rest, rest_bytes, st)
+            : eig_top_t<float>(S, n, k, max_sweeps, Qb, lambda_out, nullptr, dev_status, rest, rest_bytes, st);
     if (s != ATK_OK) return s;
-    k = R;
   }
-  // The refinement and the float32 copy of U: no host synchronisation inside,
-  // so one cached graph per (buffers, sizes).
-  const GraphKey key{{S, Qb, U64_out, lambda_out, discarded_out, U_out, rest, nullptr},
+  // The refinement: no host synchronisation inside, so one cached graph per
+  // (buffers, sizes).
+  const GraphKey key{{S, Qb, U64, lambda_out, discarded_out, lam_sorted, rest, nullptr},
                      {n, k, R, (int64_t)rest_bytes}};
   return run_graph(key, st, [&](cudaStream_t s2) -> int {
-    ATK_TRY(refine_f64(S, n, Qb, k, R, U64_out, lambda_out, discarded_out, rest, rest_bytes, s2, true));
-    if (U_out) ATK_TRY(f64_to_f32(U64_out, U_out, n * R, s2));
-    return ATK_OK;
+    return refine_f64(S, n, Qb, k, R, U64, lambda_out, discarded_out, lam_sorted, rest, rest_bytes, s2, 1, 1e-5);
   });
+}
+
+// Projected deflation S_out = P S_in P with P = I - U U^T (U n x h, orthonormal):
+// S_in - U W^T - W U^T + (V U^T + U V^T) / 2 with W = S_in U and V = U (U^T W),
+// over the upper triangle, mirrored.  Its error from an inexact U is second
+// order in the error of U (a direct S - U diag(lambda) U^T is first order).
+// Thread (i, j), i <= j, reads S_in(i, j) only and writes (i, j) and (j, i),
+// so S_out may be S_in.
+__global__ void deflate_kernel(const double* S_in, const double* __restrict__ U, const double* __restrict__ W,
+                               const double* __restrict__ V, int64_t n, int64_t h, double* S_out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx % n, j = idx / n;
+  if (i > j) return;
+  double v = S_in[i + n * j];
+  for (int64_t t = 0; t < h; ++t) {
+    const int64_t ci = i + n * t, cj = j + n * t;
+    v -= U[ci] * W[cj] + W[ci] * U[cj] - 0.5 * (V[ci] * U[cj] + U[ci] * V[cj]);
+  }
+  S_out[i + n * j] = v;
+  S_out[j + n * i] = v;
+}
+
+// Floating-point resolution of a level, in units of eps_32 times the level's
+// largest eigenvalue: the float32 products and rotations of a level resolve
+// eigenvalue differences down to about eps_32 lambda_1 of the matrix they
+// work on, and the float64 refinement's first-order rotations need a margin
+// above that.
+constexpr double LEVEL_RESOLVE = 64.0 * 1.1920928955078125e-7;
+constexpr int MAX_LEVELS = 4;
+// Float64 subspace steps on a level's block before its leading vectors are
+// deflated (each shrinks their components outside the block by
+// lambda_{k+1} / lambda_j), and the image floor of those steps: the float64
+// rounding level of the products rather than the float32 level of the Gram.
+constexpr int DEFLATE_STEPS = 3;
+constexpr double DEFLATE_KEEP_REL = 1e-10;
+
+// Leading-R eigenvectors (Alg. 2, EIG branch).  U64_out (n x R float64) is the
+// orthonormalised basis; U_out its float32 copy.
+//
+// Deflation levels (float32 rotations).  Level 0 solves S.  When the gap at
+// the cut, lambda_R - lambda_{R+1} (float64 Rayleigh quotients of the refined
+// block), is below LEVEL_RESOLVE lambda_1, float32 arithmetic on S cannot
+// resolve the cut: the split between the vectors on either side of it is
+// decided by rounding (a spectrum that decays like k^-3 reaches that at
+// R = 64 for a 256^3 tensor).  The level's block then takes DEFLATE_STEPS
+// more float64 subspace steps; its leading vectors whose eigenvalues lie
+// LEVEL_RESOLVE lambda_1 or more above the cut are resolved and final.  They
+// are deflated in float64, S_1 = P S P with P = I - U_h U_h^T, and the
+// remaining R - h vectors are the leading ones of S_1, whose largest
+// eigenvalue is about lambda_{h+1}, so the same float32 arithmetic resolves
+// the cut some lambda_1 / lambda_{h+1} times finer.  Each level repeats this
+// test.  The kept vectors of all levels are then refined together on S
+// (orthonormalisation, Rayleigh-Ritz, simultaneous rotations), which also
+// gives the kept eigenvalues and the discarded energy.  With float64
+// rotations the cut is resolved at level 0.
+int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, float* U_out,
+            double* U64_out, double* lambda_out, double* discarded_out, int* dev_status, char* scratch,
+            size_t scratch_bytes, cudaStream_t st, int* unresolved) {
+  if (n <= 0 || R <= 0 || R > n || n > 1024) { set_error("eig: need 1 <= R <= n <= 1024"); return ATK_EUNSUPPORTED; }
+  if (unresolved) *unresolved = 0;
+  Arena ar{scratch, scratch_bytes, 0};
+  double* lam_s = (double*)ar.take(sizeof(double) * 160);
+  double* Ufin = (double*)ar.take(sizeof(double) * n * R);
+  double* Ulev = (double*)ar.take(sizeof(double) * n * R);
+  double* W = (double*)ar.take(sizeof(double) * n * R);
+  double* V = (double*)ar.take(sizeof(double) * n * R);
+  double* M = (double*)ar.take(sizeof(double) * R * R);
+  double* SL = (double*)ar.take(sizeof(double) * n * n);
+  if (!SL) { set_error("eig: scratch too small"); return ATK_EINVAL; }
+  char* rest = scratch + ar.used;
+  const size_t rest_bytes = scratch_bytes - ar.used;
+  Level lv{};
+  ATK_TRY(eig_level(S, n, R, arith, method, max_sweeps, false, U64_out, lambda_out, discarded_out, lam_s, dev_status,
+                    rest, rest_bytes, st, &lv));
+  if (arith == ATK_EIG_ROT_FP32 && lv.k > R) {
+    double h[161];
+    auto read_lam = [&](int64_t count) -> int {
+      ATK_CUDA(cudaMemcpyAsync(h, lam_s, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+      ATK_CUDA(cudaStreamSynchronize(st));
+      return ATK_OK;
+    };
+    ATK_TRY(read_lam(R + 1));
+    if (h[R - 1] - h[R] < LEVEL_RESOLVE * fabs(h[0])) {
+      if (unresolved) {
+        *unresolved = 1;
+        return ATK_OK;
+      }
+      // The cut is not resolved at level 0: deflation levels.
+      const double* src = S;
+      int64_t done = 0, RL = R;
+      for (int level = 1;; ++level) {
+        // More float64 steps on this level's block, so that the vectors to be
+        // deflated are accurate to float64 level.
+        ATK_TRY(refine_f64(src, n, lv.Qb, lv.k, RL, Ulev, nullptr, nullptr, lam_s, lv.rest, lv.rest_bytes, st,
+                           DEFLATE_STEPS, DEFLATE_KEEP_REL));
+        ATK_TRY(read_lam(RL + 1));
+        const double delta = LEVEL_RESOLVE * fabs(h[0]);
+        if (level >= MAX_LEVELS || h[RL - 1] - h[RL] >= delta) break;  // resolved at this level
+        int64_t hd = 0;
+        while (hd < RL && h[hd] >= h[RL - 1] + delta) ++hd;
+        if (hd == 0) break;  // nothing to deflate: the kept vectors all sit at the cut
+        ATK_CUDA(cudaMemcpyAsync(Ufin + n * done, Ulev, sizeof(double) * n * hd, cudaMemcpyDeviceToDevice, st));
+        ATK_TRY(gemm_f64(src, Ulev, n, n, hd, W, st));          // W = S_L U_h
+        ATK_TRY(gemm_tn_f64(Ulev, W, n, hd, M, st));            // M = U_h^T W
+        ATK_TRY(gemm_f64(Ulev, M, n, hd, hd, V, st));           // V = U_h M
+        deflate_kernel<<<(unsigned)ceil_div(n * n, 256), 256, 0, st>>>(src, Ulev, W, V, n, hd, SL);
+        ATK_LAUNCHED();
+        src = SL;
+        done += hd;
+        RL -= hd;
+        ATK_TRY(eig_level(SL, n, RL, arith, method, max_sweeps, true, Ulev, nullptr, nullptr, lam_s, dev_status,
+                          rest, rest_bytes, st, &lv));
+        if (lv.k <= RL) break;
+        ATK_TRY(read_lam(RL + 1));
+        if (h[RL - 1] - h[RL] >= LEVEL_RESOLVE * fabs(h[0])) break;  // resolved without more steps
+      }
+      ATK_CUDA(cudaMemcpyAsync(Ufin + n * done, Ulev, sizeof(double) * n * RL, cudaMemcpyDeviceToDevice, st));
+      // The kept vectors of every level, refined together on S.
+      ATK_TRY(refine_f64(S, n, Ufin, R, R, U64_out, lambda_out, discarded_out, nullptr, rest, rest_bytes, st, 0,
+                         0.0));
+      if (lambda_out && n > R) ATK_CUDA(cudaMemsetAsync(lambda_out + R, 0xFF, sizeof(double) * (n - R), st));
+    }
+  }
+  if (U_out) ATK_TRY(f64_to_f32(U64_out, U_out, n * R, st));
+  return ATK_OK;
 }
 
 }  // namespace atk

@@ -122,7 +122,7 @@ struct atucker_plan_s {
   int precision = ATK_FP32, als_sweeps = 5;
   uint64_t seed = 0;
   cudaStream_t st = nullptr;
-  int eig_arith = ATK_EIG_ROT_FP32, eig_method = ATK_EIG_AUTO, sync = 0, max_sweeps = 40;
+  int eig_arith = ATK_EIG_ROT_FP32, eig_method = ATK_EIG_AUTO, sync = 0, max_sweeps = 40, gram_refine = 1;
   // device workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -209,7 +209,9 @@ static int plan_alloc(atucker_plan_s* p) {
     if (p->solver[n] == ATK_EIG) {
       s_elems = std::max(s_elems, (size_t)(v.n * v.n));
       scratch = std::max(scratch, gram_scratch_bytes(v, p->gbm[n]));
-      if (p->precision != ATK_FP32) scratch = std::max(scratch, tc_gram_scratch_bytes(v, p->precision));
+      if (p->precision != ATK_FP32 && p->precision != ATK_FP32C)
+        scratch = std::max(scratch, tc_gram_scratch_bytes(v, p->precision));
+      scratch = std::max(scratch, gram_cmp_scratch_bytes(v));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP64));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP32));
       scratch = std::max(scratch, smallla_scratch_bytes(v.n, R));
@@ -314,7 +316,7 @@ int atucker_plan_create_classes(atucker_plan_t* plan, int order, const int64_t* 
     solver[k] = class_per_mode[k] == ATK_CLASS_ALS ? ATK_ALS : ATK_EIG;
   }
   ATK_TRY(validate(order, dims, ranks, mode_order, solver));
-  if (precision < ATK_FP32 || precision > ATK_FP8E4M3) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  if (precision < ATK_FP32 || precision > ATK_FP32C) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
   atucker_plan_s* p = new atucker_plan_s();
   p->order = order;
   int64_t off = 0;
@@ -395,6 +397,10 @@ int atucker_plan_set_option(atucker_plan_t p, int key, int64_t value) {
       if (value < 1 || value > 200) break;
       p->max_sweeps = (int)value;
       return ATK_OK;
+    case ATK_OPT_GRAM_REFINE:
+      if (value < 0 || value > 2) break;
+      p->gram_refine = (int)value;
+      return ATK_OK;
     default:
       break;
   }
@@ -449,6 +455,9 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
       cudaEvent_t mid = tm ? p->ev() : nullptr;
       if (p->precision == ATK_FP32) {
         ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid, p->gbm[n], p->dev_status));
+      } else if (p->precision == ATK_FP32C) {
+        ATK_TRY(gram_cmp(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st));
+        if (mid) ATK_CUDA(cudaEventRecord(mid, st));
       } else {
         ATK_TRY(tc_gram(Y, v, p->precision, p->S, (float*)p->scratch, p->scratch_bytes, p->dev_status, st));
         if (mid) ATK_CUDA(cudaEventRecord(mid, st));
@@ -460,8 +469,18 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
       }
       ATK_TRY(mark(PH_GRAM_REDUCE));
       const int em = p->eigm[n] >= 0 ? p->eigm[n] : p->eig_method;
+      // A cut that the float32 Gram cannot resolve (ATK_OPT_GRAM_REFINE):
+      // recompute this mode's Gram with compensated sums and solve again.
+      const bool refine = p->precision != ATK_FP32C && p->eig_arith == ATK_EIG_ROT_FP32 &&
+                          (p->gram_refine == 2 || (p->gram_refine == 1 && step > 0));
+      int unresolved = 0;
       ATK_TRY(eig_top(p->S, v.n, R, p->eig_arith, em, p->max_sweeps, U32, p->U64, nullptr, disc,
-                      p->dev_status, p->scratch, p->scratch_bytes, st));
+                      p->dev_status, p->scratch, p->scratch_bytes, st, refine ? &unresolved : nullptr));
+      if (unresolved) {
+        ATK_TRY(gram_cmp(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st));
+        ATK_TRY(eig_top(p->S, v.n, R, p->eig_arith, em, p->max_sweeps, U32, p->U64, nullptr, disc,
+                        p->dev_status, p->scratch, p->scratch_bytes, st));
+      }
       ATK_TRY(mark(PH_EIG));
       ATK_TRY(ttm_f32(Y, v, U32, R, out, st));
       ATK_TRY(mark(PH_TTM));
@@ -593,11 +612,18 @@ static int read_status(int* dev, cudaStream_t st) {
 int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precision, double* S_out, void* stream) {
   if (!y || !S_out) { set_error("null argument"); return ATK_EINVAL; }
   ATK_TRY(check_view(lo, n, hi));
-  if (precision < ATK_FP32 || precision > ATK_FP8E4M3) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  if (precision < ATK_FP32 || precision > ATK_FP32C) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
   if (n > 4096) { set_error("Gram needs n <= 4096"); return ATK_EUNSUPPORTED; }
   cudaStream_t st = (cudaStream_t)stream;
   View v{lo, n, hi};
   StreamScratch sc(st);
+  if (precision == ATK_FP32C) {
+    const size_t bytes = gram_cmp_scratch_bytes(v);
+    ATK_TRY(sc.alloc(bytes));
+    ATK_TRY(gram_cmp(y, v, S_out, (float*)sc.ptr, bytes, st));
+    ATK_CUDA(cudaStreamSynchronize(st));
+    return ATK_OK;
+  }
   if (precision == ATK_FP32) {
     size_t bytes = gram_scratch_bytes(v) + 256;
     ATK_TRY(sc.alloc(bytes));

@@ -1,4 +1,4 @@
-// Learned per-mode selector (the paper's adaptive solver selection, Sec. IV-C):
+// Learned per-mode selector (the paper's adaptive solver selection, Sec. IV):
 // features of each mode (Table I plus the mode's position and the remaining
 // tensor size), host inference of a 12 -> 64 -> 64 -> K ReLU network, and the
 // CUDA kernels that train it on the GPU (forward, masked squared loss,

@@ -1,4 +1,4 @@
-"""Learned per-mode solver-and-tile selector (Sec. IV-C, with an MLP in place of
+"""Learned per-mode solver-and-tile selector (Sec. IV, with an MLP in place of
 the paper's decision tree).
 
 Every step here is a call into the CUDA library: features come from
