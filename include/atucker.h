@@ -118,16 +118,26 @@ typedef enum {
   ATK_OPT_TIMING = 4,     /* 1: record CUDA events around each phase (see atucker_plan_timings) */
   ATK_OPT_EIG_METHOD = 5, /* atucker_eig_method; default ATK_EIG_AUTO */
   /* Precise Gram for a cut that float32 does not resolve (float32 rotations).
-   * When the Gram's largest eigenvalue times LEVEL (64 eps_32) exceeds the
-   * gap between the R-th and the next Rayleigh quotient, a float32 Gram
-   * cannot decide which vectors lie on either side of the cut: its rounding
-   * reaches eps_32 times the largest partial sum.  The mode's Gram is then
+   * A float32 Gram's rounding reaches eps_32 times its largest partial sum,
+   * about eps_32 lambda_1 when the energy sits in few entries.  When the gap
+   * between the R-th and the next Rayleigh quotient is below 64 eps_32
+   * lambda_1 (the Gram cannot decide which vectors lie on either side of the
+   * cut) or below 1e4 eps_32 sqrt(2 R) lambda_1 (the kept subspace could
+   * turn by more than a 1e-4 projector distance), the mode's Gram is
    * recomputed in ATK_FP32C and solved again.  0: never; 1 (default): every
    * EIG mode but the first processed one (that mode reads the caller's
    * tensor, whose entries are of comparable size, so its float32 roundings
    * stay independent and small; later modes read the shrinking core, whose
    * energy sits in few entries); 2: every EIG mode. */
-  ATK_OPT_GRAM_REFINE = 6
+  ATK_OPT_GRAM_REFINE = 6,
+  /* Poll limit of every grid-barrier wait of the cooperative block Jacobi
+   * (full Jacobi with I_n > 160) in this plan's runs; 0 (default) keeps 2e7
+   * polls of 64 ns, about a second.  A wait that reaches the limit records
+   * ATK_ETIMEOUT in the plan's status and its CTA returns; the others give up
+   * at their next wait, so the kernel ends on its own and the next
+   * atucker_plan_sync reports ATK_ETIMEOUT.  The results of such a run are
+   * not usable; the plan is.  Small values exist to test that path. */
+  ATK_OPT_WAIT_LIMIT = 7
 } atucker_option;
 
 typedef struct atucker_plan_s* atucker_plan_t;
@@ -237,6 +247,14 @@ int atucker_sthosvd_oneshot(const float* x, int order, const int64_t* dims, cons
                             const int* mode_order, const int* solver_per_mode, float* core_out,
                             float* factors_out);
 
+/* Process-wide cap on the size of any single device allocation the library
+ * makes: plan workspaces, host-buffer staging, step-level scratch, batch and
+ * selector buffers.  A request above the cap fails with ATK_ENOMEM before
+ * any CUDA call, exactly as an exhausted device would fail it, so a service
+ * can bound what the library takes and tests can drive the out-of-memory
+ * paths.  0 (default) removes the cap.  Always returns ATK_OK. */
+int atucker_set_device_alloc_limit(uint64_t bytes);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char* atucker_last_error(void);
 
@@ -269,11 +287,15 @@ int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precisio
  *     the library (float32).  Every GPU that loads the library holds it until
  *     the process exits.
  *   - Limit: n <= 2048 (one split's partial tiles must fit); larger n returns
- *     ATK_EUNSUPPORTED.  Larger J runs in fewer, longer splits than
- *     atucker_gram when the array is the bound.
+ *     ATK_EUNSUPPORTED.  When a view needs more splits than the array holds,
+ *     they run in rounds whose sums are added in float64, so every float32
+ *     partial sum stays within 8192 terms, as in atucker_gram.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current.  That lookup may load
+ *     the library's module on the device and so reserve the 16 MiB then: make
+ *     a first call before fixing a memory budget, and before any stream
+ *     capture.  The address is cached for the process; after a device reset,
+ *     start a new process.
  *   - All calls share the array: calls that overlap on the GPU (other streams,
  *     other threads) race and corrupt each other's results.  Nothing in the
  *     array needs to start at zero; each call writes every tile it reads.

@@ -28,6 +28,7 @@ EIG, ALS = 0, 1
 FP32, TF32, BF16, BF16X3, FP8E4M3, FP32C = 0, 1, 2, 3, 4, 5
 EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
 OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD, OPT_GRAM_REFINE = 1, 2, 3, 4, 5, 6
+OPT_WAIT_LIMIT = 7
 EIG_AUTO, EIG_FULL_JACOBI, EIG_SUBSPACE = 0, 1, 2
 BATCH_OPT_VARIANT, BATCH_OPT_GRAPH, BATCH_OPT_SYNC, BATCH_OPT_JACOBI_MAX_SWEEPS = 1, 2, 3, 4
 AUTO = -1
@@ -59,6 +60,7 @@ _SIGS = {
     "atucker_plan_destroy": (None, [_vp]),
     "atucker_sthosvd_oneshot": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "atucker_last_error": (ctypes.c_char_p, []),
+    "atucker_set_device_alloc_limit": (_i32, [_u64]),
     "atucker_version": (ctypes.c_char_p, []),
     "atucker_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "atucker_gram_noalloc": (_i32, [_vp, _i64, _i64, _i64, _vp, _vp]),
@@ -217,6 +219,9 @@ class Plan:
         _check(lib().atucker_sthosvd_host(self._h, ctypes.c_void_p(x_host.data_ptr()),
                                           ctypes.c_void_p(core_host.data_ptr()),
                                           ctypes.c_void_p(factors_host.data_ptr()), d), "atucker_sthosvd_host")
+
+    def set_option(self, key: int, value: int):
+        _check(lib().atucker_plan_set_option(self._h, int(key), int(value)), "set_option")
 
     def set_timing(self, on: bool = True):
         _check(lib().atucker_plan_set_option(self._h, OPT_TIMING, 1 if on else 0), "set_option")

@@ -130,6 +130,16 @@ __device__ inline bool grid_barrier(unsigned* bar, unsigned nblocks, int* status
 
 // ------------------------------------------------------------- host helpers
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+// Device allocations of the library (plan workspaces, host-buffer staging,
+// step-level scratch, batch and selector buffers).  A request above the
+// process-wide cap of atucker_set_device_alloc_limit fails with ATK_ENOMEM
+// before any CUDA call; otherwise cudaMalloc / cudaMallocAsync.
+int dev_alloc(void** ptr, size_t bytes, const char* what);
+int dev_alloc_async(void** ptr, size_t bytes, cudaStream_t st, const char* what);
+// Poll limit of the grid-barrier waits of the cooperative Jacobi for plan runs
+// on the calling host thread (ATK_OPT_WAIT_LIMIT); 0 keeps the default.
+void set_wait_limit(long long polls);
+long long wait_limit();
 int num_sms();
 
 // Device scratch carved from one allocation; each take() is 256-byte aligned.

@@ -547,7 +547,7 @@ int atucker_batch_create(atucker_batch_t* out, int count, const int64_t* dims3, 
   if (cudaMalloc(&b->d_ptrs, sizeof(Ptrs) * count) != cudaSuccess) return fail("batch: out of device memory");
   if (cudaMalloc(&b->d_counter, sizeof(int) * 2) != cudaSuccess) return fail("batch: out of device memory");
   if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) return fail("batch: out of device memory");
-  if (cudaMalloc(&b->ws, sizeof(float) * b->ws_per_cta * b->max_grid) != cudaSuccess)
+  if (dev_alloc((void**)&b->ws, sizeof(float) * b->ws_per_cta * b->max_grid, "cudaMalloc(batch workspace)") != ATK_OK)
     return fail("batch: out of device memory (workspace)");
   if (cudaMallocHost(&b->h_ptrs, sizeof(Ptrs) * count) != cudaSuccess) return fail("batch: pinned memory");
   if (cudaMemcpy(b->d_desc, desc.data(), sizeof(Desc) * count, cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -353,7 +353,7 @@ struct Block {
 template <int BM, int TM, bool DIAG, bool VEC>
 __global__ void __launch_bounds__(NT, 2)
 gram_ci_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, int T, int64_t kc,
-               float* __restrict__ part) {
+               float* __restrict__ part, int64_t c_base = 0) {
   constexpr int SA = TK * (BM + PAD);
   __shared__ __align__(16) float sA[2 * SA];
   __shared__ __align__(16) float sB[DIAG ? 1 : 2 * SA];
@@ -370,7 +370,7 @@ gram_ci_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, i
   }
   const int tile = ti * T - ti * (ti - 1) / 2 + (tj - ti);
   const int64_t J = lo * hi;
-  const int64_t cb = (int64_t)split * kc, ce = min(J, cb + kc);
+  const int64_t cb = c_base + (int64_t)split * kc, ce = min(J, cb + kc);
   ViewLoaderKC<BM, VEC> la, lb;
   la.init(y, lo, n, ce, (int64_t)ti * BM);
   if (!DIAG) lb.init(y, lo, n, ce, (int64_t)tj * BM);
@@ -416,19 +416,21 @@ static bool kc_vec_ok(const float* y, const View& v) {
   return v.lo == 1 && v.n % 4 == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0;
 }
 
+// c_base: the first c of split 0 (a round of a split-K that runs in several
+// rounds; 0 otherwise).
 template <int BM, int TM, bool VEC>
 static void launch_gram_tiles_v(const float* y, const View& v, int T, int ns_d, int64_t kc_d, int ns_o,
-                                int64_t kc_o, float* part, cudaStream_t st) {
-  gram_ci_kernel<BM, TM, true, VEC><<<dim3(T, ns_d), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_d, part);
+                                int64_t kc_o, float* part, cudaStream_t st, int64_t c_base) {
+  gram_ci_kernel<BM, TM, true, VEC><<<dim3(T, ns_d), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_d, part, c_base);
   if (T > 1)
     gram_ci_kernel<BM, TM, false, VEC><<<dim3(T * (T - 1) / 2, ns_o), NT, 0, st>>>(y, v.lo, v.n, v.hi, T, kc_o,
-                                                                                    part);
+                                                                                    part, c_base);
 }
 template <int BM, int TM>
 static void launch_gram_tiles(const float* y, const View& v, int T, int ns_d, int64_t kc_d, int ns_o, int64_t kc_o,
-                              float* part, cudaStream_t st) {
-  if (kc_vec_ok(y, v)) launch_gram_tiles_v<BM, TM, true>(y, v, T, ns_d, kc_d, ns_o, kc_o, part, st);
-  else launch_gram_tiles_v<BM, TM, false>(y, v, T, ns_d, kc_d, ns_o, kc_o, part, st);
+                              float* part, cudaStream_t st, int64_t c_base = 0) {
+  if (kc_vec_ok(y, v)) launch_gram_tiles_v<BM, TM, true>(y, v, T, ns_d, kc_d, ns_o, kc_o, part, st, c_base);
+  else launch_gram_tiles_v<BM, TM, false>(y, v, T, ns_d, kc_d, ns_o, kc_o, part, st, c_base);
 }
 
 // ------------------------------------------------ bulk-fed Gram (mode-1 views)
@@ -604,7 +606,7 @@ __device__ __forceinline__ FFSum ff_sum_splits(const float* __restrict__ p, int6
 // sym: C is n x n from upper-triangle tiles (T x T grid of BM tiles); diagonal
 // tiles have ns_d splits, off-diagonal tiles ns_o.
 __global__ void reduce_sym_kernel(const float* __restrict__ part, int ns_d, int ns_o, int ntiles, int T, int BM,
-                                  int64_t n, double* __restrict__ C) {
+                                  int64_t n, double* __restrict__ C, int accumulate = 0) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   int64_t i = idx / n, j = idx % n;  // lanes along j: contiguous within a tile row
@@ -614,7 +616,7 @@ __global__ void reduce_sym_kernel(const float* __restrict__ part, int ns_d, int 
   int64_t o = (i - (int64_t)ti * BM) * BM + (j - (int64_t)tj * BM);
   const int nsplit = ti == tj ? ns_d : ns_o;
   const FFSum acc = ff_sum_splits(part + (int64_t)id * BM * BM + o, (int64_t)ntiles * BM * BM, nsplit);
-  const double s = acc.value();
+  const double s = accumulate ? C[i + n * j] + acc.value() : acc.value();
   C[i + n * j] = s;
   C[j + n * i] = s;
 }
@@ -789,10 +791,11 @@ int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t sc
   return ATK_OK;
 }
 
-// Same kernels as gram_f32, with the split count capped so that the partial
-// tiles fit in `scratch_bytes` (callers whose scratch is a fixed block).
-// Fewer splits mean longer float32 chains per partial sum; the float64
-// reduction across splits is unchanged.
+// Same kernels as gram_f32 for callers whose scratch is a fixed block.  The
+// float32 chains keep the library's length (at most SPLIT_MAX_K terms); when
+// the partial tiles of all splits do not fit in `scratch_bytes`, the splits
+// run in rounds of as many as fit, and each round's sum (float-float, rounded
+// to float64) is added to S in float64, in round order (deterministic).
 int gram_f32_fixed_scratch(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes,
                            cudaStream_t st) {
   if (v.n <= 0) return ATK_OK;
@@ -807,20 +810,22 @@ int gram_f32_fixed_scratch(const float* y, const View& v, double* S, float* scra
     set_error("gram: the partial tiles of one split do not fit in the fixed scratch");
     return ATK_EUNSUPPORTED;
   }
-  for (SplitPlan* sp : {&g.d, &g.o}) {
-    if (sp->nsplit > fit) {
-      sp->kc = ceil_div(ceil_div(v.J(), fit), TK) * TK;
-      sp->nsplit = (int)ceil_div(v.J(), sp->kc);
-    }
+  // One split plan for both launches: chains of at most SPLIT_MAX_K terms.
+  const int64_t J = v.J();
+  const int64_t kc = std::min<int64_t>(std::min(g.d.kc, g.o.kc), SPLIT_MAX_K);
+  const int64_t total = ceil_div(J, kc);
+  for (int64_t first = 0; first < total; first += fit) {
+    const int ns = (int)std::min<int64_t>(fit, total - first);
+    const int64_t c_base = first * kc;
+    if (g.bm == 128) launch_gram_tiles<128, 8>(y, v, g.T, ns, kc, ns, kc, scratch, st, c_base);
+    else if (g.bm == 64) launch_gram_tiles<64, 4>(y, v, g.T, ns, kc, ns, kc, scratch, st, c_base);
+    else launch_gram_tiles<32, 2>(y, v, g.T, ns, kc, ns, kc, scratch, st, c_base);
+    ATK_LAUNCHED();
+    if (g.T > 1) count_launch();
+    reduce_sym_kernel<<<(unsigned)ceil_div(v.n * v.n, 256), 256, 0, st>>>(scratch, ns, ns, g.nt, g.T, g.bm, v.n, S,
+                                                                           first > 0 ? 1 : 0);
+    ATK_LAUNCHED();
   }
-  if (g.bm == 128) launch_gram_tiles<128, 8>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
-  else if (g.bm == 64) launch_gram_tiles<64, 4>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
-  else launch_gram_tiles<32, 2>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
-  ATK_LAUNCHED();
-  if (g.T > 1) count_launch();
-  reduce_sym_kernel<<<(unsigned)ceil_div(v.n * v.n, 256), 256, 0, st>>>(scratch, g.d.nsplit, g.o.nsplit, g.nt, g.T,
-                                                                         g.bm, v.n, S);
-  ATK_LAUNCHED();
   return ATK_OK;
 }
 

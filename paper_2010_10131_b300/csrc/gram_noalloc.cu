@@ -14,13 +14,17 @@
 namespace atk {
 
 // 16 MiB of float32 partial tiles: enough for one split of any n <= 2048
-// (136 tiles of 128 x 128).  Larger J runs in more splits when they fit.
+// (136 tiles of 128 x 128).  When a view needs more splits than fit, they run
+// in rounds (gram_f32_fixed_scratch), so every float32 chain stays as short
+// as in atucker_gram.
 constexpr size_t NOALLOC_GRAM_FLOATS = size_t(4) << 20;
 static __device__ __align__(256) float g_gram_partials[NOALLOC_GRAM_FLOATS];
 
 // Device address of g_gram_partials for each device, looked up once with that
 // device current.  In host code the array's name is only a host-side stand-in,
-// so kernels must be handed this address instead.
+// so kernels must be handed this address instead.  The lookup can load the
+// library's module on that device (which reserves the array), and the cached
+// address belongs to that context: after a device reset, use a new process.
 static std::mutex g_partials_mutex;
 static float* g_partials_ptr[64] = {nullptr};
 

@@ -96,6 +96,7 @@ struct BlockJacobiArgs {
   unsigned* bar;  // grid barrier words (2)
   int* sweep_flags;  // per outer sweep: 1 if any rotation happened
   int* status;
+  long long wait_polls;  // poll limit of each grid-barrier wait
 };
 
 // Global index of local index u (0..63) in the sub-problem of blocks (P, Q).
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256) jacobi_block_kernel(BlockJacobiArgs args,
         }
         __syncthreads();
       }
-      if (!grid_barrier(args.bar, G, args.status)) return;
+      if (!grid_barrier(args.bar, G, args.status, args.wait_polls)) return;
       // Phase 2: A_kl <- W_k^T A_kl W_l (k < l, mirrored) and V_l <- V_l W_l.
       const int ntA = half * (half - 1) / 2;
       const int nrow = m / JS;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(256) jacobi_block_kernel(BlockJacobiArgs args,
           __syncthreads();
         }
       }
-      if (!grid_barrier(args.bar, G, args.status)) return;
+      if (!grid_barrier(args.bar, G, args.status, args.wait_polls)) return;
     }
     if (*(volatile int*)(args.sweep_flags + sweep) == 0) return;  // converged
   }
@@ -381,6 +382,7 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
   args.bar = reinterpret_cast<unsigned*>(words);
   args.sweep_flags = words + 2;
   args.status = dev_status;
+  args.wait_polls = wait_limit() > 0 ? wait_limit() : 20000000LL;
   size_t sm = block_smem<T>();
   ATK_TRY(raise_smem_limit((const void*)jacobi_block_kernel<T>, sm));
   int per_sm = 0;
@@ -1163,6 +1165,11 @@ __global__ void deflate_kernel(const double* S_in, const double* __restrict__ U,
 // work on, and the float64 refinement's first-order rotations need a margin
 // above that.
 constexpr double LEVEL_RESOLVE = 64.0 * 1.1920928955078125e-7;
+// A Gram computed with float32 sums errs by up to about eps_32 lambda_1 where
+// its energy sits in few entries, which turns the kept subspace by about
+// eps_32 lambda_1 / gap per direction; the projector distance stays within
+// 1e-4 only while gap >= GRAM_PROJ_RESOLVE sqrt(2 R) lambda_1.
+constexpr double GRAM_PROJ_RESOLVE = 1e4 * 1.1920928955078125e-7;
 constexpr int MAX_LEVELS = 4;
 // Float64 subspace steps on a level's block before its leading vectors are
 // deflated (each shrinks their components outside the block by
@@ -1217,11 +1224,12 @@ int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int ma
       return ATK_OK;
     };
     ATK_TRY(read_lam(R + 1));
-    if (h[R - 1] - h[R] < LEVEL_RESOLVE * fabs(h[0])) {
-      if (unresolved) {
-        *unresolved = 1;
-        return ATK_OK;
-      }
+    const double gap0 = h[R - 1] - h[R];
+    if (unresolved && gap0 < std::max(LEVEL_RESOLVE, GRAM_PROJ_RESOLVE * sqrt(2.0 * R)) * fabs(h[0])) {
+      *unresolved = 1;
+      return ATK_OK;
+    }
+    if (gap0 < LEVEL_RESOLVE * fabs(h[0])) {
       // The cut is not resolved at level 0: deflation levels.
       const double* src = S;
       int64_t done = 0, RL = R;

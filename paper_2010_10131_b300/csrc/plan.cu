@@ -27,6 +27,33 @@ void count_launch() { ++t_launches; }
 long long launch_count() { return t_launches; }
 void count_launches(long long k) { t_launches += k; }
 
+static std::atomic<unsigned long long> g_alloc_limit{0};
+static int alloc_over_limit(size_t bytes, const char* what) {
+  const unsigned long long lim = g_alloc_limit.load();
+  if (lim && bytes > lim) {
+    g_err = std::string("device allocation above the library's limit: ") + what;
+    return ATK_ENOMEM;
+  }
+  return ATK_OK;
+}
+int dev_alloc(void** ptr, size_t bytes, const char* what) {
+  *ptr = nullptr;
+  ATK_TRY(alloc_over_limit(bytes, what));
+  const cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) { *ptr = nullptr; return cuda_status(e, what); }
+  return ATK_OK;
+}
+int dev_alloc_async(void** ptr, size_t bytes, cudaStream_t st, const char* what) {
+  *ptr = nullptr;
+  ATK_TRY(alloc_over_limit(bytes, what));
+  const cudaError_t e = cudaMallocAsync(ptr, bytes, st);
+  if (e != cudaSuccess) { *ptr = nullptr; return cuda_status(e, what); }
+  return ATK_OK;
+}
+static thread_local long long t_wait_limit = 0;
+void set_wait_limit(long long polls) { t_wait_limit = polls; }
+long long wait_limit() { return t_wait_limit; }
+
 int num_sms() {
   static const int sms = [] {  // thread-safe one-time initialisation
     int dev = 0, v = 0;
@@ -123,6 +150,7 @@ struct atucker_plan_s {
   uint64_t seed = 0;
   cudaStream_t st = nullptr;
   int eig_arith = ATK_EIG_ROT_FP32, eig_method = ATK_EIG_AUTO, sync = 0, max_sweeps = 40, gram_refine = 1;
+  long long wait_polls = 0;  // ATK_OPT_WAIT_LIMIT (0: default)
   // device workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -235,8 +263,7 @@ static int plan_alloc(atucker_plan_s* p) {
     add(nr * 4); add(rr * 4);
   }
   add(scratch); add(256);
-  cudaError_t e = cudaMalloc(&p->ws, need);
-  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc(plan workspace)");
+  ATK_TRY(dev_alloc((void**)&p->ws, need, "cudaMalloc(plan workspace)"));
   p->ws_bytes = need;
   Arena ar{p->ws, need, 0};
   p->buf[0] = (float*)ar.take(bufsz[0] * 4);
@@ -401,6 +428,10 @@ int atucker_plan_set_option(atucker_plan_t p, int key, int64_t value) {
       if (value < 0 || value > 2) break;
       p->gram_refine = (int)value;
       return ATK_OK;
+    case ATK_OPT_WAIT_LIMIT:
+      if (value < 0) break;
+      p->wait_polls = value;
+      return ATK_OK;
     default:
       break;
   }
@@ -508,7 +539,9 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
 int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* factors_out, double* discarded_out) {
   if (!p || !x || !core_out || !factors_out) { set_error("null argument"); return ATK_EINVAL; }
   const long long l0 = launch_count();
+  set_wait_limit(p->wait_polls);
   const int s = sthosvd_run(p, x, core_out, factors_out, discarded_out);
+  set_wait_limit(0);
   p->launches += launch_count() - l0;
   return s;
 }
@@ -519,7 +552,7 @@ int atucker_sthosvd_host(atucker_plan_t p, const float* x_host, float* core_host
   if (!p->x_dev) {
     size_t need = (size_t)p->total * 4 + (size_t)p->core_total * 4 + (size_t)p->fac_total * 4 + 8 * 8 + 1024;
     char* base = nullptr;
-    ATK_CUDA(cudaMalloc(&base, need));
+    ATK_TRY(dev_alloc((void**)&base, need, "cudaMalloc(host-buffer staging)"));
     Arena ar{base, need, 0};
     p->x_dev = (float*)ar.take((size_t)p->total * 4);
     p->core_dev = (float*)ar.take((size_t)p->core_total * 4);
@@ -575,6 +608,11 @@ int atucker_sthosvd_oneshot(const float* x, int order, const int64_t* dims, cons
   return s;
 }
 
+int atucker_set_device_alloc_limit(uint64_t bytes) {
+  g_alloc_limit.store(bytes);
+  return ATK_OK;
+}
+
 const char* atucker_last_error(void) { return g_err.c_str(); }
 const char* atucker_version(void) { return "0.1.0"; }
 
@@ -583,11 +621,7 @@ struct StreamScratch {
   void* ptr = nullptr;
   cudaStream_t st;
   explicit StreamScratch(cudaStream_t s) : st(s) {}
-  int alloc(size_t bytes) {
-    cudaError_t e = cudaMallocAsync(&ptr, bytes, st);
-    if (e != cudaSuccess) { ptr = nullptr; return cuda_status(e, "cudaMallocAsync(scratch)"); }
-    return ATK_OK;
-  }
+  int alloc(size_t bytes) { return dev_alloc_async(&ptr, bytes, st, "cudaMallocAsync(scratch)"); }
   ~StreamScratch() {
     if (ptr) cudaFreeAsync(ptr, st);
   }

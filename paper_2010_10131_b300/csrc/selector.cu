@@ -179,7 +179,7 @@ struct ActBuf {
   Acts a{};
   int alloc(int B, int h, int out, cudaStream_t st) {
     const size_t bh = (size_t)B * h, bo = (size_t)B * out;
-    ATK_CUDA(cudaMallocAsync((void**)&base, sizeof(float) * (6 * bh + 2 * bo), st));
+    ATK_TRY(dev_alloc_async((void**)&base, sizeof(float) * (6 * bh + 2 * bo), st, "cudaMallocAsync(mlp buffers)"));
     a.z1 = base;
     a.a1 = a.z1 + bh;
     a.z2 = a.a1 + bh;
@@ -355,7 +355,7 @@ int atucker_mlp_train(const float* X, const float* Y, const float* M, int B, int
   sel::ActBuf buf;
   ATK_TRY(buf.alloc(B, hidden, out, st));
   float* grad = nullptr;
-  if (cudaMallocAsync((void**)&grad, sizeof(float) * (np + 1), st) != cudaSuccess) {
+  if (dev_alloc_async((void**)&grad, sizeof(float) * (np + 1), st, "cudaMallocAsync(mlp gradient)") != ATK_OK) {
     buf.release(st);
     set_error("mlp_train: out of device memory");
     return ATK_ENOMEM;

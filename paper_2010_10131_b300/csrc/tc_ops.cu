@@ -42,6 +42,7 @@
 
 #include "async_copy.cuh"
 #include "atk_internal.cuh"
+#include "tc_common.cuh"
 
 namespace atk {
 
@@ -65,33 +66,6 @@ using ac::mbar_wait;
 using ac::bulk_load;
 using ac::arrive_expect;
 
-// tcgen05 shared-memory matrix descriptor, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-template <int P>
-struct Form;
-// ES: element bytes; ARR: arrays per block (hi [, lo]); FMT: MMA operand format
-// code; KIND: 0 kind::f16, 1 kind::tf32, 2 kind::f8f6f4.
-template <>
-struct Form<ATK_TF32> {
-  static constexpr int ES = 4, ARR = 1, FMT = 2, KIND = 1;
-};
-template <>
-struct Form<ATK_BF16> {
-  static constexpr int ES = 2, ARR = 1, FMT = 1, KIND = 0;
-};
-template <>
-struct Form<ATK_BF16X3> {
-  static constexpr int ES = 2, ARR = 2, FMT = 1, KIND = 0;
-};
-template <>
-struct Form<ATK_FP8E4M3> {
-  static constexpr int ES = 1, ARR = 1, FMT = 0, KIND = 2;
-};
-
 template <int P>
 struct Blk {
   static constexpr int KB = 128 / Form<P>::ES;          // c values per block
@@ -99,20 +73,6 @@ struct Blk {
   static constexpr int W = 16 / Form<P>::ES;            // values per 16-byte piece
 };
 
-__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc, int kind) {
-  if (kind == 0)
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                 "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  else if (kind == 1)
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                 "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  else
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                 "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 
 // ---------------------------------------------------------------------------
 // Pack
@@ -146,20 +106,6 @@ __device__ __forceinline__ void load_tile(const float* __restrict__ y, int lo, i
       sm[k * PACK_LD + r] = (cv && i < n) ? __ldg(base + (int64_t)lo * i) : 0.f;
     }
   }
-}
-
-// FP8 row scale from the row max: 2^(8 - e) with max in [2^(e-1), 2^e).
-__device__ __forceinline__ float fp8_row_scale(float m) {
-  if (!(m > 0.f)) return 1.f;
-  int e;
-  frexpf(m, &e);
-  e = min(max(8 - e, -126), 127);
-  return ldexpf(1.f, e);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&h);
 }
 
 template <int P>

@@ -41,13 +41,37 @@ def test_noalloc_gram_matches_allocating_gram_twice():
     # First call: 640 rows and a long J, so the 16 MiB array caps the split count.
     # Second call: a smaller, ragged middle-mode view on the same array.
     for lo, n, hi in [(1, 640, 40000), (7, 130, 333)]:
-        y = torch.from_numpy(g.standard_normal(lo * n * hi).astype(np.float32)).cuda()
+        y_host = g.standard_normal(lo * n * hi).astype(np.float32)
+        y = torch.from_numpy(y_host).cuda()
         ref, new = _gram_both(atk, y, lo, n, hi)
         assert np.all(np.isfinite(new))
         scale = np.abs(np.diag(ref)).max()
         tol = 2e-6 * scale * max(1.0, np.sqrt(lo * hi / 8192))
         assert np.abs(new - ref).max() <= tol
         np.testing.assert_array_equal(new, new.T)
+        if n == 130:
+            # and against a float64 Gram of the same float32 data, on the host
+            y3 = y_host.astype(np.float64).reshape(hi, n, lo)
+            exact = np.einsum("bia,bja->ij", y3, y3)
+            assert np.abs(new - exact).max() <= tol
+
+
+@pytest.mark.gpu
+def test_noalloc_gram_in_rounds_at_n_2048():
+    """n = 2048 with a J needing 13 splits of at most 8192 terms: one split's
+    partial tiles (136 of 128 x 128) fill the fixed array, so the splits run
+    in 13 rounds added in float64; the chains, and so the error, match the
+    allocating entry point's."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2010_10131_b300 as atk
+    g = np.random.default_rng(7)
+    lo, n, hi = 1, 2048, 100000
+    y = torch.from_numpy(g.standard_normal(lo * n * hi).astype(np.float32)).cuda()
+    ref, new = _gram_both(atk, y, lo, n, hi)
+    scale = np.abs(np.diag(ref)).max()
+    assert np.abs(new - ref).max() <= 2e-6 * scale * np.sqrt(lo * hi / 8192)
+    np.testing.assert_array_equal(new, new.T)
 
 
 def test_noalloc_gram_rejects_sizes_beyond_its_scratch():
