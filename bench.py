@@ -490,7 +490,7 @@ def run_case(args):
     elif kind == "ttm":
         R = vals[3]
         U = torch.randn(n, R, device="cuda", generator=g)
-        fn = lambda: atk.ttm(y, lo, n, hi, U)  # noqa: E731
+        fn = lambda: atk.ttm(y, lo, n, hi, U, precision=prec)  # noqa: E731
         flops = 2.0 * n * R * lo * hi
     else:
         raise SystemExit(f"unknown case {kind}")

@@ -82,11 +82,17 @@ typedef enum {
  *   ATK_FP8E4M3  each mode-n row i scaled by the power of two
  *                s_i = 2^floor(log2(448 / max |row i|)), rounded to e4m3; the
  *                product is divided by s_i s_j exactly afterwards
+ * The tensor-core forms also run the truncating TTM of EIG modes with
+ * R_n > 16 (tcgen05, operands converted from the float32 tensor in place;
+ * below that the float32 TTM already reads Y at HBM speed); FP8 scales mode-n
+ * index i of Y by s_i as above, folds 1 / s_i into U and scales each column
+ * r of U by a power of two t_r, undone exactly after the product).
  *   ATK_FP32C    float32 on the CUDA cores with compensated sums: every
  *                product made exact (p + e with e = fma(a, b, -p)) and the
  *                running sum carried as a float-float pair (TwoSum), about
  *                48 bits per partial sum at about nine times the float32 cost
- * The eigensolver, TTM, ALS and orthonormalisation are unchanged. */
+ * The eigensolver, the ALS solver and the orthonormalisation are the same
+ * in every form; ATK_FP32C applies to the Gram (its TTM is ATK_FP32). */
 typedef enum {
   ATK_FP32 = 0, ATK_TF32 = 1, ATK_BF16 = 2, ATK_BF16X3 = 3, ATK_FP8E4M3 = 4, ATK_FP32C = 5
 } atucker_precision;
@@ -303,7 +309,10 @@ int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precisio
 int atucker_gram_noalloc(const float* y, int64_t lo, int64_t n, int64_t hi, double* S_out, void* stream);
 
 /* Truncating TTM Y' = Y x_n U^T (Eq. 2 with the matrix U^T; Alg. 2, EIG branch).
- * U: n x R float32 column-major.  out: lo x R x hi float32 column-major. */
+ * U: n x R float32 column-major.  out: lo x R x hi float32 column-major.
+ * precision: ATK_FP32 (or ATK_FP32C, the same) on the CUDA cores, R <= 1024;
+ * a tensor-core form (R <= 128) is synchronous and returns ATK_ETIMEOUT if a
+ * bounded device-side wait gave up. */
 int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* U, int64_t R, int precision,
                 float* out, void* stream);
 

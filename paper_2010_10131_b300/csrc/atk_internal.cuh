@@ -187,6 +187,15 @@ int gram_cmp(const float* y, const View& v, double* S, float* scratch, size_t sc
 size_t tc_gram_scratch_bytes(const View& v, int precision);
 int tc_gram(const float* y, const View& v, int precision, double* S, float* scratch, size_t scratch_bytes,
             int* status, cudaStream_t st);
+// max_c |Y(c, i)| for every mode-n index i (bits of the non-negative float,
+// combined by atomicMax); rmax (n floats) must be zero on entry.
+int tc_rowmax(const float* y, const View& v, float* rmax, cudaStream_t st);
+// Tensor-core TTM (tc_ttm.cu): out = Y x_n U^T in the (lo, R, hi) layout for
+// the precision forms of tc_gram, R <= 128.  Bounded waits report DEV_TIMEOUT
+// through *status.
+size_t tc_ttm_scratch_bytes(const View& v, int64_t R, int precision);
+int tc_ttm(const float* y, const View& v, const float* U, int64_t R, int precision, float* out, char* scratch,
+           size_t scratch_bytes, int* status, cudaStream_t st);
 
 // Jacobi eigensolver (jacobi.cu).
 size_t eig_scratch_bytes(int64_t n, int arith);

@@ -87,6 +87,10 @@ static void als_initial_guess(uint64_t seed, int mode, int64_t I, int64_t R, dou
 
 __global__ void sub_kernel(const double* a, const double* b, double* out) { *out = *a - *b; }
 
+// Below this rank the float32 TTM reads Y at HBM speed, and the tensor-core
+// TTM of the precision forms is no faster (measured at I_n = 128, R = 16).
+constexpr int64_t TC_TTM_MIN_R = 16;
+
 // Phase slots of atucker_plan_timings.
 enum { PH_GRAM = 0, PH_GRAM_REDUCE, PH_EIG, PH_TTM, PH_ALS, PH_OTHER, PH_TOTAL, PH_SLOTS = PH_TOTAL + 4 };
 
@@ -237,8 +241,10 @@ static int plan_alloc(atucker_plan_s* p) {
     if (p->solver[n] == ATK_EIG) {
       s_elems = std::max(s_elems, (size_t)(v.n * v.n));
       scratch = std::max(scratch, gram_scratch_bytes(v, p->gbm[n]));
-      if (p->precision != ATK_FP32 && p->precision != ATK_FP32C)
+      if (p->precision != ATK_FP32 && p->precision != ATK_FP32C) {
         scratch = std::max(scratch, tc_gram_scratch_bytes(v, p->precision));
+        scratch = std::max(scratch, tc_ttm_scratch_bytes(v, R, p->precision));
+      }
       scratch = std::max(scratch, gram_cmp_scratch_bytes(v));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP64));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP32));
@@ -513,7 +519,12 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
                         p->dev_status, p->scratch, p->scratch_bytes, st));
       }
       ATK_TRY(mark(PH_EIG));
-      ATK_TRY(ttm_f32(Y, v, U32, R, out, st));
+      // Tensor cores where the TTM is a dense contraction: with R <= 16 the
+      // float32 kernel is already bound by HBM (and exact in float32).
+      if (p->precision == ATK_FP32 || p->precision == ATK_FP32C || R <= TC_TTM_MIN_R)
+        ATK_TRY(ttm_f32(Y, v, U32, R, out, st));
+      else
+        ATK_TRY(tc_ttm(Y, v, U32, R, p->precision, out, p->scratch, p->scratch_bytes, p->dev_status, st));
       ATK_TRY(mark(PH_TTM));
     } else {
       ATK_TRY(als_mode_run(Y, v, R, p->L0 + p->l0off[n], p->als_sweeps, U32, out, p->als, st));
@@ -679,9 +690,18 @@ int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* 
   if (!y || !U || !out) { set_error("null argument"); return ATK_EINVAL; }
   ATK_TRY(check_view(lo, n, hi));
   if (R < 1 || R > 1024) { set_error("TTM needs 1 <= R <= 1024"); return ATK_EUNSUPPORTED; }
-  if (precision != ATK_FP32) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
+  if (precision < ATK_FP32 || precision > ATK_FP32C) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
   View v{lo, n, hi};
-  return ttm_f32(y, v, U, R, out, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == ATK_FP32 || precision == ATK_FP32C) return ttm_f32(y, v, U, R, out, st);
+  if (R > 128) { set_error("tensor-core TTM needs R <= 128"); return ATK_EUNSUPPORTED; }
+  StreamScratch sc(st);
+  const size_t bytes = tc_ttm_scratch_bytes(v, R, precision) + 256;
+  ATK_TRY(sc.alloc(bytes));
+  int* status = (int*)((char*)sc.ptr + bytes - 256);
+  ATK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  ATK_TRY(tc_ttm(y, v, U, R, precision, out, (char*)sc.ptr, bytes - 256, status, st));
+  return read_status(status, st);
 }
 
 int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, int eig_method, float* U_out,

@@ -456,6 +456,18 @@ int tc_gram_t(const float* y, const View& v, double* S, float* scratch, size_t s
 
 }  // namespace tc
 
+int tc_rowmax(const float* y, const View& v, float* rmax, cudaStream_t st) {
+  const size_t pack_smem = (size_t)tc::KP * tc::PACK_LD * sizeof(float);
+  static const bool attr = cudaFuncSetAttribute(tc::tc_rowmax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)pack_smem) == cudaSuccess;
+  if (!attr) { set_error("tc_rowmax: cannot set the kernel's shared-memory size"); return ATK_ECUDA; }
+  const dim3 grid((unsigned)ceil_div(v.J(), tc::KP), (unsigned)ceil_div(v.n, tc::BM));
+  tc::tc_rowmax_kernel<<<grid, tc::PACK_THREADS, pack_smem, st>>>(y, (int)v.lo, (int)v.n, v.J(),
+                                                                  reinterpret_cast<int*>(rmax));
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+
 size_t tc_gram_scratch_bytes(const View& v, int precision) {
   switch (precision) {
     case ATK_TF32: return tc::tc_scratch_t<ATK_TF32>(v);

@@ -10,7 +10,10 @@ the mixed forms are judged as in the method's statement: relative
 reconstruction error within 1e-4 of the oracle's.  FP8-e4m3 cannot meet that
 bound.  With a 3-bit mantissa the Gram is perturbed by about 2^-4 ||S||,
 which moves the captured subspace at first order (measured on the 96^3 case:
-|relerr - relerr_oracle| = 1.4e-3).  Its stated bound is 3e-3.
+|relerr - relerr_oracle| = 1.4e-3 with the float32 TTM), and each e4m3 TTM
+adds rounding noise of energy about (2^-4 / sqrt 3)^2 (R_n / I_n) ||Y||^2 to
+the core, some 1e-4 of relerr^2 per mode at R / I = 1 / 12 (measured 4.4e-3
+in all).  Its stated bound is 1e-2: the form is reported, not claimed.
 """
 import numpy as np
 import pytest
@@ -73,7 +76,7 @@ def test_mixed_precision_sthosvd_relerr(atk, prec, dims, ranks):
     ref = oracle.sthosvd(x64, dims, ranks, solver=[0] * len(dims))
     rel_g = oracle.relerr(x64, core, ranks, facs, dims)
     rel_o = oracle.relerr(x64, ref["core"], ranks, ref["factors"], dims)
-    bound = 3e-3 if prec == FP8 else 1e-4
+    bound = 1e-2 if prec == FP8 else 1e-4
     assert abs(rel_g - rel_o) <= bound, (rel_g, rel_o)
 
 
@@ -99,3 +102,25 @@ def test_mixed_precision_decaying_spectrum(atk, prec, dims, rmax):
     rel_o = oracle.relerr(x64, ref["core"], ranks, ref["factors"], dims)
     bound = 3e-4 if prec == BF16 else 1e-4
     assert abs(rel_g - rel_o) <= bound, (rel_g, rel_o)
+
+
+# TTM forms: each output is a sum of I_n products carrying relative error of
+# order u, so its error relative to max |ref| is a few u (3xBF16 keeps the
+# hi lo and lo hi terms, so only u_bf16^2 and the float32 sums remain).
+TOL_TTM = {TF32: 2e-3, BF16: 1.6e-2, BF16X3: 1e-4, FP8: 2e-1}
+
+
+@pytest.mark.parametrize("prec", [TF32, BF16, BF16X3, FP8])
+@pytest.mark.parametrize("lo,n,hi,R", [(1, 96, 2000, 8), (1, 300, 333, 64), (8, 96, 96, 8), (7, 50, 33, 17),
+                                       (4096, 20, 1, 3), (5, 130, 9, 128), (1, 33, 1, 33), (16, 9, 40, 1),
+                                       (1, 640, 700, 64), (1, 130, 257, 100)])
+def test_tc_ttm_matches_oracle(atk, prec, lo, n, hi, R):
+    """Tensor-core TTM (every view shape of the float32 TTM test, ragged c and
+    n, R up to 128) against the oracle's Eq. 2."""
+    g = np.random.default_rng(lo * 7 + n * 3 + hi + R + prec)
+    y = g.standard_normal(lo * n * hi).astype(np.float32)
+    U = (g.standard_normal((n, R)) * np.logspace(-2, 1, n)[:, None]).astype(np.float32)
+    out = atk.ttm(torch.from_numpy(y).cuda(), lo, n, hi, torch.from_numpy(U).cuda(), precision=prec).cpu().numpy()
+    ref = oracle.ttm(y.astype(np.float64), [lo, n, hi], 1, U.astype(np.float64))
+    err = np.abs(out - ref).max() / np.abs(ref).max()
+    assert err <= TOL_TTM[prec], err
