@@ -393,9 +393,23 @@ int64_t atucker_mlp_param_count(int in, int hidden, int out);
 int atucker_selector_set(const float* params, int64_t count);
 void atucker_selector_clear(void);
 
+/* The paper's own selector as an alternative (Sec. IV-B: a decision tree on
+ * Table I's features, trained offline): a binary tree of `nodes` nodes, node
+ * 0 the root.  Node i is a leaf when feature[i] < 0, choosing class
+ * leaf_class[i]; otherwise it sends a row to left[i] when
+ * features[feature[i]] <= threshold[i] (raw features, as from
+ * atucker_mode_features), else to right[i], with both children numbered after
+ * i.  Loading a tree makes it the active selector (AUTO and
+ * atucker_selector_predict) until atucker_selector_set loads a network or
+ * atucker_selector_clear removes both.  Process-wide; the arrays are copied. */
+int atucker_selector_set_tree(int nodes, const int* feature, const double* threshold, const int* left,
+                              const int* right, const int* leaf_class);
+
 /* Host inference of the loaded selector on `rows` raw feature rows (rows x 12,
  * as from atucker_mode_features): class_out[rows] the chosen class,
- * scores_out (nullable) rows x ATK_NUM_CLASSES network outputs. */
+ * scores_out (nullable) rows x ATK_NUM_CLASSES network outputs (for a tree:
+ * 0 for the chosen class, 1 for the others).  A mode with I_n > 1024 gets
+ * ATK_CLASS_ALS. */
 int atucker_selector_predict(const double* features, int rows, int* class_out, float* scores_out);
 
 /* GPU training of the network (the project's own CUDA kernels).  All pointers

@@ -82,6 +82,7 @@ _SIGS = {
     "atucker_mlp_param_count": (_i64, [_i32, _i32, _i32]),
     "atucker_selector_set": (_i32, [_vp, _i64]),
     "atucker_selector_clear": (None, []),
+    "atucker_selector_set_tree": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp]),
     "atucker_selector_predict": (_i32, [_vp, _i32, _vp, _vp]),
     "atucker_mlp_forward": (_i32, [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp]),
     "atucker_mlp_loss_grad": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),

@@ -18,11 +18,19 @@
 namespace atk {
 namespace sel {
 
+// The active selector is the MLP (kind 0) or the decision tree (kind 1),
+// whichever was loaded last.
+struct Tree {
+  std::vector<int> feature, left, right, cls;
+  std::vector<double> threshold;
+};
 struct State {
   std::mutex mu;
   bool loaded = false;
+  int kind = 0;
   float fmean[ATK_SELECTOR_FEATURES], fscale[ATK_SELECTOR_FEATURES];
   std::vector<float> params;
+  Tree tree;
 };
 State& state() {
   static State s;
@@ -259,6 +267,38 @@ int atucker_selector_set(const float* params, int64_t count) {
   }
   s.params.assign(params + 2 * ATK_SELECTOR_FEATURES, params + count);
   s.loaded = true;
+  s.kind = 0;
+  return ATK_OK;
+}
+
+int atucker_selector_set_tree(int nodes, const int* feature, const double* threshold, const int* left,
+                              const int* right, const int* leaf_class) {
+  if (nodes < 1 || nodes > (1 << 20) || !feature || !threshold || !left || !right || !leaf_class) {
+    set_error("selector_set_tree: bad arguments");
+    return ATK_EINVAL;
+  }
+  for (int i = 0; i < nodes; ++i) {
+    if (feature[i] < 0) {
+      if (leaf_class[i] < 0 || leaf_class[i] >= ATK_NUM_CLASSES) {
+        set_error("selector_set_tree: leaf class out of range");
+        return ATK_EINVAL;
+      }
+    } else if (feature[i] >= ATK_SELECTOR_FEATURES || left[i] <= i || right[i] <= i || left[i] >= nodes ||
+               right[i] >= nodes || !(threshold[i] == threshold[i])) {
+      // children after their parent: every path ends, no cycle
+      set_error("selector_set_tree: bad split node");
+      return ATK_EINVAL;
+    }
+  }
+  auto& s = sel::state();
+  std::lock_guard<std::mutex> g(s.mu);
+  s.tree.feature.assign(feature, feature + nodes);
+  s.tree.threshold.assign(threshold, threshold + nodes);
+  s.tree.left.assign(left, left + nodes);
+  s.tree.right.assign(right, right + nodes);
+  s.tree.cls.assign(leaf_class, leaf_class + nodes);
+  s.loaded = true;
+  s.kind = 1;
   return ATK_OK;
 }
 
@@ -267,6 +307,7 @@ void atucker_selector_clear(void) {
   std::lock_guard<std::mutex> g(s.mu);
   s.loaded = false;
   s.params.clear();
+  s.tree = sel::Tree{};
 }
 
 int atucker_selector_predict(const double* features, int rows, int* class_out, float* scores_out) {
@@ -275,6 +316,20 @@ int atucker_selector_predict(const double* features, int rows, int* class_out, f
   std::lock_guard<std::mutex> g(s.mu);
   if (!s.loaded) { set_error("selector_predict: no selector loaded"); return ATK_EINVAL; }
   constexpr int IN = ATK_SELECTOR_FEATURES, H = ATK_SELECTOR_HIDDEN, K = ATK_NUM_CLASSES;
+  if (s.kind == 1) {
+    const sel::Tree& t = s.tree;
+    for (int r = 0; r < rows; ++r) {
+      const double* f = features + (int64_t)r * IN;
+      int node = 0;
+      while (t.feature[node] >= 0) node = f[t.feature[node]] <= t.threshold[node] ? t.left[node] : t.right[node];
+      int c = t.cls[node];
+      if (c != ATK_CLASS_ALS && f[0] > 10.0 + 1e-9) c = ATK_CLASS_ALS;  // EIG classes need I_n <= 1024
+      class_out[r] = c;
+      if (scores_out)
+        for (int k = 0; k < K; ++k) scores_out[(int64_t)r * K + k] = k == c ? 0.f : 1.f;
+    }
+    return ATK_OK;
+  }
   const float* W1 = s.params.data();
   const float* b1 = W1 + H * IN;
   const float* W2 = b1 + H;

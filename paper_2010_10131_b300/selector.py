@@ -325,9 +325,154 @@ def train_and_evaluate(timings=TIMINGS, extra=TIMINGS_EXTRA, n_train: int = 192,
     return report, packed
 
 
+# ------------------------------------------- decision tree (the paper's selector)
+# Sec. IV-B trains a decision tree classifier on Table I's features to pick
+# the solver.  Here, as a baseline for the MLP: a CART tree (Gini impurity,
+# binary splits at midpoints between consecutive distinct values, depth <= 10)
+# on the ten Table I features, labelled with the fastest measured class of
+# each (shape, mode).  Features enter as the library computes them (log2):
+# a tree's splits are invariant under monotone maps of a feature.  Training is
+# an offline host step; inference runs in the library
+# (atucker_selector_set_tree / atucker_selector_predict).
+TABLE_I = tuple(range(10))
+
+
+def best_labels(T):
+    """Fastest measured class of every row, -1 where none was measured."""
+    T = np.asarray(T, dtype=np.float64)
+    ok = np.isfinite(T).any(axis=1)
+    lab = np.full(len(T), -1, dtype=np.int64)
+    lab[ok] = np.nanargmin(np.where(np.isfinite(T[ok]), T[ok], np.nan), axis=1)
+    return lab
+
+
+def _gini(counts):
+    n = counts.sum(axis=-1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        p = counts / np.maximum(n, 1)[..., None]
+    return 1.0 - (p * p).sum(axis=-1)
+
+
+def fit_tree(F, labels, max_depth: int = 10, min_leaf: int = 2, features=TABLE_I, n_classes: int = NUM_CLASSES):
+    """CART classification tree.  Returns a dict of node arrays (feature,
+    threshold, left, right, cls) in creation order (children after their
+    parent), as atucker_selector_set_tree takes them."""
+    F = np.asarray(F, dtype=np.float64)
+    y = np.asarray(labels, dtype=np.int64)
+    keep = y >= 0
+    F, y = F[keep], y[keep]
+    nodes = {"feature": [], "threshold": [], "left": [], "right": [], "cls": [], "depth": []}
+
+    def new_node(depth):
+        for k in nodes:
+            nodes[k].append(-1 if k != "threshold" else 0.0)
+        nodes["depth"][-1] = depth
+        return len(nodes["feature"]) - 1
+
+    root = new_node(0)
+    stack = [(root, np.arange(len(y)), 0)]
+    while stack:
+        node, idx, depth = stack.pop()
+        counts = np.bincount(y[idx], minlength=n_classes).astype(np.float64)
+        nodes["cls"][node] = int(np.argmax(counts))  # majority, ties to the lower class
+        if depth >= max_depth or len(idx) < 2 * min_leaf or counts.max() == len(idx):
+            continue
+        parent = _gini(counts) * len(idx)
+        best = (parent - 1e-12, None, None)
+        for f in features:
+            order = idx[np.argsort(F[idx, f], kind="stable")]
+            v = F[order, f]
+            onehot = np.zeros((len(order), n_classes))
+            onehot[np.arange(len(order)), y[order]] = 1.0
+            left = np.cumsum(onehot, axis=0)[:-1]
+            right = counts[None, :] - left
+            nl = np.arange(1, len(order))
+            nr = len(order) - nl
+            cost = _gini(left) * nl + _gini(right) * nr
+            valid = (v[1:] > v[:-1]) & (nl >= min_leaf) & (nr >= min_leaf)
+            if not valid.any():
+                continue
+            j = int(np.argmin(np.where(valid, cost, np.inf)))
+            if cost[j] < best[0]:
+                best = (cost[j], f, 0.5 * (v[j] + v[j + 1]))
+        if best[1] is None:
+            continue
+        f, thr = best[1], best[2]
+        go_left = F[idx, f] <= thr
+        li, ri = new_node(depth + 1), new_node(depth + 1)
+        nodes["feature"][node], nodes["threshold"][node] = int(f), float(thr)
+        nodes["left"][node], nodes["right"][node] = li, ri
+        stack.append((ri, idx[~go_left], depth + 1))
+        stack.append((li, idx[go_left], depth + 1))
+    return {k: np.asarray(v) for k, v in nodes.items()}
+
+
+def tree_predict_host(tree, F) -> np.ndarray:
+    """The tree's class for every row (numpy walk; the library's
+    atucker_selector_predict does the same in C)."""
+    F = np.asarray(F, dtype=np.float64)
+    out = np.empty(len(F), dtype=np.int64)
+    for r, f in enumerate(F):
+        node = 0
+        while tree["feature"][node] >= 0:
+            node = tree["left"][node] if f[tree["feature"][node]] <= tree["threshold"][node] else tree["right"][node]
+        out[r] = tree["cls"][node]
+    return out
+
+
+def install_tree(tree) -> None:
+    """Make the tree the library's active selector (atucker_selector_set_tree)."""
+    n = len(tree["feature"])
+    feat = np.ascontiguousarray(tree["feature"], dtype=np.int32)
+    thr = np.ascontiguousarray(tree["threshold"], dtype=np.float64)
+    left = np.ascontiguousarray(tree["left"], dtype=np.int32)
+    right = np.ascontiguousarray(tree["right"], dtype=np.int32)
+    cls = np.ascontiguousarray(tree["cls"], dtype=np.int32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().atucker_selector_set_tree(n, vp(feat), vp(thr), vp(left), vp(right), vp(cls)),
+           "atucker_selector_set_tree")
+
+
+def inference_us(F, reps: int = 20) -> float:
+    """Host inference time of the active selector, microseconds per mode."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    predict(F)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        predict(F)
+    return (time.perf_counter() - t0) / reps / len(F) * 1e6
+
+
+def compare_tree_mlp(timings=TIMINGS, extra=TIMINGS_EXTRA, n_train: int = 192, max_depth: int = 10):
+    """The paper's decision tree against the installed MLP on the held-out
+    shapes: regret, gain over always-EIG and host inference time per mode.
+    The tree is trained on the same timing sets as the installed network
+    (the first n_train shapes plus the extra set).  Leaves the installed
+    network active afterwards."""
+    shapes, times = load_timings(timings)
+    F, T = dataset(shapes[:n_train], times[:n_train])
+    if extra and os.path.exists(extra):
+        es, et = load_timings(extra)
+        Fe, Te = dataset(es, et)
+        F, T = np.concatenate([F, Fe]), np.concatenate([T, Te])
+    Fh, Th = dataset(shapes[n_train:], times[n_train:])
+    rows = shape_rows(shapes[n_train:])
+    out = {}
+    if install():
+        out["mlp"] = dict(evaluate(Fh, Th, rows), inference_us_per_mode=inference_us(Fh))
+    tree = fit_tree(F, best_labels(T), max_depth=max_depth)
+    install_tree(tree)
+    out["tree"] = dict(evaluate(Fh, Th, rows), inference_us_per_mode=inference_us(Fh),
+                       nodes=int(len(tree["feature"])), depth=int(tree["depth"].max()),
+                       train_modes=int(len(F)))
+    lib().atucker_selector_clear()
+    install()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2010_10131_b300.selector")
-    ap.add_argument("cmd", choices=["collect", "train"])
+    ap.add_argument("cmd", choices=["collect", "train", "tree"])
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--train", type=int, default=192)
@@ -343,6 +488,9 @@ def main(argv=None):
         with open(args.timings, "w") as f:
             json.dump({"shapes": shapes, "classes": list(CLASS_NAMES),
                        "times_ms": [np.where(np.isfinite(t), t, -1.0).tolist() for t in times]}, f)
+        return 0
+    if args.cmd == "tree":
+        print(json.dumps(compare_tree_mlp(args.timings, args.extra, n_train=args.train)))
         return 0
     report, packed = train_and_evaluate(args.timings, args.extra, n_train=args.train, steps=args.steps)
     with open(args.weights, "w") as f:
