@@ -437,6 +437,12 @@ def run_case(args):
     if kind == "precision":
         print(json.dumps({"case": "precision", "sweep": run_precision(args)}), flush=True)
         return 0
+    if kind == "table2":
+        print(json.dumps({"case": "table2", "stand_ins": run_table2(args)}), flush=True)
+        return 0
+    if kind == "explicit":
+        print(json.dumps({"case": "explicit", "ablation": run_explicit(args)}), flush=True)
+        return 0
     if kind == "batchrun":
         # The batched kernel alone (fixed launch variant, no tuning and no
         # one-at-a-time leg): the command profiles of the kernel use.
@@ -680,6 +686,129 @@ def run_selector(args, e2e_shapes: int = 64):
                             "inputs": "random Tucker + 1e-3 noise built on the GPU, new seeds"}
     report["train_s"] = train_s
     return report
+
+
+# Table II of the paper (its six real tensors, not available here) as
+# synthetic stand-ins: the same shapes and truncations, random Tucker cores
+# with those ranks plus 10 % noise (the real tensors' errors are 0.2 - 0.9).
+# MNIST's R_2 = 142 is clamped to the library's rank limit of 128.
+TABLE_II = (("MNIST", (784, 5000, 10), (65, 128, 10)),
+            ("Cavity", (100, 100, 10000), (20, 20, 20)),
+            ("Boats", (320, 240, 7000), (10, 10, 10)),
+            ("Air", (30648, 376, 6), (10, 10, 5)),
+            ("Video", (112, 160, 3, 32), (10, 10, 3, 32)),
+            ("HSI", (1021, 1340, 33, 8), (10, 10, 10, 5)))
+
+
+def random_tucker_big(dims, ranks, seed, noise):
+    """Random Tucker signal scaled to RMS 1 per element plus noise * N(0,1),
+    built on the GPU (the stand-ins are too large to build on the host),
+    column-major flat.  With 10 % noise the relative errors land where the
+    paper's real tensors do (0.1 - 0.4) and the signal stays above the noise."""
+    import torch
+    from paper_2010_10131_b300 import selector
+    x = selector.random_tucker_gpu(dims, ranks, seed, noise=0.0)
+    x *= (1.0 / torch.sqrt(torch.mean(x.double() ** 2))).float()
+    g = torch.Generator(device="cuda").manual_seed(int(seed) + 1)
+    x += noise * torch.randn(x.shape, device="cuda", generator=g)
+    return x
+
+
+def reconstruct_relerr(x, core, facs, dims, ranks):
+    """||X - G x_1 U1 ... x_N UN|| / ||X|| on the GPU (float64 sums)."""
+    import torch
+    N = len(dims)
+    g = core.view(*reversed(ranks)).double()
+    for n in range(N):
+        ax = N - 1 - n
+        g = torch.movedim(torch.tensordot(facs[n].double(), g, dims=([1], [ax])), 0, ax)
+    xx = x.view(*reversed(dims)).double()
+    return float(torch.linalg.norm(xx - g) / torch.linalg.norm(xx))
+
+
+def time_plan(x, dims, ranks, steps, warmup, **kw):
+    """ms per st-HOSVD (CUDA events), device memory the plan took (free memory
+    before creation minus after the first run) and the result."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    explicit = kw.pop("explicit", 0)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    p = atk.Plan(dims, ranks, **kw)
+    if explicit:
+        p.set_option(atk.OPT_EXPLICIT_UNFOLD, 1)
+    core = torch.empty(p.core_numel, device="cuda")
+    fac = torch.empty(p.factors_numel, device="cuda")
+    for _ in range(max(warmup, 1)):
+        p.run(x, core, fac)
+    p.sync()
+    mem = free0 - torch.cuda.mem_get_info()[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(max(steps, 1)):
+        p.run(x, core, fac)
+    e1.record()
+    p.sync()
+    ms = e0.elapsed_time(e1) / max(steps, 1)
+    facs = [f.view(r, d).t() for f, d, r in zip(torch.split(fac, [d * r for d, r in zip(dims, ranks)]), dims, ranks)]
+    classes = p.classes
+    p.close()
+    return ms, mem, core, facs, classes
+
+
+def run_table2(args):
+    """The Table II stand-ins with EIG in every mode, ALS in every mode and
+    the learned selector (AUTO): time, device memory and relative error."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    from paper_2010_10131_b300 import selector
+    selector.install()
+    out = []
+    for i, (name, dims, ranks) in enumerate(TABLE_II):
+        x = random_tucker_big(dims, ranks, 7000 + i, noise=0.1)
+        row = {"name": name, "dims": list(dims), "ranks": list(ranks), "solvers": {}}
+        for sname, sv in (("EIG", atk.EIG), ("ALS", atk.ALS), ("AUTO", atk.AUTO)):
+            try:
+                ms, mem, core, facs, cls = time_plan(x, list(dims), list(ranks), args.steps, args.warmup,
+                                                     solver=[sv] * len(dims))
+                row["solvers"][sname] = {"ms": ms, "gbs": x.numel() * 4 / (ms * 1e-3) / 1e9,
+                                         "plan_mem_gb": mem / 1e9,
+                                         "relerr": reconstruct_relerr(x, core, facs, dims, ranks)}
+                if sv == atk.AUTO:
+                    row["solvers"][sname]["classes"] = [atk.CLASS_NAMES[c] for c in cls]
+            except Exception as e:  # a solver that cannot run this shape
+                row["solvers"][sname] = {"error": str(e)[:160]}
+            torch.cuda.empty_cache()
+        out.append(row)
+        del x
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_explicit(args):
+    """Ablation of the matricization-free design (Sec. VI-E): the same plans
+    with every mode with I_<n > 1 explicitly unfolded into a buffer and the
+    result folded back (ATK_OPT_EXPLICIT_UNFOLD), EIG every mode; time and the
+    device memory each plan took."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    shapes = [("640^3 R64", (640, 640, 640), (64, 64, 64)), ("128^4 R16", (128, 128, 128, 128), (16, 16, 16, 16))]
+    shapes += [(n, d, r) for n, d, r in TABLE_II if n in ("Cavity", "Boats", "Video", "HSI")]
+    out = []
+    for i, (name, dims, ranks) in enumerate(shapes):
+        x = random_tucker_big(dims, ranks, 8000 + i, noise=0.1)
+        row = {"name": name, "dims": list(dims), "ranks": list(ranks)}
+        for label, ex in (("free", 0), ("explicit", 1)):
+            ms, mem, core, facs, _ = time_plan(x, list(dims), list(ranks), args.steps, args.warmup,
+                                               solver=[atk.EIG] * len(dims), explicit=ex)
+            row[label] = {"ms": ms, "plan_mem_gb": mem / 1e9, "relerr": reconstruct_relerr(x, core, facs, dims, ranks)}
+            torch.cuda.empty_cache()
+        row["speedup_free_vs_explicit"] = row["explicit"]["ms"] / row["free"]["ms"]
+        row["memory_saved"] = 1.0 - row["free"]["plan_mem_gb"] / max(row["explicit"]["plan_mem_gb"], 1e-12)
+        out.append(row)
+        del x
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():

@@ -24,8 +24,11 @@
  *   - Every call returns an atucker_status.  On failure, atucker_last_error()
  *     returns a thread-local message.  A status of ATK_ECUDA means the CUDA
  *     runtime reported an error.  The library does not reset the device.
- *   - Size limits: order <= 8, every I_n <= 1024 for EIG modes (Gram + Jacobi),
- *     R_n <= 128, and the tensor has fewer than 2^31 elements.
+ *   - Size limits: order <= 8, R_n <= 128, fewer than 2^31 elements.  EIG
+ *     modes: I_n <= 1024 for the full Jacobi eigensolver, I_n <= 32768 for
+ *     the subspace eigensolver (float32 rotations, R_n + p <= I_n / 2 with
+ *     the guard p of atucker_eig_method; its n x n float64 Gram and float32
+ *     copy take 12 n^2 bytes of device memory, 11 GB at 30648).
  */
 #ifndef ATUCKER_H
 #define ATUCKER_H
@@ -143,7 +146,17 @@ typedef enum {
    * at their next wait, so the kernel ends on its own and the next
    * atucker_plan_sync reports ATK_ETIMEOUT.  The results of such a run are
    * not usable; the plan is.  Small values exist to test that path. */
-  ATK_OPT_WAIT_LIMIT = 7
+  ATK_OPT_WAIT_LIMIT = 7,
+  /* 1: explicit matricization, the baseline that Sec. V removes (the
+   * ablation of Sec. VI-E).  Before each mode with I_<n > 1 the tensor's
+   * mode-n unfolding is copied into a buffer (a batched transpose of the
+   * view's slabs), the mode's Gram, eigensolver, TTM or ALS run on that
+   * matrix as a mode-1 view, and the R_n x J_n result is transposed back into
+   * the core's natural layout.  Same arithmetic, so the same results to
+   * rounding; extra device memory (allocated at the first such run): the
+   * largest unfolding plus the largest TTM result.  0 (default): the
+   * matricization-free path. */
+  ATK_OPT_EXPLICIT_UNFOLD = 8
 } atucker_option;
 
 typedef struct atucker_plan_s* atucker_plan_t;
@@ -329,7 +342,8 @@ int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* 
  *               the remaining eigenvalues, descending, from the full Jacobi
  *               (NaN when the subspace method ran)
  *   discarded_out 1 float64 (nullable): trace(S) minus the kept eigenvalues
- * Needs 1 <= R <= n <= 1024 and R <= 128.  Returns ATK_ENOCONV if a sweep cap
+ * Needs 1 <= R <= 128 and R <= n <= 1024, or n <= 32768 on the subspace path
+ * (ATK_EUNSUPPORTED otherwise).  Returns ATK_ENOCONV if a sweep cap
  * was reached.  Synchronous. */
 int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, int eig_method, float* U_out,
                 double* lambda_out, double* discarded_out, void* stream);
@@ -408,8 +422,9 @@ int atucker_selector_set_tree(int nodes, const int* feature, const double* thres
 /* Host inference of the loaded selector on `rows` raw feature rows (rows x 12,
  * as from atucker_mode_features): class_out[rows] the chosen class,
  * scores_out (nullable) rows x ATK_NUM_CLASSES network outputs (for a tree:
- * 0 for the chosen class, 1 for the others).  A mode with I_n > 1024 gets
- * ATK_CLASS_ALS. */
+ * 0 for the chosen class, 1 for the others).  A class is chosen only where
+ * it can run: the full-Jacobi classes need I_n <= 1024, the other EIG
+ * classes I_n <= 32768; beyond that the mode gets ATK_CLASS_ALS. */
 int atucker_selector_predict(const double* features, int rows, int* class_out, float* scores_out);
 
 /* GPU training of the network (the project's own CUDA kernels).  All pointers

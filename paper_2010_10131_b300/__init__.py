@@ -28,7 +28,7 @@ EIG, ALS = 0, 1
 FP32, TF32, BF16, BF16X3, FP8E4M3, FP32C = 0, 1, 2, 3, 4, 5
 EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
 OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD, OPT_GRAM_REFINE = 1, 2, 3, 4, 5, 6
-OPT_WAIT_LIMIT = 7
+OPT_WAIT_LIMIT, OPT_EXPLICIT_UNFOLD = 7, 8
 EIG_AUTO, EIG_FULL_JACOBI, EIG_SUBSPACE = 0, 1, 2
 BATCH_OPT_VARIANT, BATCH_OPT_GRAPH, BATCH_OPT_SYNC, BATCH_OPT_JACOBI_MAX_SWEEPS = 1, 2, 3, 4
 AUTO = -1

@@ -190,12 +190,21 @@ int tc_gram(const float* y, const View& v, int precision, double* S, float* scra
 // max_c |Y(c, i)| for every mode-n index i (bits of the non-negative float,
 // combined by atomicMax); rmax (n floats) must be zero on entry.
 int tc_rowmax(const float* y, const View& v, float* rmax, cudaStream_t st);
+// Explicit matricization (matricize.cu): dst slab b (B x A) = transpose of
+// src slab b (A x B), both column-major, b < count.
+int permute_slabs(const float* src, int64_t A, int64_t B, int64_t count, float* dst, cudaStream_t st);
+
 // Tensor-core TTM (tc_ttm.cu): out = Y x_n U^T in the (lo, R, hi) layout for
 // the precision forms of tc_gram, R <= 128.  Bounded waits report DEV_TIMEOUT
 // through *status.
 size_t tc_ttm_scratch_bytes(const View& v, int64_t R, int precision);
 int tc_ttm(const float* y, const View& v, const float* U, int64_t R, int precision, float* out, char* scratch,
            size_t scratch_bytes, int* status, cudaStream_t st);
+
+// Size limits of EIG modes: the full Jacobi eigensolver works on I_n <= 1024;
+// the subspace eigensolver (R_n + p <= I_n / 2) on I_n <= EIG_MAX_N.
+constexpr int64_t JACOBI_MAX_N = 1024;
+constexpr int64_t EIG_MAX_N = 32768;
 
 // Jacobi eigensolver (jacobi.cu).
 size_t eig_scratch_bytes(int64_t n, int arith);

@@ -994,7 +994,7 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
 // Scratch of one level (eig_level): the Ritz block, then the largest of the
 // solvers' and the refinement's needs.
 static size_t level_scratch_bytes(int64_t n, int arith) {
-  size_t jac = arith == ATK_EIG_ROT_FP64 ? eig_bytes_t<double>(n) : eig_bytes_t<float>(n);
+  size_t jac = n > JACOBI_MAX_N ? 0 : arith == ATK_EIG_ROT_FP64 ? eig_bytes_t<double>(n) : eig_bytes_t<float>(n);
   size_t rr = rr_bytes(n, 156);
   const int64_t kmax = std::min<int64_t>(n, 156);
   // the Ritz block is carved first and outlives the solver that fills it
@@ -1122,6 +1122,11 @@ static int eig_level(const double* S, int64_t n, int64_t R, int arith, int metho
       ATK_CUDA(cudaMemsetAsync(lambda_out + R, 0xFF, sizeof(double) * (n - R), st));
     }
   }
+  if (s != ATK_OK && n > JACOBI_MAX_N) {
+    set_error(rr ? "eig: the subspace eigensolver did not converge and I_n > 1024 has no full-Jacobi fallback"
+                 : "eig: I_n > 1024 needs the subspace eigensolver (float32 rotations, R + p <= I_n / 2)");
+    return rr ? ATK_ENOCONV : ATK_EUNSUPPORTED;
+  }
   if (s != ATK_OK) {
     // Full Jacobi: the k leading vectors (and all eigenvalues) of the whole matrix.
     s = arith == ATK_EIG_ROT_FP64
@@ -1200,7 +1205,10 @@ constexpr double DEFLATE_KEEP_REL = 1e-10;
 int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, float* U_out,
             double* U64_out, double* lambda_out, double* discarded_out, int* dev_status, char* scratch,
             size_t scratch_bytes, cudaStream_t st, int* unresolved) {
-  if (n <= 0 || R <= 0 || R > n || n > 1024) { set_error("eig: need 1 <= R <= n <= 1024"); return ATK_EUNSUPPORTED; }
+  if (n <= 0 || R <= 0 || R > n || n > EIG_MAX_N) {
+    set_error("eig: need 1 <= R <= n <= 32768");
+    return ATK_EUNSUPPORTED;
+  }
   if (unresolved) *unresolved = 0;
   Arena ar{scratch, scratch_bytes, 0};
   double* lam_s = (double*)ar.take(sizeof(double) * 160);

@@ -155,6 +155,9 @@ struct atucker_plan_s {
   cudaStream_t st = nullptr;
   int eig_arith = ATK_EIG_ROT_FP32, eig_method = ATK_EIG_AUTO, sync = 0, max_sweeps = 40, gram_refine = 1;
   long long wait_polls = 0;  // ATK_OPT_WAIT_LIMIT (0: default)
+  int explicit_unfold = 0;   // ATK_OPT_EXPLICIT_UNFOLD
+  float* xunf = nullptr;     // unfolding buffer and TTM result of the explicit form (one allocation)
+  float* xttm = nullptr;
   // device workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -218,7 +221,7 @@ static int validate(int order, const int64_t* dims, const int64_t* ranks, const 
       set_error("solver_per_mode entries must be 0 (EIG), 1 (ALS) or -1 (AUTO)");
       return ATK_EINVAL;
     }
-    if (s == ATK_EIG && dims[k] > 1024) { set_error("EIG modes need I_n <= 1024"); return ATK_EUNSUPPORTED; }
+    if (s == ATK_EIG && dims[k] > EIG_MAX_N) { set_error("EIG modes need I_n <= 32768"); return ATK_EUNSUPPORTED; }
   }
   return ATK_OK;
 }
@@ -349,6 +352,12 @@ int atucker_plan_create_classes(atucker_plan_t* plan, int order, const int64_t* 
     solver[k] = class_per_mode[k] == ATK_CLASS_ALS ? ATK_ALS : ATK_EIG;
   }
   ATK_TRY(validate(order, dims, ranks, mode_order, solver));
+  for (int k = 0; k < order; ++k)
+    if ((class_per_mode[k] == ATK_CLASS_EIG_JACOBI || class_per_mode[k] == ATK_CLASS_EIG_JACOBI_SMALL) &&
+        dims[k] > JACOBI_MAX_N) {
+      set_error("the full-Jacobi classes need I_n <= 1024");
+      return ATK_EUNSUPPORTED;
+    }
   if (precision < ATK_FP32 || precision > ATK_FP32C) { set_error("unsupported precision"); return ATK_EUNSUPPORTED; }
   atucker_plan_s* p = new atucker_plan_s();
   p->order = order;
@@ -438,6 +447,10 @@ int atucker_plan_set_option(atucker_plan_t p, int key, int64_t value) {
       if (value < 0) break;
       p->wait_polls = value;
       return ATK_OK;
+    case ATK_OPT_EXPLICIT_UNFOLD:
+      if (value != 0 && value != 1) break;
+      p->explicit_unfold = (int)value;
+      return ATK_OK;
     default:
       break;
   }
@@ -457,8 +470,34 @@ int atucker_plan_sync(atucker_plan_t p) {
   return ATK_OK;
 }
 
+// Buffers of the explicit-matricization form, at its first run: the largest
+// unfolding of a mode with lo > 1 and the largest R x J TTM result.
+static int explicit_buffers(atucker_plan_t p) {
+  if (p->xunf) return ATK_OK;
+  int64_t cur[8];
+  for (int k = 0; k < p->order; ++k) cur[k] = p->dims[k];
+  size_t unf = 1, ttm = 1;
+  for (int step = 0; step < p->order; ++step) {
+    const int n = p->mode_order[step];
+    const View v = make_view(p->order, cur, n);
+    if (v.lo > 1) {
+      unf = std::max(unf, (size_t)v.size());
+      ttm = std::max(ttm, (size_t)(v.J() * p->ranks[n]));
+    }
+    cur[n] = p->ranks[n];
+  }
+  char* base = nullptr;
+  const size_t need = 4 * (unf + ttm) + 512;
+  ATK_TRY(dev_alloc((void**)&base, need, "cudaMalloc(explicit unfolding)"));
+  Arena ar{base, need, 0};
+  p->xunf = (float*)ar.take(4 * unf);
+  p->xttm = (float*)ar.take(4 * ttm);
+  return ATK_OK;
+}
+
 static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float* factors_out, double* discarded_out) {
   cudaStream_t st = p->st;
+  if (p->explicit_unfold) ATK_TRY(explicit_buffers(p));
   int64_t cur[8];
   for (int k = 0; k < p->order; ++k) cur[k] = p->dims[k];
   const float* Y = x;
@@ -481,10 +520,18 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
   }
   for (int step = 0; step < p->order; ++step) {
     const int n = p->mode_order[step];
-    const View v = make_view(p->order, cur, n);
+    const View vn = make_view(p->order, cur, n);
     cudaEvent_t e_mode = e_prev;
     const int64_t R = p->ranks[n];
-    float* out = (step == p->order - 1) ? core_out : p->buf[step & 1];
+    float* const out_final = (step == p->order - 1) ? core_out : p->buf[step & 1];
+    // Explicit form: the mode-n unfolding is materialised and the mode's
+    // contractions run on its mode-1 view; their (R, J) result is folded
+    // into out_final after the mode.
+    const bool unfold = p->explicit_unfold && vn.lo > 1;
+    if (unfold) ATK_TRY(permute_slabs(Y, vn.lo, vn.n, vn.hi, p->xunf, st));
+    const View v = unfold ? View{1, vn.n, vn.J()} : vn;
+    if (unfold) Y = p->xunf;
+    float* out = unfold ? p->xttm : out_final;
     float* U32 = factors_out + p->foff[n];
     double* disc = discarded_out ? discarded_out + n : nullptr;
     if (p->solver[n] == ATK_EIG) {
@@ -537,9 +584,10 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
         ATK_TRY(mark(PH_OTHER));
       }
     }
+    if (unfold) ATK_TRY(permute_slabs(p->xttm, R, vn.lo, vn.hi, out_final, st));
     if (tm) p->mrecs.push_back({n, e_mode, e_prev});
     cur[n] = R;
-    Y = out;
+    Y = out_final;
   }
   if (tm) p->recs.push_back({PH_TOTAL, e_first, e_prev});
   if (p->order == 0) return ATK_OK;
@@ -606,6 +654,7 @@ void atucker_plan_destroy(atucker_plan_t p) {
   for (cudaEvent_t e : p->evpool) cudaEventDestroy(e);
   if (p->ws) cudaFree(p->ws);
   if (p->x_dev) cudaFree(p->x_dev);
+  if (p->xunf) cudaFree(p->xunf);
   delete p;
 }
 
@@ -707,8 +756,8 @@ int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* 
 int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, int eig_method, float* U_out,
                 double* lambda_out, double* discarded_out, void* stream) {
   if (!S || !U_out) { set_error("null argument"); return ATK_EINVAL; }
-  if (n < 1 || R < 1 || R > n || n > 1024 || R > 128) {
-    set_error("need 1 <= R <= n <= 1024 and R <= 128");
+  if (n < 1 || R < 1 || R > n || n > EIG_MAX_N || R > 128) {
+    set_error("need 1 <= R <= n <= 32768 and R <= 128");
     return ATK_EUNSUPPORTED;
   }
   if (eig_arith != ATK_EIG_ROT_FP32 && eig_arith != ATK_EIG_ROT_FP64) { set_error("bad eig_arith"); return ATK_EINVAL; }

@@ -32,6 +32,14 @@ struct State {
   std::vector<float> params;
   Tree tree;
 };
+// Whether a class can run a mode of log2 size lg: the full-Jacobi classes
+// need I_n <= 1024, the other EIG classes I_n <= 32768 (feature 0 is log2 I_n).
+bool class_fits(int k, double lg) {
+  if (k == ATK_CLASS_ALS) return true;
+  const bool jac = k == ATK_CLASS_EIG_JACOBI || k == ATK_CLASS_EIG_JACOBI_SMALL;
+  return lg <= (jac ? 10.0 : 15.0) + 1e-9;
+}
+
 State& state() {
   static State s;
   return s;
@@ -323,7 +331,7 @@ int atucker_selector_predict(const double* features, int rows, int* class_out, f
       int node = 0;
       while (t.feature[node] >= 0) node = f[t.feature[node]] <= t.threshold[node] ? t.left[node] : t.right[node];
       int c = t.cls[node];
-      if (c != ATK_CLASS_ALS && f[0] > 10.0 + 1e-9) c = ATK_CLASS_ALS;  // EIG classes need I_n <= 1024
+      if (!sel::class_fits(c, f[0])) c = ATK_CLASS_ALS;
       class_out[r] = c;
       if (scores_out)
         for (int k = 0; k < K; ++k) scores_out[(int64_t)r * K + k] = k == c ? 0.f : 1.f;
@@ -355,11 +363,9 @@ int atucker_selector_predict(const double* features, int rows, int* class_out, f
       for (int q = 0; q < H; ++q) a = std::fma(W3[k * H + q], h2[q], a);
       o[k] = a;
     }
-    // EIG classes need I_n <= 1024 (feature 0 is log2 I_n).
-    const bool eig_ok = f[0] <= 10.0 + 1e-9;
     int best = ATK_CLASS_ALS;
     for (int k = 0; k < K; ++k) {
-      if (k != ATK_CLASS_ALS && !eig_ok) continue;
+      if (!sel::class_fits(k, f[0])) continue;
       if (o[k] < o[best] || (o[k] == o[best] && k < best)) best = k;
     }
     class_out[r] = best;

@@ -119,3 +119,15 @@ def test_gram_compensated_concentrated_energy(atk):
     err_c, err_32 = np.abs(Sc - So), np.abs(S32 - So)
     assert np.all(err_c <= 2e-6 * np.sqrt(lo) * small + 1e-13 * np.abs(So))
     assert err_c.max() * 100 <= err_32.max()
+
+
+def test_eig_mode_beyond_1024_rows(atk):
+    """An EIG mode with I_n = 1056 > 1024 (the Table II shapes have EIG modes
+    of up to 30648 rows): the subspace eigensolver on the full 1056-row Gram,
+    end to end against the oracle's full Jacobi."""
+    dims, ranks = [1056, 24, 10], [10, 8, 5]
+    x, _, _ = synth.random_tucker(dims, ranks, noise=1e-2, seed=6)
+    facs, disc, ref, rel_g, rel_o = _e2e(atk, x, dims, ranks)
+    assert abs(rel_g - rel_o) <= 1e-5
+    for U, Uo in zip(facs, ref["factors"]):
+        assert oracle.projector_distance(U, Uo) <= 1e-4

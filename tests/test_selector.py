@@ -55,8 +55,12 @@ def test_host_inference_matches_oracle():
     ref, _ = omlp.forward(p.astype(np.float64), X, IN, H, K)
     np.testing.assert_allclose(scores, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
     np.testing.assert_array_equal(cls, np.argmin(scores, axis=1))
-    # EIG needs I_n <= 1024: a mode with I_n = 2048 always gets ALS
+    # The full-Jacobi classes need I_n <= 1024: at I_n = 2048 a mode gets the
+    # subspace EIG classes or ALS; beyond 32768, ALS only.
     F[:, 0] = 11.0
+    cls, _ = selector.predict(F)
+    assert not np.any((cls == atk.CLASS_EIG_JACOBI) | (cls == atk.CLASS_EIG_JACOBI_SMALL))
+    F[:, 0] = 16.0
     cls, _ = selector.predict(F)
     assert np.all(cls == atk.CLASS_ALS)
     atk.lib().atucker_selector_clear()
