@@ -40,7 +40,7 @@ UNIT = "GB/s"
 TENSORS = [((640, 640, 640), (64, 64, 64)), ((128, 128, 128, 128), (16, 16, 16, 16))]
 WORKLOAD = "plain FP32 st-HOSVD (EIG every mode): 640^3 R64 + 128^4 R16, random Tucker + 1e-3 noise"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
-GRAM_TRAFFIC_RATIO = 1.02  # DRAM bytes / input bytes per Gram launch, from the ncu capture in profiles/
+GRAM_TRAFFIC_RATIO = 1.02  # DRAM bytes / input bytes per Gram launch (ncu capture of the mode-1 Gram)
 CPU_SAMPLE = ((640, 640, 8), (64, 64, 8))       # cpu_baseline: a 640 x 640 x 8 slab of the workload
 REF_SAMPLE = ((640, 160, 8), (64, 64, 8))       # reference arm: one such slab sample per step
 
@@ -153,16 +153,6 @@ def cpu_oracle_sample(sample, reps=1):
         oracle.sthosvd(x64, dims, ranks, solver=[0] * len(dims))
         times.append(time.perf_counter() - t0)
     return x.nbytes, times
-
-
-def relerr_identity(x_np, core_t):
-    """||X - X_hat|| / ||X|| from ||X||^2 - ||G||^2 (exact for EIG modes with orthonormal factors)."""
-    nx2 = 0.0
-    for chunk in np.array_split(x_np, 64):
-        c = chunk.astype(np.float64)
-        nx2 += float(np.dot(c, c))
-    g = core_t.detach().cpu().numpy().astype(np.float64)
-    return float(np.sqrt(max(nx2 - float(np.dot(g, g)), 0.0) / nx2))
 
 
 def run_reference(args):
@@ -291,9 +281,9 @@ def run_ours(args):
 
     # Dominant kernel: the Gram partial-tile kernel (float32 CUDA cores).
     # DRAM traffic per Gram call, scaled from one ncu capture of a smaller view
-    # (profiles/gram_fp32_mode1_640x80000.md): each launch reads its input once
-    # (measured traffic / input bytes = 1.02), and a call makes two launches
-    # (diagonal and off-diagonal tiles) when the Gram has more than 128 rows.
+    # of the mode-1 Gram: each launch reads its input once (measured traffic /
+    # input bytes = 1.02), and a call makes two launches (diagonal and
+    # off-diagonal tiles) when the Gram has more than 128 rows.
     calls, traffic_bytes = 0, 0.0
     for d, r in TENSORS:
         cur = list(d)
@@ -312,6 +302,13 @@ def run_ours(args):
               ("gram", "gram_reduce", "eig", "ttm", "als", "norms", "total")}
     launches = int(sum(t["launches"] for t in tims))
 
+    def relerr_recon(x, core, fac, dims, ranks):
+        """||X - G x_1 U1 ... x_N UN|| / ||X|| by reconstruction on the GPU:
+        valid for any core (the identity ||X||^2 - ||G||^2 needs the exact
+        projection, which a rounded TTM is not)."""
+        facs = [f.view(r, d).t() for f, d, r in zip(torch.split(fac, [d * r for d, r in zip(dims, ranks)]), dims, ranks)]
+        return reconstruct_relerr(x, core, facs, dims, ranks)
+
     def time_variant(precision=atk.FP32, mode_solver=atk.EIG):
         """ms per step (concurrent, like the headline) and relerr of the same
         workload under other plan settings (`mode_solver` for every mode: EIG,
@@ -324,13 +321,13 @@ def run_ours(args):
         for _ in range(args.warmup):
             concurrent_step(vplans)
         vms = timed(vplans, args.steps, concurrent_step)
-        rel = [relerr_identity(xn, c) for xn, (_, c, _) in zip(xnps, vplans)]
+        rel = [relerr_recon(x, c, f, list(d), list(r)) for x, (_, c, f), (d, r) in zip(xs, vplans, TENSORS)]
         classes = [vp.classes for vp, _, _ in vplans]
         for vp, _, _ in vplans:
             vp.close()
         return vms, rel, classes
 
-    rel_plain = [relerr_identity(xn, core) for xn, (_, core, _) in zip(xnps, plans)]
+    rel_plain = [relerr_recon(x, c, f, list(d), list(r)) for x, (_, c, f), (d, r) in zip(xs, plans, TENSORS)]
     # Mixed precision on the same tensors: the tensor-core Gram forms, timed
     # like the plain step, each compared by relative error with the plain output.
     mixed = None
@@ -357,6 +354,20 @@ def run_ours(args):
             sms, srel, scls = time_variant(mode_solver=atk.AUTO)
             solvers["AUTO"] = {"ms_per_step": sms, "value": in_bytes / (sms * 1e-3) / 1e9, "relerr": srel,
                                "speedup_vs_EIG": ems / sms, "classes": scls}
+
+    # The form the method's target names: learned selector and a split-product
+    # precision form together, against the plain float32 step.
+    mixed_selector = None
+    if not args.no_mixed and solvers is not None and "AUTO" in solvers:
+        best = None
+        for name, prec in (("BF16X3", atk.BF16X3), ("TF32", atk.TF32)):
+            mms, rel, cls = time_variant(precision=prec, mode_solver=atk.AUTO)
+            row = {"form": name, "ms_per_step": mms, "value": in_bytes / (mms * 1e-3) / 1e9,
+                   "speedup_vs_plain": ms / mms, "relerr": rel, "classes": cls,
+                   "max_relerr_delta_vs_plain": max(abs(a - b) for a, b in zip(rel, rel_plain))}
+            if row["max_relerr_delta_vs_plain"] <= 1e-4 and (best is None or mms < best["ms_per_step"]):
+                best = row
+        mixed_selector = best
 
     # End to end through the C ABI with host buffers (copies inside the timed
     # region): the concurrent host-buffer call, so one tensor's copies overlap
@@ -405,6 +416,7 @@ def run_ours(args):
             "phases_ms_per_step": phases,
             "mixed": mixed,
             "solvers": solvers,
+            "mixed_selector": mixed_selector,
             "e2e": {"value": in_bytes / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -412,9 +424,30 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "hbm_peak_gbs": pk.get("hbm_gbs"),
         }
-        print(json.dumps(line), flush=True)
     for p, _, _ in plans:
         p.close()
+    xs.clear()
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extra:
+        # The other workloads of the metric, each a bounded leg (few steps):
+        # precision sweep, batched form, learned selector against the paper's
+        # decision tree, the Table II stand-ins and the matricization ablation.
+        xargs = argparse.Namespace(**vars(args))
+        xargs.steps, xargs.warmup = min(args.steps, 3), 1
+        extra = {}
+        for key, fn in (("precision_sweep", run_precision), ("roofline_48x5", run_roofline_small),
+                        ("batched", run_batched), ("selector", run_selector_summary),
+                        ("table2", run_table2), ("explicit_ablation", run_explicit)):
+            t0 = time.time()
+            try:
+                extra[key] = fn(xargs)
+            except Exception as e:  # a leg that cannot run is reported, not fatal
+                extra[key] = {"error": str(e)[:200]}
+            extra[key + "_wall_s"] = time.time() - t0
+            torch.cuda.empty_cache()
+        line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -605,10 +638,9 @@ def decaying_tucker_gpu(dims, r_max: int, seed: int = 0, noise: float = 1e-3):
 
 
 def run_precision(args):
-    """The precision sweep: every Gram form on 768^3 (R 32, 64, 128) and 48^5
-    (R 8), decaying spectrum; time per st-HOSVD (CUDA events) and relative
-    error from the float64 norms (||X||^2 - ||G||^2, exact for EIG modes),
-    beside the float32 plan's."""
+    """The precision sweep: every form (Gram and TTM) on 768^3 (R 32, 64, 128)
+    and 48^5 (R 8), decaying spectrum; time per st-HOSVD (CUDA events) and
+    relative error by reconstruction, beside the float32 plan's."""
     import torch
     import paper_2010_10131_b300 as atk
     forms = (("FP32", atk.FP32), ("TF32", atk.TF32), ("BF16", atk.BF16), ("BF16X3", atk.BF16X3),
@@ -616,7 +648,6 @@ def run_precision(args):
     out = []
     for dims, R in PRECISION_SWEEP:
         x = decaying_tucker_gpu(dims, R)
-        nx2 = float((x.double() ** 2).sum().item())
         ranks = [R] * len(dims)
         row = {"dims": list(dims), "ranks": ranks, "forms": {}}
         for name, prec in forms:
@@ -633,8 +664,9 @@ def run_precision(args):
             e1.record()
             p.sync()
             ms = e0.elapsed_time(e1) / max(args.steps, 1)
-            g2 = float((core.double() ** 2).sum().item())
-            rel = math.sqrt(max(nx2 - g2, 0.0) / nx2)
+            facs = [f.view(r, d).t() for f, d, r in zip(torch.split(fac, [d * r for d, r in zip(dims, ranks)]),
+                                                        dims, ranks)]
+            rel = reconstruct_relerr(x, core, facs, list(dims), ranks)
             row["forms"][name] = {"ms": ms, "gbs": x.numel() * 4 / (ms * 1e-3) / 1e9, "relerr": rel}
             p.close()
         base = row["forms"]["FP32"]
@@ -644,6 +676,60 @@ def run_precision(args):
         out.append(row)
         del x
         torch.cuda.empty_cache()
+    return out
+
+
+def run_roofline_small(args):
+    """HBM roofline of the memory-bound contractions: the mode-1 Gram and the
+    R = 8 TTM of the 48^5 tensor (view 1 x 48 x 48^4), float32, through the C
+    ABI, device time by CUDA events.  Algorithmic bytes: the input read once
+    (Gram); input read once plus the output written (TTM)."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    lo, n, hi, R = 1, 48, 48 ** 4, 8
+    g = torch.Generator(device="cuda").manual_seed(0)
+    y = torch.randn(lo * n * hi, device="cuda", generator=g)
+    U = torch.linalg.qr(torch.randn(n, R, device="cuda", generator=g))[0]
+    hbm = peaks().get("hbm_gbs") or 6400.0
+    out = {"view": [lo, n, hi], "hbm_peak_gbs": hbm}
+    for name, fn, nbytes in (("gram", lambda: atk.gram(y, lo, n, hi), 4.0 * y.numel()),
+                             ("ttm", lambda: atk.ttm(y, lo, n, hi, U), 4.0 * y.numel() * (1 + R / n))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "gbs": gbs, "frac_of_measured_hbm": gbs / hbm}
+    return out
+
+
+def run_selector_summary(args, e2e_shapes: int = 24):
+    """The learned selector as installed (weights trained by the library's
+    kernels on the committed timing sets) against the paper's decision tree
+    trained on the same timings: held-out regret and host inference time, then
+    end to end on held-out shapes, every mode AUTO against every mode EIG."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    from paper_2010_10131_b300 import selector
+    out = selector.compare_tree_mlp()
+    shapes, _ = selector.load_timings(selector.TIMINGS)
+    held = shapes[192:192 + e2e_shapes]
+    tot = {"AUTO": 0.0, "EIG": 0.0}
+    for i, (dims, ranks) in enumerate(held):
+        x = selector.random_tucker_gpu(dims, ranks, 900001 + i)
+        for name, sv in (("AUTO", atk.AUTO), ("EIG", atk.EIG)):
+            ms, _, _, _, _ = time_plan(x, dims, ranks, 2, 1, solver=[sv] * len(dims))
+            tot[name] += ms
+        del x
+        torch.cuda.empty_cache()
+    out["end_to_end"] = {"shapes": len(held), "auto_ms": tot["AUTO"], "eig_ms": tot["EIG"],
+                         "gain_vs_fixed_EIG": tot["EIG"] / tot["AUTO"]}
     return out
 
 
@@ -821,6 +907,8 @@ def main():
     ap.add_argument("--case", default=None, help="profile one op: gram:LO,N,HI, ttm:LO,N,HI,R, eig:N,R[,METHOD] or batched[:COUNT]")
     ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 TF32, 2 BF16, 3 3xBF16, 4 FP8-e4m3 (--case)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (precision sweep, batched, selector, Table II, ablation)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

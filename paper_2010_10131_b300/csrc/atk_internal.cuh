@@ -190,6 +190,14 @@ int tc_gram(const float* y, const View& v, int precision, double* S, float* scra
 // max_c |Y(c, i)| for every mode-n index i (bits of the non-negative float,
 // combined by atomicMax); rmax (n floats) must be zero on entry.
 int tc_rowmax(const float* y, const View& v, float* rmax, cudaStream_t st);
+// Fused ALS sweep (als_fused.cu): A = Y (Y^T Lt) (n x R float64) in one pass
+// over Y for I_n <= 256 and R <= 32; Rk (nullable) receives Y^T Lt in the
+// (lo, R, hi) layout.
+bool als_fused_ok(const View& v, int64_t R);
+size_t als_fused_scratch_bytes(const View& v, int64_t R);
+int als_fused(const float* y, const View& v, const float* Lt, int64_t R, double* A, float* Rk, float* scratch,
+              size_t scratch_bytes, cudaStream_t st);
+
 // Explicit matricization (matricize.cu): dst slab b (B x A) = transpose of
 // src slab b (A x B), both column-major, b < count.
 int permute_slabs(const float* src, int64_t A, int64_t B, int64_t count, float* dst, cudaStream_t st);

@@ -104,8 +104,7 @@ struct AlsBufs {
 };
 
 static size_t als_scratch_need(const View& v, int64_t R) {
-  View vp{v.lo, R, v.hi};
-  size_t s = std::max(cross_scratch_bytes(v, R), cross_scratch_bytes(vp, R));
+  size_t s = std::max(cross_scratch_bytes(v, R), als_fused_scratch_bytes(v, R));
   s = std::max(s, smallla_scratch_bytes(std::max(v.n, R), R));
   return s;
 }
@@ -113,22 +112,34 @@ static size_t als_scratch_need(const View& v, int64_t R) {
 // One ALS solve (Alg. 3 with `sweeps` iterations), QR of L (CholeskyQR2 in
 // float64, the unique QR with diag(R^) > 0), and the core update
 // Y' = R_{K-1} x_n R^ written to `out` (a (lo, R, hi) tensor).
+// A sweep needs A = Y R_k with R_k = Y^T L~, and B = R_k^T R_k, which equals
+// L~^T A: only A is taken from the tensor.  Small modes (I_n <= 256, R <= 32)
+// form A in one fused pass over Y that keeps R_k on chip (als_fused.cu) and
+// write R_k only on the last sweep; the others run the TTM kernel for R_k and
+// the cross kernel for A.
 static int als_mode_run(const float* y, const View& v, int64_t R, const double* L0, int sweeps, float* U_out,
                         float* out, AlsBufs& b, cudaStream_t st) {
   const int64_t n = v.n;
   View vp{v.lo, R, v.hi};
   double* ss = (double*)b.scratch;
+  const bool fused = als_fused_ok(v, R);
   ATK_CUDA(cudaMemcpyAsync(b.L, L0, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
   for (int k = 0; k < sweeps; ++k) {
-    // R_k = (Y^T L_k)(L_k^T L_k)^{-1} = Y^T L~ with L~ = L_k (L_k^T L_k)^{-1}.
+    const bool last = k == sweeps - 1;
+    // L~ = L_k (L_k^T L_k)^{-1}.
     ATK_TRY(gemm_tn_f64(b.L, b.L, n, R, b.G, st));
     ATK_CUDA(cudaMemcpyAsync(b.Lt, b.L, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
     ATK_TRY(solve_spd_right_f64(b.Lt, n, R, b.G, ss, b.dev_status, st));
     ATK_TRY(f64_to_f32(b.Lt, b.Lt32, n * R, st));
-    ATK_TRY(ttm_f32(y, v, b.Lt32, R, b.P, st));  // P = R_k as a (lo, R, hi) tensor
-    // L_{k+1} = (Y R_k)(R_k^T R_k)^{-1}.
-    ATK_TRY(cross_f32(y, v, b.P, R, b.A, (float*)b.scratch, b.scratch_bytes, st));
-    ATK_TRY(cross_f32(b.P, vp, b.P, R, b.B, (float*)b.scratch, b.scratch_bytes, st));
+    // A = Y R_k with R_k = Y^T L~ (R_k kept, as a (lo, R, hi) tensor, on the last sweep).
+    if (fused) {
+      ATK_TRY(als_fused(y, v, b.Lt32, R, b.A, last ? b.P : nullptr, (float*)b.scratch, b.scratch_bytes, st));
+    } else {
+      ATK_TRY(ttm_f32(y, v, b.Lt32, R, b.P, st));
+      ATK_TRY(cross_f32(y, v, b.P, R, b.A, (float*)b.scratch, b.scratch_bytes, st));
+    }
+    // B = R_k^T R_k = L~^T A; L_{k+1} = A B^{-1}.
+    ATK_TRY(gemm_tn_f64(b.Lt, b.A, n, R, b.B, st));
     ATK_TRY(solve_spd_right_f64(b.A, n, R, b.B, ss, b.dev_status, st));
     ATK_CUDA(cudaMemcpyAsync(b.L, b.A, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, st));
   }

@@ -212,68 +212,103 @@ int gemm_tn_f64(const double* A, const double* B, int64_t n, int64_t R, double* 
   return dgemm<true, false>(A, n, B, n, R, n, R, G, R, st);
 }
 
-// One CTA: Cholesky G = C C^T (C lower), Cinv = C^{-1} (lower) and, if
-// requested, Ginv = Cinv^T Cinv.  Everything lives in global memory (L2);
-// R <= 128.  A non-positive pivot sets DEV_CHOL and leaves identity factors,
-// so later kernels stay finite.
-__global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ G, int R, double* __restrict__ C,
-                                                       double* __restrict__ Cinv, double* __restrict__ Ginv,
-                                                       int* __restrict__ status) {
+// One CTA: Cholesky G = C C^T (C lower) and Cinv = C^{-1} (lower), R <= 128,
+// float64 (Golub & Van Loan, Matrix Computations, Alg. 4.2.2 for the
+// factor, row-oriented forward substitution for the inverse).  Both live in
+// one shared-memory R x (R + 1) array: C on and below the diagonal, the
+// strictly lower part of Cinv transposed into the upper part, the diagonals
+// in two vectors.  The factor is right-looking, three barriers per column
+// (the pivot's root and reciprocal by one thread, the column scaled, the
+// rank-1 update of the trailing triangle); row i of the inverse, X_ik = -(sum_{k<=t<i} C_it
+// X_tk) / C_ii, takes one barrier per row, its sums split over lane groups of
+// four and combined by shuffles.  A non-positive pivot sets DEV_CHOL and
+// leaves identity factors, so later kernels stay finite.
+constexpr int CI_THREADS = 512;
+size_t chol_inv_smem(int R) { return sizeof(double) * ((size_t)R * (R + 1) + 2 * (size_t)R) + 16; }
+
+__global__ void __launch_bounds__(CI_THREADS) chol_inv_kernel(const double* __restrict__ G, int R,
+                                                              double* __restrict__ C, double* __restrict__ Cinv,
+                                                              int* __restrict__ status) {
+  extern __shared__ double cm[];
+  const int ld = R + 1;
+  double* M = cm;                 // R x ld, row-major: M[i * ld + j]
+  double* dC = cm + (size_t)R * ld;  // diagonal of C
+  double* dX = dC + R;               // diagonal of Cinv
   __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) C[idx] = G[idx];
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int idx = tid; idx < R * R; idx += CI_THREADS) {
+    const int i = idx % R, j = idx / R;
+    if (i >= j) M[i * ld + j] = G[i + (int64_t)R * j];
+  }
   __syncthreads();
-  // Right-looking Cholesky on the lower triangle (column-major, C[i + R*j]).
+  __shared__ double pinv;
   for (int j = 0; j < R; ++j) {
-    if (threadIdx.x == 0) {
-      double d = C[j + R * j];
-      if (!(d > 0.0)) { bad = 1; d = 1.0; }
-      C[j + R * j] = sqrt(d);
+    // One thread takes the square root and reciprocal (float64 division and
+    // square root are long instruction sequences on the float64 pipe, which
+    // B300 issues at about two per clock per SM: every thread recomputing
+    // them cost more than the whole factorisation).
+    if (tid == 0) {
+      double piv = M[j * ld + j];
+      if (!(piv > 0.0)) {
+        bad = 1;
+        piv = 1.0;
+      }
+      const double d = sqrt(piv);
+      dC[j] = d;
+      dX[j] = 1.0 / d;
+      pinv = dX[j];
     }
     __syncthreads();
-    double cjj = C[j + R * j];
-    for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) C[i + R * j] /= cjj;
+    const double inv = pinv;
+    for (int i = j + 1 + tid; i < R; i += CI_THREADS) M[i * ld + j] *= inv;
     __syncthreads();
-    int rem = R - j - 1;
-    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-      int i = j + 1 + idx % rem, k = j + 1 + idx / rem;
-      if (i >= k) C[i + R * k] -= C[i + R * j] * C[k + R * j];
+    const int rem = R - j - 1;
+    for (int idx = tid; idx < rem * rem; idx += CI_THREADS) {
+      const int i = j + 1 + idx / rem, k = j + 1 + idx % rem;
+      if (k <= i) M[i * ld + k] -= M[i * ld + j] * M[k * ld + j];
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-    int i = idx % R, k = idx / R;
-    if (i < k) C[idx] = 0.0;
-  }
-  __syncthreads();
   if (bad) {
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-      double e = (idx % R == idx / R) ? 1.0 : 0.0;
+    for (int idx = tid; idx < R * R; idx += CI_THREADS) {
+      const double e = (idx % R == idx / R) ? 1.0 : 0.0;
       C[idx] = e;
       Cinv[idx] = e;
-      if (Ginv) Ginv[idx] = e;
     }
-    if (threadIdx.x == 0) atomicOr(status, DEV_CHOL);
+    if (tid == 0) atomicOr(status, DEV_CHOL);
     return;
   }
-  // Cinv: column k solves C x = e_k by forward substitution (one thread per column).
-  for (int k = threadIdx.x; k < R; k += blockDim.x) {
-    for (int i = 0; i < R; ++i) {
-      if (i < k) { Cinv[i + R * k] = 0.0; continue; }
-      double s = (i == k) ? 1.0 : 0.0;
-      for (int t = k; t < i; ++t) s -= C[i + R * t] * Cinv[t + R * k];
-      Cinv[i + R * k] = s / C[i + R * i];
+  // Inverse, row by row: lane group g (4 lanes) takes column k = g.
+  const int grp = tid / 4, sub = tid % 4;
+  for (int i = 0; i < R; ++i) {
+    const int k = grp;
+    double acc = 0.0;
+    if (k < i) {
+      if (sub == 0) acc = M[i * ld + k] * dX[k];  // t = k term: C_ik X_kk
+      for (int t = k + 1 + sub; t < i; t += 4) acc += M[i * ld + t] * M[k * ld + t];  // X_tk sits at M[k][t]
     }
+    // every lane takes part in the shuffles (the groups of a warp diverge above)
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (sub == 0 && k < i) M[k * ld + i] = -acc * dX[i];
+    __syncthreads();
   }
-  __syncthreads();
-  if (Ginv) {
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-      int i = idx % R, k = idx / R;
-      double s = 0.0;
-      for (int t = max(i, k); t < R; ++t) s += Cinv[t + R * i] * Cinv[t + R * k];
-      Ginv[idx] = s;
-    }
+  for (int idx = tid; idx < R * R; idx += CI_THREADS) {
+    const int i = idx % R, j = idx / R;  // column-major outputs
+    C[idx] = i > j ? M[i * ld + j] : (i == j ? dC[i] : 0.0);
+    Cinv[idx] = i > j ? M[j * ld + i] : (i == j ? dX[i] : 0.0);
   }
+}
+
+static int launch_chol_inv(const double* G, int R, double* C, double* Cinv, int* status, cudaStream_t st) {
+  if (R < 1 || R > 128) { set_error("chol_inv: need 1 <= R <= 128"); return ATK_EUNSUPPORTED; }
+  static const bool attr = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)chol_inv_smem(128)) == cudaSuccess;
+  if (!attr) { set_error("chol_inv: cannot set the kernel's shared-memory size"); return ATK_ECUDA; }
+  chol_inv_kernel<<<1, CI_THREADS, chol_inv_smem(R), st>>>(G, R, C, Cinv, status);
+  ATK_LAUNCHED();
+  return ATK_OK;
 }
 
 int gemm_f64(const double* A, const double* B, int64_t m, int64_t k, int64_t p, double* C, cudaStream_t st) {
@@ -307,14 +342,15 @@ SmallBufs carve(double* scratch, int64_t n, int64_t R) {
 }
 }  // namespace
 
+// X <- X G^{-1} = (X C^{-T}) C^{-1} with G = C C^T: two products with the
+// triangular inverse, no explicit G^{-1}.
 int solve_spd_right_f64(double* X, int64_t m, int64_t R, const double* G, double* scratch, int* dev_status,
                         cudaStream_t st) {
   SmallBufs b = carve(scratch, m, R);
   if (!b.panel) { set_error("solve_spd: scratch too small"); return ATK_EINVAL; }
-  chol_inv_kernel<<<1, 256, 0, st>>>(G, (int)R, b.M1, b.M2, b.M3, dev_status);
-  ATK_LAUNCHED();
-  ATK_TRY((dgemm<false, false>(X, m, b.M3, R, m, R, R, b.panel, m, st)));
-  ATK_CUDA(cudaMemcpyAsync(X, b.panel, sizeof(double) * m * R, cudaMemcpyDeviceToDevice, st));
+  ATK_TRY(launch_chol_inv(G, (int)R, b.M1, b.M2, dev_status, st));
+  ATK_TRY((dgemm<false, true>(X, m, b.M2, R, m, R, R, b.panel, m, st)));
+  ATK_TRY((dgemm<false, false>(b.panel, m, b.M2, R, m, R, R, X, m, st)));
   return ATK_OK;
 }
 
@@ -341,13 +377,11 @@ int cholqr2_f64(double* L, int64_t n, int64_t R, double* Rhat, double* scratch, 
   if (!b.panel) { set_error("cholqr2: scratch too small"); return ATK_EINVAL; }
   // Pass 1: L^T L = C1 C1^T, Q1 = L C1^{-T}.
   ATK_TRY(gemm_tn_f64(L, L, n, R, b.M1, st));
-  chol_inv_kernel<<<1, 256, 0, st>>>(b.M1, (int)R, b.M2, b.M3, nullptr, dev_status);
-  ATK_LAUNCHED();
+  ATK_TRY(launch_chol_inv(b.M1, (int)R, b.M2, b.M3, dev_status, st));
   ATK_TRY((dgemm<false, true>(L, n, b.M3, R, n, R, R, b.panel, n, st)));
   // Pass 2 on Q1: Q1^T Q1 = C2 C2^T, Q = Q1 C2^{-T}.
   ATK_TRY(gemm_tn_f64(b.panel, b.panel, n, R, b.M1, st));
-  chol_inv_kernel<<<1, 256, 0, st>>>(b.M1, (int)R, b.M4, b.M3, nullptr, dev_status);
-  ATK_LAUNCHED();
+  ATK_TRY(launch_chol_inv(b.M1, (int)R, b.M4, b.M3, dev_status, st));
   ATK_TRY((dgemm<false, true>(b.panel, n, b.M3, R, n, R, R, L, n, st)));
   rhat_kernel<<<(unsigned)ceil_div(R * R, 256), 256, 0, st>>>(b.M2, b.M4, R, Rhat);
   ATK_LAUNCHED();
