@@ -905,7 +905,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, help="profile one op: gram:LO,N,HI, ttm:LO,N,HI,R, eig:N,R[,METHOD] or batched[:COUNT]")
-    ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 TF32, 2 BF16, 3 3xBF16, 4 FP8-e4m3 (--case)")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="0 FP32, 1 TF32, 2 BF16, 3 3xBF16, 4 FP8-e4m3, 5 FP32 compensated (--case)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (precision sweep, batched, selector, Table II, ablation)")

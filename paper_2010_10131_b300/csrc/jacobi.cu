@@ -480,7 +480,8 @@ int run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
 //     CholeskyQR passes suffice) and further Rayleigh-Ritz projections until
 //     the predicted error after the float64 refinement,
 //       (theta_m / theta_K) * max_{j<K} ||S q_j - theta_j q_j|| / (theta_K - theta_m),
-//     drops below RR_TARGET.  That is a Davis-Kahan bound on the angle
+//     drops below RR_TARGET, or stops falling while below RR_FLOOR_OK (the
+//     float32 floor of the residuals).  That is a Davis-Kahan bound on the angle
 //     between q_K and the leading space, times the contraction of the
 //     refinement's subspace step.  K is R, or fewer: Ritz values below
 //     RR_RESOLVE eps_32 theta_1 are not resolved by float32 products at all,
@@ -496,6 +497,12 @@ constexpr int RR_MAX_POWER = 160;
 constexpr int RR_POWER_CHUNK = 8;
 constexpr double RR_TARGET = 1e-6;
 constexpr double RR_MAX_RATE = 0.92;
+// Stall test: a projection after power steps that leaves the predicted error
+// above RR_STALL times the previous one has met the float32 floor; below
+// RR_FLOOR_OK that is accepted, above it three such projections in a row
+// mean no convergence.
+constexpr double RR_STALL = 0.5;
+constexpr double RR_FLOOR_OK = 1e-4;
 constexpr float RR_RESOLVE = 32.f * 1.1920929e-7f;
 
 // Block width m = R + p.  The default guard p = clamp(R / 2, 8, 16) suits a
@@ -719,6 +726,8 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
   const GraphKey kpow{{scratch, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (const void*)4},
                       {n, R, m, (int64_t)scratch_bytes}};
   int power = 0;
+  double prev_pred = 0.0;
+  int stalls = 0;
   for (;;) {
     // Rayleigh-Ritz: Z = S Q, B = Q^T Z = W diag(theta) W^T; Ritz vectors
     // Y = Q W (descending theta) and S Q W = Z W; residuals and summary.
@@ -747,7 +756,14 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
     const double rate = thm / thK;
     if (rate > RR_MAX_RATE) return ATK_ENOCONV;  // the cut sits in a cluster wider than the guard
     const double predicted = rate * res / (thK - thm);
-    if (predicted <= RR_TARGET) {
+    // Converged, or at the float32 floor: the residuals of float32 products
+    // stop falling (a deflated level reaches eps_32 ||S|| long before 1e-6 of
+    // its gap).  Below RR_FLOOR_OK the float64 refinement that follows removes
+    // what is left; a stall above it is no convergence.
+    const bool stalled = prev_pred > 0.0 && predicted > RR_STALL * prev_pred;
+    stalls = stalled && predicted > RR_FLOOR_OK ? stalls + 1 : 0;
+    if (stalls >= 3) return ATK_ENOCONV;  // three projections in a row without progress
+    if (predicted <= RR_TARGET || (stalled && predicted <= RR_FLOOR_OK)) {
       f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Y, Qblk, n * (int64_t)m);
       ATK_LAUNCHED();
       return ATK_OK;
@@ -760,6 +776,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
     steps = std::max(1, std::min(steps, RR_POWER_CHUNK));
     if (power + steps > RR_MAX_POWER) return ATK_ENOCONV;
     power += steps;
+    prev_pred = predicted;
     // First step from the Ritz vectors: S (Q W) = Z W is in T; its columns are
     // nearly orthogonal, so two plain CholeskyQR passes orthonormalise it.
     ATK_TRY(run_graph(knext, st, [&](cudaStream_t s2) -> int {
