@@ -168,8 +168,20 @@ typedef struct atucker_plan_s* atucker_plan_t;
  *                    in (the paper's loop runs n = 1..N); NULL = 0,1,..,N-1
  *   solver_per_mode  host array of N atucker_solver values indexed by mode;
  *                    NULL = EIG for every mode.  ATK_AUTO lets the learned
- *                    selector (atucker_selector_set) pick the mode's class;
- *                    with no selector loaded AUTO means ATK_CLASS_EIG.
+ *                    selector (atucker_selector_set or _set_tree) pick the
+ *                    mode's class.  Where it cannot decide, the plan's first
+ *                    atucker_sthosvd times the candidates on that input (an
+ *                    exhaustive search, Sec. IV): with no selector loaded,
+ *                    every class that can run the mode; with the network,
+ *                    its two best classes when their predicted log2 times
+ *                    differ by less than 0.15 (about 11 %).  That call runs
+ *                    each candidate twice (warm-up, then timed with CUDA
+ *                    events), keeps each mode's fastest, and caches the choice
+ *                    for the process, keyed by shape, ranks, order and the
+ *                    plan's options; later plans of that key skip the search.
+ *                    Until then atucker_plan_classes reports the starting
+ *                    guess (the prediction, or ATK_CLASS_EIG).  The workspace
+ *                    of such a plan covers every candidate.
  *   precision        atucker_precision
  *   als_sweeps       ALS iterations (num_iters of Eq. 5; the paper's default is
  *                    5); <= 0 selects 5

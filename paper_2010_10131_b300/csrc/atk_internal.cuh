@@ -160,6 +160,8 @@ struct Arena {
 int gram_tile(int64_t n);
 // True once atucker_selector_set has loaded a selector (selector.cu).
 bool selector_loaded();
+// Whether class k can run a mode with log2 I_n = lg (selector.cu).
+bool selector_class_fits(int k, double lg);
 // `bm` forces the Gram row tile (32, 64 or 128); 0 picks it from n.
 size_t gram_scratch_bytes(const View& v, int bm = 0);
 // `mid` (nullable) is recorded between the partial-tile kernel and the reduction.

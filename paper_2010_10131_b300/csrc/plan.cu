@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -87,6 +89,10 @@ static void als_initial_guess(uint64_t seed, int mode, int64_t I, int64_t R, dou
 
 __global__ void sub_kernel(const double* a, const double* b, double* out) { *out = *a - *b; }
 
+// Two predicted classes closer than this (log2 of the time ratio, about 11 %)
+// are settled by timing them at the plan's first run.
+constexpr float SELECTOR_MARGIN = 0.15f;
+
 // Below this rank the float32 TTM reads Y at HBM speed, and the tensor-core
 // TTM of the precision forms is no faster (measured at I_n = 128, R = 16).
 constexpr int64_t TC_TTM_MIN_R = 16;
@@ -167,6 +173,12 @@ struct atucker_plan_s {
   int eig_arith = ATK_EIG_ROT_FP32, eig_method = ATK_EIG_AUTO, sync = 0, max_sweeps = 40, gram_refine = 1;
   long long wait_polls = 0;  // ATK_OPT_WAIT_LIMIT (0: default)
   int explicit_unfold = 0;   // ATK_OPT_EXPLICIT_UNFOLD
+  // Exhaustive timed search (AUTO modes without a confident prediction):
+  // candidate classes per mode, timed at the first run.
+  int ncand[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int cand[8][ATK_NUM_CLASSES];
+  bool tune_pending = false;
+  bool both[8] = {false, false, false, false, false, false, false, false};  // workspace for EIG and ALS
   float* xunf = nullptr;     // unfolding buffer and TTM result of the explicit form (one allocation)
   float* xttm = nullptr;
   // device workspace
@@ -252,9 +264,11 @@ static int plan_alloc(atucker_plan_s* p) {
     u_elems = std::max(u_elems, (size_t)(v.n * R));
     maxn = std::max(maxn, v.n);
     maxr = std::max(maxr, R);
-    if (p->solver[n] == ATK_EIG) {
+    if (p->solver[n] == ATK_EIG || p->both[n]) {
       s_elems = std::max(s_elems, (size_t)(v.n * v.n));
       scratch = std::max(scratch, gram_scratch_bytes(v, p->gbm[n]));
+      if (p->ncand[n] > 0)  // a timed search may try the smaller Gram tile
+        scratch = std::max(scratch, gram_scratch_bytes(v, std::max(32, gram_tile(v.n) / 2)));
       if (p->precision != ATK_FP32 && p->precision != ATK_FP32C) {
         scratch = std::max(scratch, tc_gram_scratch_bytes(v, p->precision));
         scratch = std::max(scratch, tc_ttm_scratch_bytes(v, R, p->precision));
@@ -263,7 +277,8 @@ static int plan_alloc(atucker_plan_s* p) {
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP64));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP32));
       scratch = std::max(scratch, smallla_scratch_bytes(v.n, R));
-    } else {
+    }
+    if (p->solver[n] == ATK_ALS || p->both[n]) {
       any_als = true;
       pbuf = std::max(pbuf, out_elems);
       scratch = std::max(scratch, als_scratch_need(v, R));
@@ -315,7 +330,8 @@ static int plan_alloc(atucker_plan_s* p) {
   if (l0_elems) {
     std::vector<double> h(l0_elems);
     for (int n = 0; n < p->order; ++n)
-      if (p->solver[n] == ATK_ALS) als_initial_guess(p->seed, n, p->dims[n], p->ranks[n], h.data() + p->l0off[n]);
+      if (p->solver[n] == ATK_ALS || p->both[n])
+        als_initial_guess(p->seed, n, p->dims[n], p->ranks[n], h.data() + p->l0off[n]);
     ATK_CUDA(cudaMemcpyAsync(p->L0, h.data(), l0_elems * 8, cudaMemcpyHostToDevice, p->st));
     ATK_CUDA(cudaStreamSynchronize(p->st));
   }
@@ -323,6 +339,10 @@ static int plan_alloc(atucker_plan_s* p) {
 }
 
 extern "C" {
+
+static int plan_create_impl(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
+                            const int* mode_order, const int* class_per_mode, int precision, int als_sweeps,
+                            uint64_t seed, void* stream, const int* ncand, const int (*cand)[ATK_NUM_CLASSES]);
 
 int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
                         const int* mode_order, const int* solver_per_mode, int precision, int als_sweeps,
@@ -337,22 +357,48 @@ int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, co
     cls[k] = s == ATK_ALS ? ATK_CLASS_ALS : ATK_CLASS_EIG;
     any_auto = any_auto || s == ATK_AUTO;
   }
+  int ncand[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int cand[8][ATK_NUM_CLASSES];
   if (any_auto) {
     double feat[8 * ATK_SELECTOR_FEATURES];
     int pick[8];
+    float scores[8 * ATK_NUM_CLASSES];
     ATK_TRY(atucker_mode_features(order, dims, ranks, mode_order, feat));
-    if (selector_loaded() && atucker_selector_predict(feat, order, pick, nullptr) == ATK_OK) {
-      for (int k = 0; k < order; ++k)
-        if (solver_per_mode[k] == ATK_AUTO) cls[k] = pick[k];
+    const bool have = selector_loaded() && atucker_selector_predict(feat, order, pick, scores) == ATK_OK;
+    for (int k = 0; k < order; ++k) {
+      if (solver_per_mode[k] != ATK_AUTO) continue;
+      const double lg = feat[k * ATK_SELECTOR_FEATURES];  // log2 I_n
+      if (have) {
+        // The prediction, and the runner-up when the two are too close to call.
+        cls[k] = pick[k];
+        int second = -1;
+        for (int c = 0; c < ATK_NUM_CLASSES; ++c)
+          if (c != pick[k] && selector_class_fits(c, lg) &&
+              (second < 0 || scores[k * ATK_NUM_CLASSES + c] < scores[k * ATK_NUM_CLASSES + second]))
+            second = c;
+        if (second >= 0 &&
+            scores[k * ATK_NUM_CLASSES + second] - scores[k * ATK_NUM_CLASSES + pick[k]] < SELECTOR_MARGIN) {
+          cand[k][0] = pick[k];
+          cand[k][1] = second;
+          ncand[k] = 2;
+        }
+      } else {
+        // No selector: every class that can run the mode is timed.
+        for (int c = 0; c < ATK_NUM_CLASSES; ++c)
+          if (selector_class_fits(c, lg)) cand[k][ncand[k]++] = c;
+        cls[k] = selector_class_fits(ATK_CLASS_EIG, lg) ? ATK_CLASS_EIG : ATK_CLASS_ALS;
+      }
     }
   }
-  return atucker_plan_create_classes(plan, order, dims, ranks, mode_order, cls, precision, als_sweeps, seed,
-                                     stream);
+  return plan_create_impl(plan, order, dims, ranks, mode_order, cls, precision, als_sweeps, seed, stream, ncand,
+                          cand);
 }
 
-int atucker_plan_create_classes(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
-                                const int* mode_order, const int* class_per_mode, int precision, int als_sweeps,
-                                uint64_t seed, void* stream) {
+// Plan creation; ncand / cand (nullable): candidate classes of the modes that
+// the first run settles by timing them (exhaustive search).
+static int plan_create_impl(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
+                            const int* mode_order, const int* class_per_mode, int precision, int als_sweeps,
+                            uint64_t seed, void* stream, const int* ncand, const int (*cand)[ATK_NUM_CLASSES]) {
   if (!plan) { set_error("plan is null"); return ATK_EINVAL; }
   *plan = nullptr;
   if (!class_per_mode) { set_error("class_per_mode is null"); return ATK_EINVAL; }
@@ -400,10 +446,29 @@ int atucker_plan_create_classes(atucker_plan_t* plan, int order, const int64_t* 
   p->als_sweeps = als_sweeps > 0 ? als_sweeps : 5;
   p->seed = seed;
   p->st = (cudaStream_t)stream;
+  if (ncand && cand) {
+    for (int k = 0; k < order; ++k) {
+      p->ncand[k] = ncand[k];
+      bool eig = false, als = false;
+      for (int j = 0; j < ncand[k]; ++j) {
+        p->cand[k][j] = cand[k][j];
+        (cand[k][j] == ATK_CLASS_ALS ? als : eig) = true;
+      }
+      p->both[k] = eig && als;
+      if (ncand[k] > 0) p->tune_pending = true;
+    }
+  }
   int s = plan_alloc(p);
   if (s != ATK_OK) { atucker_plan_destroy(p); return s; }
   *plan = p;
   return ATK_OK;
+}
+
+int atucker_plan_create_classes(atucker_plan_t* plan, int order, const int64_t* dims, const int64_t* ranks,
+                                const int* mode_order, const int* class_per_mode, int precision, int als_sweeps,
+                                uint64_t seed, void* stream) {
+  return plan_create_impl(plan, order, dims, ranks, mode_order, class_per_mode, precision, als_sweeps, seed, stream,
+                          nullptr, nullptr);
 }
 
 int atucker_plan_classes(atucker_plan_t p, int* class_out) {
@@ -606,10 +671,99 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
   return ATK_OK;
 }
 
+// ------------------------------------------- exhaustive timed search (AUTO)
+// The classes chosen by timing, per shape and settings, for the process.
+static std::mutex g_tuned_mu;
+static std::map<std::vector<int64_t>, std::vector<int>> g_tuned;
+
+static std::vector<int64_t> tune_key(const atucker_plan_s* p) {
+  std::vector<int64_t> k{p->order, p->precision, p->eig_arith, p->eig_method, p->als_sweeps, p->gram_refine};
+  for (int i = 0; i < p->order; ++i) {
+    k.push_back(p->dims[i]);
+    k.push_back(p->ranks[i]);
+    k.push_back(p->mode_order[i]);
+    k.push_back(p->ncand[i]);
+  }
+  return k;
+}
+
+static void set_mode_class(atucker_plan_s* p, int k, int c) {
+  p->cls[k] = c;
+  p->solver[k] = c == ATK_CLASS_ALS ? ATK_ALS : ATK_EIG;
+  const bool jac = c == ATK_CLASS_EIG_JACOBI || c == ATK_CLASS_EIG_JACOBI_SMALL;
+  const bool small = c == ATK_CLASS_EIG_SMALL || c == ATK_CLASS_EIG_JACOBI_SMALL;
+  p->eigm[k] = jac ? ATK_EIG_FULL_JACOBI : -1;
+  p->gbm[k] = small ? std::max(32, gram_tile(p->dims[k]) / 2) : 0;
+}
+
+// Time every candidate class of the AUTO modes on this input (round t runs
+// every such mode with its t-th candidate; one warm-up and one timed run, the
+// per-mode CUDA-event times), keep each mode's fastest, and cache the choice.
+static int tune_plan(atucker_plan_s* p, const float* x, float* core_out, float* factors_out) {
+  const std::vector<int64_t> key = tune_key(p);
+  {
+    std::lock_guard<std::mutex> g(g_tuned_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      for (int k = 0; k < p->order; ++k)
+        if (p->ncand[k] > 0) set_mode_class(p, k, it->second[k]);
+      p->tune_pending = false;
+      return ATK_OK;
+    }
+  }
+  int rounds = 0;
+  for (int k = 0; k < p->order; ++k) rounds = std::max(rounds, p->ncand[k]);
+  double best_ms[8];
+  int best[8];
+  for (int k = 0; k < p->order; ++k) {
+    best_ms[k] = 1e300;
+    best[k] = p->cls[k];
+  }
+  const int timing = p->timing, sync = p->sync;
+  p->timing = 1;
+  p->sync = 0;
+  for (int t = 0; t < rounds; ++t) {
+    for (int k = 0; k < p->order; ++k)
+      if (p->ncand[k] > 0) set_mode_class(p, k, p->cand[k][std::min(t, p->ncand[k] - 1)]);
+    double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      p->recs.clear();
+      p->mrecs.clear();
+      p->evnext = 0;
+      ok = sthosvd_run(p, x, core_out, factors_out, nullptr) == ATK_OK && atucker_plan_sync(p) == ATK_OK;
+      if (ok && rep == 1) ok = atucker_plan_mode_timings(p, ms, p->order) == ATK_OK;
+    }
+    if (!ok) continue;  // a class that fails on this input is not chosen
+    for (int k = 0; k < p->order; ++k)
+      if (p->ncand[k] > t && ms[k] < best_ms[k]) {
+        best_ms[k] = ms[k];
+        best[k] = p->cand[k][t];
+      }
+  }
+  for (int k = 0; k < p->order; ++k) set_mode_class(p, k, best[k]);
+  p->timing = timing;
+  p->sync = sync;
+  p->recs.clear();
+  p->mrecs.clear();
+  p->evnext = 0;
+  p->tune_pending = false;
+  std::lock_guard<std::mutex> g(g_tuned_mu);
+  g_tuned[key] = std::vector<int>(best, best + p->order);
+  return ATK_OK;
+}
+
 int atucker_sthosvd(atucker_plan_t p, const float* x, float* core_out, float* factors_out, double* discarded_out) {
   if (!p || !x || !core_out || !factors_out) { set_error("null argument"); return ATK_EINVAL; }
   const long long l0 = launch_count();
   set_wait_limit(p->wait_polls);
+  if (p->tune_pending) {
+    const int s = tune_plan(p, x, core_out, factors_out);
+    if (s != ATK_OK) {
+      set_wait_limit(0);
+      return s;
+    }
+  }
   const int s = sthosvd_run(p, x, core_out, factors_out, discarded_out);
   set_wait_limit(0);
   p->launches += launch_count() - l0;

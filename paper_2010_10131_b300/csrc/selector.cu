@@ -32,6 +32,9 @@ struct State {
   std::vector<float> params;
   Tree tree;
 };
+}  // namespace sel
+bool selector_class_fits(int k, double lg);
+namespace sel {
 // Whether a class can run a mode of log2 size lg: the full-Jacobi classes
 // need I_n <= 1024, the other EIG classes I_n <= 32768 (feature 0 is log2 I_n).
 bool class_fits(int k, double lg) {
@@ -39,6 +42,10 @@ bool class_fits(int k, double lg) {
   const bool jac = k == ATK_CLASS_EIG_JACOBI || k == ATK_CLASS_EIG_JACOBI_SMALL;
   return lg <= (jac ? 10.0 : 15.0) + 1e-9;
 }
+
+}  // namespace sel
+bool selector_class_fits(int k, double lg) { return sel::class_fits(k, lg); }
+namespace sel {
 
 State& state() {
   static State s;

@@ -93,8 +93,38 @@ def test_auto_plan_uses_the_selector():
     plan.close()
     atk.lib().atucker_selector_clear()
     plan = atk.Plan([30, 20, 10], [4, 4, 4], solver=[atk.AUTO] * 3)
-    assert plan.classes == [atk.CLASS_EIG] * 3  # no selector loaded: EIG
+    assert plan.classes == [atk.CLASS_EIG] * 3  # no selector loaded: EIG until the first run times the classes
     plan.close()
+
+
+@pytest.mark.gpu
+def test_auto_without_selector_settles_classes_by_timing():
+    """No selector loaded: the first run times every class that fits each AUTO
+    mode and keeps the fastest; a second plan of the same key takes the cached
+    choice, and either gives bit for bit what a plan built with those classes
+    gives (the search changes which kernels run, not what they compute)."""
+    torch = _gpu()
+    atk.lib().atucker_selector_clear()
+    dims, ranks = [48, 200, 36], [6, 10, 5]
+    g = torch.Generator().manual_seed(3)
+    x = torch.randn(dims[0] * dims[1] * dims[2], generator=g).cuda()
+    p1 = atk.Plan(dims, ranks, solver=[atk.AUTO, atk.EIG, atk.AUTO])
+    assert p1.classes == [atk.CLASS_EIG] * 3
+    c1, f1 = p1.run(x)
+    chosen = p1.classes
+    assert chosen[1] == atk.CLASS_EIG  # a fixed mode is not searched
+    assert all(0 <= c < atk.NUM_CLASSES for c in chosen)
+    c1b, f1b = p1.run(x)
+    p2 = atk.Plan(dims, ranks, solver=[atk.AUTO, atk.EIG, atk.AUTO])
+    c2, f2 = p2.run(x)
+    assert p2.classes == chosen
+    p3 = atk.Plan(dims, ranks, classes=chosen)
+    c3, f3 = p3.run(x)
+    torch.cuda.synchronize()
+    for a, b in ((c1b, c3), (f1b, f3), (c2, c3), (f2, f3), (c1, c3), (f1, f3)):
+        assert torch.equal(a, b)
+    for p in (p1, p2, p3):
+        p.close()
 
 
 def _gpu():
