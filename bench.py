@@ -254,9 +254,12 @@ def run_ours(args):
     for _ in range(args.warmup):
         concurrent_step(plans)
     # Serial leg: one tensor at a time, so that each Gram launch has the GPU to
-    # itself; its CUDA-event durations give the kernel's roofline figure.
+    # itself; its CUDA-event durations give the kernel's roofline figure.  The
+    # fused TTM + next-mode Gram is off in this leg, so every mode's Gram runs
+    # in the Gram kernel whose flops the figure counts.
     for p, _, _ in plans:
         p.sync()
+        p.set_option(atk.OPT_FUSE_TTM_GRAM, 0)
         p.set_timing(True)
     serial_ms = timed(plans, args.steps, serial_step)
     stims = [p.timings() for p, _, _ in plans]

@@ -156,7 +156,13 @@ typedef enum {
    * rounding; extra device memory (allocated at the first such run): the
    * largest unfolding plus the largest TTM result.  0 (default): the
    * matricization-free path. */
-  ATK_OPT_EXPLICIT_UNFOLD = 8
+  ATK_OPT_EXPLICIT_UNFOLD = 8,
+  /* 1: where the next mode in the processing order is an EIG mode with
+   * 16 <= I_m <= 128, this mode's R_n <= 64 and the precision is ATK_FP32,
+   * the TTM closing this mode also forms the next mode's Gram from its output
+   * tiles (atucker_ttm_gram), and that mode skips its Gram pass over Y'.
+   * 0 (default): every Gram reads its input from memory. */
+  ATK_OPT_FUSE_TTM_GRAM = 9
 } atucker_option;
 
 typedef struct atucker_plan_s* atucker_plan_t;
@@ -340,6 +346,24 @@ int atucker_gram_noalloc(const float* y, int64_t lo, int64_t n, int64_t hi, doub
  * bounded device-side wait gave up. */
 int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* U, int64_t R, int precision,
                 float* out, void* stream);
+
+/* Fused truncating TTM and next-mode Gram (Alg. 2: the TTM that closes one
+ * mode and the Gram that opens the next are adjacent steps).
+ *   y, lo, n, hi, U, R  as atucker_ttm (ATK_FP32): out = Y x_n U^T, lo x R x hi
+ *   s, m_size           the next mode m of out: its stride among the rows
+ *                       c = a + lo b of the mode-n view, and its size I_m, so
+ *                       that c = low + s (i + I_m high), i < I_m; s I_m must
+ *                       divide lo hi.  For out's modes in storage order, s is
+ *                       the product of the sizes of the modes below m other
+ *                       than n.
+ *   S_out               device, I_m x I_m float64: S = out_(m) out_(m)^T, the
+ *                       Gram of out's mode m (summed in a fixed order, so
+ *                       reproducible; not bit-identical to atucker_gram)
+ * Needs 1 <= R <= 64 and 16 <= I_m <= 128 (ATK_EUNSUPPORTED otherwise).
+ * Allocates its partial-Gram scratch (at most 8 x 148 x I_m^2 floats) on the
+ * stream; synchronous. */
+int atucker_ttm_gram(const float* y, int64_t lo, int64_t n, int64_t hi, const float* U, int64_t R, int64_t s,
+                     int64_t m_size, float* out, double* S_out, void* stream);
 
 /* Leading-R eigenpairs of the symmetric n x n float64 matrix S (Alg. 2, EIG
  * branch) by parallel-order cyclic Jacobi, on the whole matrix or on a

@@ -14,7 +14,7 @@ import os
 import re
 
 __all__ = [
-    "lib", "abi_symbols", "AtuckerError", "Plan", "Batch", "sthosvd", "gram", "ttm", "eig", "als_mode",
+    "lib", "abi_symbols", "AtuckerError", "Plan", "Batch", "sthosvd", "gram", "ttm", "ttm_gram", "eig", "als_mode",
     "EIG", "ALS", "FP32", "TF32", "BF16", "BF16X3", "FP8E4M3", "FP32C", "EIG_ROT_FP32", "EIG_ROT_FP64",
 ]
 
@@ -28,7 +28,7 @@ EIG, ALS = 0, 1
 FP32, TF32, BF16, BF16X3, FP8E4M3, FP32C = 0, 1, 2, 3, 4, 5
 EIG_ROT_FP32, EIG_ROT_FP64 = 0, 1
 OPT_EIG_ARITH, OPT_SYNC, OPT_JACOBI_MAX_SWEEPS, OPT_TIMING, OPT_EIG_METHOD, OPT_GRAM_REFINE = 1, 2, 3, 4, 5, 6
-OPT_WAIT_LIMIT, OPT_EXPLICIT_UNFOLD = 7, 8
+OPT_WAIT_LIMIT, OPT_EXPLICIT_UNFOLD, OPT_FUSE_TTM_GRAM = 7, 8, 9
 EIG_AUTO, EIG_FULL_JACOBI, EIG_SUBSPACE = 0, 1, 2
 BATCH_OPT_VARIANT, BATCH_OPT_GRAPH, BATCH_OPT_SYNC, BATCH_OPT_JACOBI_MAX_SWEEPS = 1, 2, 3, 4
 AUTO = -1
@@ -65,6 +65,7 @@ _SIGS = {
     "atucker_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "atucker_gram_noalloc": (_i32, [_vp, _i64, _i64, _i64, _vp, _vp]),
     "atucker_ttm": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _i32, _vp, _vp]),
+    "atucker_ttm_gram": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp, _vp]),
     "atucker_eig": (_i32, [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _vp, _vp]),
     "atucker_als_mode": (_i32, [_vp, _i64, _i64, _i64, _i64, _vp, _u64, _i32, _i32, _i32, _vp, _vp, _vp]),
     "atucker_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp]),
@@ -340,6 +341,21 @@ def ttm(y, lo: int, n: int, hi: int, U, precision: int = FP32):
     _check(lib().atucker_ttm(_dev(y, torch.float32), lo, n, hi, _dev(Ucm, torch.float32), R, precision,
                              _dev(out, torch.float32), _stream_ptr()), "atucker_ttm")
     return out
+
+
+def ttm_gram(y, lo: int, n: int, hi: int, U, s: int, m_size: int):
+    """Fused TTM and next-mode Gram (atucker_ttm_gram): returns (out, S) with out
+    the flat (lo, R, hi) TTM result and S the (I_m, I_m) Gram of out's mode of
+    size m_size and row stride s."""
+    torch = _torch()
+    R = U.shape[1]
+    Ucm = U.t().contiguous().to(torch.float32)
+    out = torch.empty(lo * R * hi, device=y.device, dtype=torch.float32)
+    S = torch.empty(m_size * m_size, device=y.device, dtype=torch.float64)
+    _check(lib().atucker_ttm_gram(_dev(y, torch.float32), lo, n, hi, _dev(Ucm, torch.float32), R, s, m_size,
+                                  _dev(out, torch.float32), _dev(S, torch.float64), _stream_ptr()),
+           "atucker_ttm_gram")
+    return out, S.view(m_size, m_size).t()
 
 
 def eig(S, R: int, eig_arith: int = EIG_ROT_FP32, method: int = EIG_AUTO):

@@ -173,6 +173,14 @@ int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t sc
 int gram_f32_fixed_scratch(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes,
                            cudaStream_t st);
 int ttm_f32(const float* y, const View& v, const float* U, int64_t R, float* out, cudaStream_t st);
+// Fused TTM and next-mode Gram (ttm_gram.cu): out = Y x_n U^T as ttm_f32, and
+// S = the I_m x I_m Gram of the next mode m of out, whose stride among the
+// TTM's rows c is s (c = low + s (i + I_m high)).  Needs 1 <= R <= 64,
+// 16 <= I_m <= 128 and I_m s dividing J (ttm_gram_ok).
+bool ttm_gram_ok(const View& v, int64_t R, int64_t s, int64_t Im);
+size_t ttm_gram_scratch_bytes(const View& v, int64_t R, int64_t s, int64_t Im);
+int ttm_gram(const float* y, const View& v, const float* U, int64_t R, int64_t s, int64_t Im, float* out,
+             double* S, void* scratch, size_t scratch_bytes, cudaStream_t st);
 // C (n x R, float64) = sum_c Y(c, i) P(c, r); P is a (lo, R, hi) tensor.
 size_t cross_scratch_bytes(const View& v, int64_t R);
 int cross_f32(const float* y, const View& v, const float* P, int64_t R, double* C, float* scratch,

@@ -172,7 +172,8 @@ struct atucker_plan_s {
   cudaStream_t st = nullptr;
   int eig_arith = ATK_EIG_ROT_FP32, eig_method = ATK_EIG_AUTO, sync = 0, max_sweeps = 40, gram_refine = 1;
   long long wait_polls = 0;  // ATK_OPT_WAIT_LIMIT (0: default)
-  int explicit_unfold = 0;   // ATK_OPT_EXPLICIT_UNFOLD
+  int explicit_unfold = 0;
+  int fuse_tg = 0;  // ATK_OPT_FUSE_TTM_GRAM   // ATK_OPT_EXPLICIT_UNFOLD
   // Exhaustive timed search (AUTO modes without a confident prediction):
   // candidate classes per mode, timed at the first run.
   int ncand[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -249,6 +250,21 @@ static int validate(int order, const int64_t* dims, const int64_t* ranks, const 
   return ATK_OK;
 }
 
+// The next mode's stride among the TTM rows of mode n and its size, when the
+// fused TTM + next-mode Gram can run the step (float32 form only).  cur is the
+// shape before mode n is truncated.
+static bool fuse_geometry(const atucker_plan_s* p, int step, const int64_t* cur, const View& v, int64_t R,
+                          int64_t* s, int64_t* Im) {
+  if (p->precision != ATK_FP32 || step + 1 >= p->order) return false;
+  const int n = p->mode_order[step], m = p->mode_order[step + 1];
+  int64_t st = 1;
+  for (int k = 0; k < m; ++k)
+    if (k != n) st *= cur[k];
+  *s = st;
+  *Im = cur[m];
+  return ttm_gram_ok(v, R, st, cur[m]);
+}
+
 static int plan_alloc(atucker_plan_s* p) {
   int64_t cur[8];
   for (int k = 0; k < p->order; ++k) cur[k] = p->dims[k];
@@ -277,6 +293,10 @@ static int plan_alloc(atucker_plan_s* p) {
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP64));
       scratch = std::max(scratch, eig_scratch_bytes(v.n, ATK_EIG_ROT_FP32));
       scratch = std::max(scratch, smallla_scratch_bytes(v.n, R));
+      int64_t fs = 0, fim = 0;
+      const int m = step + 1 < p->order ? p->mode_order[step + 1] : -1;
+      if (m >= 0 && (p->solver[m] == ATK_EIG || p->both[m]) && fuse_geometry(p, step, cur, v, R, &fs, &fim))
+        scratch = std::max(scratch, ttm_gram_scratch_bytes(v, R, fs, fim));
     }
     if (p->solver[n] == ATK_ALS || p->both[n]) {
       any_als = true;
@@ -527,6 +547,10 @@ int atucker_plan_set_option(atucker_plan_t p, int key, int64_t value) {
       if (value != 0 && value != 1) break;
       p->explicit_unfold = (int)value;
       return ATK_OK;
+    case ATK_OPT_FUSE_TTM_GRAM:
+      if (value != 0 && value != 1) break;
+      p->fuse_tg = (int)value;
+      return ATK_OK;
     default:
       break;
   }
@@ -594,6 +618,7 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
     e_first = e_prev;
     p->runs++;
   }
+  bool s_ready = false;  // p->S already holds this mode's Gram (fused into the last TTM)
   for (int step = 0; step < p->order; ++step) {
     const int n = p->mode_order[step];
     const View vn = make_view(p->order, cur, n);
@@ -613,7 +638,9 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
     if (p->solver[n] == ATK_EIG) {
       // S = Y_(n) Y_(n)^T; U = leading eigenvectors; Y' = Y x_n U^T.
       cudaEvent_t mid = tm ? p->ev() : nullptr;
-      if (p->precision == ATK_FP32) {
+      if (s_ready) {
+        // formed by the previous mode's TTM
+      } else if (p->precision == ATK_FP32) {
         ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid, p->gbm[n], p->dev_status));
       } else if (p->precision == ATK_FP32C) {
         ATK_TRY(gram_cmp(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st));
@@ -622,12 +649,13 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
         ATK_TRY(tc_gram(Y, v, p->precision, p->S, (float*)p->scratch, p->scratch_bytes, p->dev_status, st));
         if (mid) ATK_CUDA(cudaEventRecord(mid, st));
       }
-      if (tm) {
+      if (tm && !s_ready) {
         p->recs.push_back({PH_GRAM, e_prev, mid});
         e_prev = mid;
         p->gram_launches++;
+        ATK_TRY(mark(PH_GRAM_REDUCE));
       }
-      ATK_TRY(mark(PH_GRAM_REDUCE));
+      s_ready = false;
       const int em = p->eigm[n] >= 0 ? p->eigm[n] : p->eig_method;
       // A cut that the float32 Gram cannot resolve (ATK_OPT_GRAM_REFINE):
       // recompute this mode's Gram with compensated sums and solve again.
@@ -644,7 +672,15 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
       ATK_TRY(mark(PH_EIG));
       // Tensor cores where the TTM is a dense contraction: with R <= 16 the
       // float32 kernel is already bound by HBM (and exact in float32).
-      if (p->precision == ATK_FP32 || p->precision == ATK_FP32C || R <= TC_TTM_MIN_R)
+      // Fused with the next mode's Gram where that mode is an EIG mode the
+      // fused kernel covers (ATK_OPT_FUSE_TTM_GRAM).
+      int64_t fs = 0, fim = 0;
+      const int m = step + 1 < p->order ? p->mode_order[step + 1] : -1;
+      if (p->fuse_tg && !unfold && !p->explicit_unfold && m >= 0 && p->solver[m] == ATK_EIG &&
+          fuse_geometry(p, step, cur, v, R, &fs, &fim)) {
+        ATK_TRY(ttm_gram(Y, v, U32, R, fs, fim, out, p->S, p->scratch, p->scratch_bytes, st));
+        s_ready = true;
+      } else if (p->precision == ATK_FP32 || p->precision == ATK_FP32C || R <= TC_TTM_MIN_R)
         ATK_TRY(ttm_f32(Y, v, U32, R, out, st));
       else
         ATK_TRY(tc_ttm(Y, v, U32, R, p->precision, out, p->scratch, p->scratch_bytes, p->dev_status, st));
@@ -916,6 +952,24 @@ int atucker_ttm(const float* y, int64_t lo, int64_t n, int64_t hi, const float* 
   ATK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
   ATK_TRY(tc_ttm(y, v, U, R, precision, out, (char*)sc.ptr, bytes - 256, status, st));
   return read_status(status, st);
+}
+
+int atucker_ttm_gram(const float* y, int64_t lo, int64_t n, int64_t hi, const float* U, int64_t R, int64_t s,
+                     int64_t m_size, float* out, double* S_out, void* stream) {
+  if (!y || !U || !out || !S_out) { set_error("null argument"); return ATK_EINVAL; }
+  ATK_TRY(check_view(lo, n, hi));
+  View v{lo, n, hi};
+  if (!ttm_gram_ok(v, R, s, m_size)) {
+    set_error("ttm_gram needs 1 <= R <= 64, 16 <= I_m <= 128 and s I_m dividing lo hi");
+    return ATK_EUNSUPPORTED;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  StreamScratch sc(st);
+  const size_t bytes = ttm_gram_scratch_bytes(v, R, s, m_size);
+  ATK_TRY(sc.alloc(bytes));
+  ATK_TRY(ttm_gram(y, v, U, R, s, m_size, out, S_out, sc.ptr, bytes, st));
+  ATK_CUDA(cudaStreamSynchronize(st));
+  return ATK_OK;
 }
 
 int atucker_eig(const double* S, int64_t n, int64_t R, int eig_arith, int eig_method, float* U_out,
