@@ -434,13 +434,15 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         # The other workloads of the metric, each a bounded leg (few steps):
         # precision sweep, batched form, learned selector against the paper's
-        # decision tree, the Table II stand-ins and the matricization ablation.
+        # decision tree, the Table II stand-ins, the matricization ablation and the
+        # fused TTM + next-mode Gram against the separate kernels.
         xargs = argparse.Namespace(**vars(args))
         xargs.steps, xargs.warmup = min(args.steps, 3), 1
         extra = {}
         for key, fn in (("precision_sweep", run_precision), ("roofline_48x5", run_roofline_small),
                         ("batched", run_batched), ("selector", run_selector_summary),
-                        ("table2", run_table2), ("explicit_ablation", run_explicit)):
+                        ("table2", run_table2), ("explicit_ablation", run_explicit),
+                        ("fused_ttm_gram", run_fused)):
             t0 = time.time()
             try:
                 extra[key] = fn(xargs)
@@ -821,11 +823,14 @@ def time_plan(x, dims, ranks, steps, warmup, **kw):
     import torch
     import paper_2010_10131_b300 as atk
     explicit = kw.pop("explicit", 0)
+    fuse = kw.pop("fuse", 0)
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     p = atk.Plan(dims, ranks, **kw)
     if explicit:
         p.set_option(atk.OPT_EXPLICIT_UNFOLD, 1)
+    if fuse:
+        p.set_option(atk.OPT_FUSE_TTM_GRAM, 1)
     core = torch.empty(p.core_numel, device="cuda")
     fac = torch.empty(p.factors_numel, device="cuda")
     for _ in range(max(warmup, 1)):
@@ -894,6 +899,29 @@ def run_explicit(args):
             torch.cuda.empty_cache()
         row["speedup_free_vs_explicit"] = row["explicit"]["ms"] / row["free"]["ms"]
         row["memory_saved"] = 1.0 - row["free"]["plan_mem_gb"] / max(row["explicit"]["plan_mem_gb"], 1e-12)
+        out.append(row)
+        del x
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_fused(args):
+    """The fused TTM + next-mode Gram (ATK_OPT_FUSE_TTM_GRAM) against the
+    separate kernels, EIG every mode, float32: whole st-HOSVD time of plans
+    that differ only in that option."""
+    import torch
+    import paper_2010_10131_b300 as atk
+    shapes = [("48^5 R8", (48,) * 5, (8,) * 5), ("128^4 R16", (128,) * 4, (16,) * 4),
+              ("96^3 R8", (96,) * 3, (8,) * 3), ("384x96^3 R(32,16,16,16)", (384, 96, 96, 96), (32, 16, 16, 16))]
+    out = []
+    for i, (name, dims, ranks) in enumerate(shapes):
+        x = random_tucker_big(dims, ranks, 9000 + i, noise=0.1)
+        row = {"name": name, "dims": list(dims), "ranks": list(ranks)}
+        for label, fz in (("separate", 0), ("fused", 1)):
+            ms, mem, core, facs, _ = time_plan(x, list(dims), list(ranks), args.steps, args.warmup,
+                                               solver=[atk.EIG] * len(dims), fuse=fz)
+            row[label] = {"ms": ms, "relerr": reconstruct_relerr(x, core, facs, dims, ranks)}
+        row["speedup_fused"] = row["separate"]["ms"] / row["fused"]["ms"]
         out.append(row)
         del x
         torch.cuda.empty_cache()

@@ -255,7 +255,10 @@ static int validate(int order, const int64_t* dims, const int64_t* ranks, const 
 // shape before mode n is truncated.
 static bool fuse_geometry(const atucker_plan_s* p, int step, const int64_t* cur, const View& v, int64_t R,
                           int64_t* s, int64_t* Im) {
-  if (p->precision != ATK_FP32 || step + 1 >= p->order) return false;
+  // Only from a TTM whose rows are contiguous in k (lo == 1, the first mode
+  // in storage order): for lo > 1 a group's fibres lie s apart in memory and
+  // its loads do not coalesce, which costs more than the Gram pass saves.
+  if (p->precision != ATK_FP32 || step + 1 >= p->order || v.lo != 1) return false;
   const int n = p->mode_order[step], m = p->mode_order[step + 1];
   int64_t st = 1;
   for (int k = 0; k < m; ++k)

@@ -24,14 +24,11 @@
 #include <algorithm>
 
 #include "atk_internal.cuh"
+#include "fp32_block.cuh"
 
 namespace atk {
 
 namespace {
-constexpr int FG_NT = 256;      // threads: a 16 x 16 grid
-constexpr int FG_TK = 16;       // k-tile depth of the TTM
-constexpr int FG_BM = 128;      // TTM rows per group
-constexpr int FG_PAD = 4;       // smem row padding (floats)
 constexpr int FG_TG_FLOATS = 12288;  // staged fibres per group: at most 48 KB
 constexpr int FG_MAX_CHAIN = 8192;
 
@@ -44,79 +41,101 @@ struct FibreGeom {
   int ngroups;
 };
 
-// Row rho of group g -> its TTM row c, or -1 for a padding row.  Rows are
-// ordered rho = l + L (i + Im h), so consecutive rows are consecutive lows
-// (consecutive addresses when lo > 1).
-__device__ __forceinline__ int fibre_row(const FibreGeom& G, int g, int rho) {
-  const int l = rho % G.L, t = rho / G.L;
-  const int i = t % G.Im, h = t / G.Im;
-  if (h >= G.H) return -1;
-  const int low = (g % G.nlowc) * G.L + l;
-  const int high = (g / G.nlowc) * G.H + h;
-  if (low >= G.s || high >= G.nhigh) return -1;
-  return low + G.s * (i + G.Im * high);
+// Rows are ordered rho = l + L (i + Im h), so consecutive rows are
+// consecutive lows (consecutive addresses when lo > 1).  RowInfo caches the
+// group-independent part of each row's index arithmetic in shared memory
+// (the divisions would otherwise outnumber the FMAs):
+//   x  = l + s (i + Im h), the row's offset from the group's first row c, or
+//        -1 when rho is beyond the group's L Im H rows;
+//   y  = l | h << 16, checked against the group's remaining lows and highs;
+//   z  = R (l + L h) (GI + PAD) + i, the row's place in the staged fibres.
+struct GroupBase {
+  int c0, lowrem, highrem;
+};
+
+__device__ __forceinline__ GroupBase group_base(const FibreGeom& G, int g) {
+  const int lc = g % G.nlowc, hb = g / G.nlowc;
+  return {lc * G.L + G.s * G.Im * (hb * G.H), G.s - lc * G.L, G.nhigh - hb * G.H};
 }
 
-// RB: R rounded up to 16 / 32 / 64 (TN = RB / 16 columns per thread, 8 rows).
-// GI: I_m rounded up to 32 / 64 / 128 (GT = GI / 16 Gram rows and columns per
-// thread).  The Gram accumulators live in registers across the CTA's groups.
-template <int RB, int GI, int MINB>
-__global__ void __launch_bounds__(FG_NT, MINB)
+// Row c of a cached row in group gb, or -1 for a padding row.
+__device__ __forceinline__ int row_c(const int4& q, const GroupBase& gb) {
+  if (q.x < 0) return -1;
+  return ((q.y & 0xffff) < gb.lowrem && (q.y >> 16) < gb.highrem) ? gb.c0 + q.x : -1;
+}
+
+// TTM tile BM x RB (the plain TTM kernel's shapes: 256 x 16, 128 x 32,
+// 128 x 64); Gram tile GI x GI with GI = I_m rounded up to 32 / 64 / 128,
+// accumulated in registers across the CTA's groups.  Both are the shared
+// register block (packed FMA pairs); the Gram's diagonal tile skips its
+// lower-left quadrant, which the reduction reads from the mirror entries.
+template <int BM, int RB, int TM, int TN, int GI, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 ttm_gram_kernel(const float* __restrict__ y, const float* __restrict__ U, float* __restrict__ out,
                 const FibreGeom G, float* __restrict__ part) {
-  constexpr int TN = RB / 16;
+  using TB = Block<BM, RB, TM, TN, true>;
   constexpr int GT = GI / 16;
-  constexpr int SA = FG_TK * (FG_BM + FG_PAD), SB = FG_TK * (RB + FG_PAD), TGP = GI + FG_PAD;
+  using GB = Block<GI, GI, GT, GT, true>;
+  constexpr int LDA = BM + PAD, LDB = RB + PAD, TGP = GI + PAD;
+  constexpr int SA = TK * LDA, SB = TK * LDB;
+  constexpr int PER = TK * BM / NT;  // A values per thread per k-tile
+  constexpr int BPER = TK * RB / NT > 0 ? TK * RB / NT : 1;
   extern __shared__ __align__(16) float smem[];
+  __shared__ int4 rinfo[BM];
   float* const sA = smem;           // [2][TK][BM + PAD]: Y rows, k-major
   float* const sB = smem + 2 * SA;  // [2][TK][RB + PAD]: U
   float* const Tg = sB + 2 * SB;    // [L H R][GI + PAD]: the group's fibres
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x;
   const int KG = G.L * G.H * G.R;
   // Columns i >= Im of the staged fibres are never written: zero them once.
-  for (int e = tid; e < KG * TGP; e += FG_NT) Tg[e] = 0.f;
-  float gacc[GT][GT];
-#pragma unroll
-  for (int u = 0; u < GT; ++u)
-#pragma unroll
-    for (int v = 0; v < GT; ++v) gacc[u][v] = 0.f;
+  for (int e = tid; e < KG * TGP; e += NT) Tg[e] = 0.f;
+  for (int rho = tid; rho < BM; rho += NT) {
+    const int l = rho % G.L, t = rho / G.L;
+    const int i = t % G.Im, h = t / G.Im;
+    rinfo[rho] = h < G.H ? make_int4(l + G.s * (i + G.Im * h), l | (h << 16), G.R * (l + G.L * h) * TGP + i, 0)
+                         : make_int4(-1, 0, 0, 0);
+  }
+  __syncthreads();
+  GB gb;
+  gb.init();
 
   const bool lanes_k = G.lo == 1;  // Y(c, k) contiguous in k
-  const int ntile = (G.n + FG_TK - 1) / FG_TK;
-  // A loader: lanes_k: k = km, rows mm + 16 e; else: row mm, k = km + 2 e.
-  const int a_km = lanes_k ? tid % 16 : tid / FG_BM;
-  const int a_mm = lanes_k ? tid / 16 : tid % FG_BM;
+  const int ntile = (G.n + TK - 1) / TK;
+  // A loader: lanes_k: k = a_km, rows a_mm + 16 e; else: row a_mm, k = a_km + (NT / BM) e.
+  const int a_km = lanes_k ? tid % 16 : tid / BM;
+  const int a_mm = lanes_k ? tid / 16 : tid % BM;
   // B loader: k = tid % 16, columns tid / 16 + 16 e.
   const int b_km = tid % 16, b_mm = tid / 16;
 
   for (int g = blockIdx.x; g < G.ngroups; g += gridDim.x) {
-    int aoff[8];
+    const GroupBase gbase = group_base(G, g);
+    int aoff[PER];
     if (lanes_k) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int c = fibre_row(G, g, a_mm + 16 * e);
+      for (int e = 0; e < PER; ++e) {
+        const int c = row_c(rinfo[a_mm + 16 * e], gbase);
         aoff[e] = c >= 0 ? G.n * c : -1;
       }
     } else {
-      const int c = fibre_row(G, g, a_mm);
+      const int c = row_c(rinfo[a_mm], gbase);
       aoff[0] = c >= 0 ? (c % G.lo) + G.lo * G.n * (c / G.lo) : -1;
     }
-    float ra[8], rb[TN];
+    float ra[PER], rb[BPER];
     auto fetch = [&](int k0) {
       if (lanes_k) {
         const int k = k0 + a_km;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) ra[e] = (aoff[e] >= 0 && k < G.n) ? __ldg(y + aoff[e] + k) : 0.f;
+        for (int e = 0; e < PER; ++e) ra[e] = (aoff[e] >= 0 && k < G.n) ? __ldg(y + aoff[e] + k) : 0.f;
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int k = k0 + a_km + 2 * e;
+        for (int e = 0; e < PER; ++e) {
+          const int k = k0 + a_km + (NT / BM) * e;
           ra[e] = (aoff[0] >= 0 && k < G.n) ? __ldg(y + aoff[0] + G.lo * k) : 0.f;
         }
       }
       const int k = k0 + b_km;
 #pragma unroll
-      for (int e = 0; e < TN; ++e) {
+      for (int e = 0; e < BPER; ++e) {
         const int r = b_mm + 16 * e;
         rb[e] = (k < G.n && r < G.R) ? __ldg(U + k + G.n * r) : 0.f;
       }
@@ -126,121 +145,92 @@ ttm_gram_kernel(const float* __restrict__ y, const float* __restrict__ U, float*
       float* b = sB + buf * SB;
       if (lanes_k) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) a[a_km * (FG_BM + FG_PAD) + a_mm + 16 * e] = ra[e];
+        for (int e = 0; e < PER; ++e) a[a_km * LDA + a_mm + 16 * e] = ra[e];
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) a[(a_km + 2 * e) * (FG_BM + FG_PAD) + a_mm] = ra[e];
+        for (int e = 0; e < PER; ++e) a[(a_km + (NT / BM) * e) * LDA + a_mm] = ra[e];
       }
 #pragma unroll
-      for (int e = 0; e < TN; ++e) b[b_km * (RB + FG_PAD) + b_mm + 16 * e] = rb[e];
+      for (int e = 0; e < BPER; ++e) b[b_km * LDB + b_mm + 16 * e] = rb[e];
     };
 
-    // ---- TTM: acc(rho, r) = sum_k Y(c(rho), k) U(k, r), rows ty*8.., columns tx*TN..
-    float acc[8][TN];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-      for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
+    // ---- TTM: T(rho, r) = sum_k Y(c(rho), k) U(k, r)
+    TB tb;
+    tb.init();
     fetch(0);
     store(0);
     __syncthreads();
     for (int t = 0; t < ntile; ++t) {
       const int buf = t & 1;
-      if (t + 1 < ntile) fetch((t + 1) * FG_TK);
-      const float* a = sA + buf * SA;
-      const float* b = sB + buf * SB;
-#pragma unroll
-      for (int kk = 0; kk < FG_TK; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(a + kk * (FG_BM + FG_PAD) + ty * 8);
-        const float4 a1 = *reinterpret_cast<const float4*>(a + kk * (FG_BM + FG_PAD) + ty * 8 + 4);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        float bv[TN];
-#pragma unroll
-        for (int v = 0; v < TN; ++v) bv[v] = b[kk * (RB + FG_PAD) + tx * TN + v];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-          for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
-      }
+      if (t + 1 < ntile) fetch((t + 1) * TK);
+      tb.mma(sA + buf * SA, sB + buf * SB);
       if (t + 1 < ntile) store(buf ^ 1);
       __syncthreads();
     }
 
     // ---- epilogue: write Y' and stage the fibres (zeros for padding slots)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int rho = ty * 8 + u;
-      const int c = fibre_row(G, g, rho);
-      const int l = rho % G.L, t = rho / G.L;
-      const int i = t % G.Im, h = t / G.Im;
-      const bool slot = h < G.H;  // rho < L Im H
-      const int base = c >= 0 ? (c % G.lo) + G.lo * G.R * (c / G.lo) : 0;
+    for (int u = 0; u < TM; ++u) {
+      const int4 q = rinfo[TB::row_of(tb.ty, u)];
+      const int c = row_c(q, gbase);
+      const int base = c < 0 ? 0 : (lanes_k ? G.R * c : (c % G.lo) + G.lo * G.R * (c / G.lo));
 #pragma unroll
       for (int v = 0; v < TN; ++v) {
-        const int r = tx * TN + v;
+        const int r = TB::col_of(tb.tx, v);
         if (r >= G.R) continue;
-        if (c >= 0) out[base + G.lo * r] = acc[u][v];
-        if (slot) Tg[(r + G.R * (l + G.L * h)) * TGP + i] = c >= 0 ? acc[u][v] : 0.f;
+        const float val = tb.acc(u, v);
+        if (c >= 0) out[base + G.lo * r] = val;
+        if (q.x >= 0) Tg[q.z + r * TGP] = c >= 0 ? val : 0.f;
       }
     }
     __syncthreads();
 
-    // ---- Gram: gacc(i, j) += sum over the group's fibres T(i, kg) T(j, kg)
-    for (int kg = 0; kg < KG; ++kg) {
-      const float* row = Tg + kg * TGP;
-      float ai[GT], aj[GT];
-#pragma unroll
-      for (int u = 0; u < GT; u += 2) {
-        const float2 p = *reinterpret_cast<const float2*>(row + ty * GT + u);
-        const float2 q = *reinterpret_cast<const float2*>(row + tx * GT + u);
-        ai[u] = p.x; ai[u + 1] = p.y;
-        aj[u] = q.x; aj[u + 1] = q.y;
-      }
-#pragma unroll
-      for (int u = 0; u < GT; ++u)
-#pragma unroll
-        for (int v = 0; v < GT; ++v) gacc[u][v] = fmaf(ai[u], aj[v], gacc[u][v]);
-    }
+    // ---- Gram: S_part(i, j) += sum over the group's fibres T(i, kg) T(j, kg)
+#pragma unroll 4
+    for (int kg = 0; kg < KG; ++kg) gb.template step<true, TGP, TGP>(Tg, Tg, kg);
     // The next group's first shared-memory writes go to sA / sB; Tg is
     // rewritten only after that group's main loop, whose barriers order it
     // after every thread's Gram reads here.
   }
-  // ---- this CTA's partial Gram (I_m x I_m, column-major)
+  // ---- this CTA's partial Gram (I_m x I_m, column-major; lower-left
+  // quadrant entries of the tile are not computed and never read)
   float* p = part + (int64_t)blockIdx.x * G.Im * G.Im;
 #pragma unroll
   for (int u = 0; u < GT; ++u)
 #pragma unroll
     for (int v = 0; v < GT; ++v) {
-      const int i = ty * GT + u, j = tx * GT + v;
-      if (i < G.Im && j < G.Im) p[i + G.Im * j] = gacc[u][v];
+      const int i = GB::row_of(gb.ty, u), j = GB::col_of(gb.tx, v);
+      if (i <= j && j < G.Im) p[i + G.Im * j] = gb.acc(u, v);
     }
 }
 
 // S(i, j) = sum over the CTAs' partials in CTA order, float-float, rounded to
-// float64.  The partials are exactly symmetric (fmaf(a, b) == fmaf(b, a)), so
-// S is too.
+// float64, read from the upper triangle for both (i, j) and (j, i), so S is
+// exactly symmetric.
 __global__ void ttm_gram_reduce_kernel(const float* __restrict__ part, int nparts, int Im, double* __restrict__ S) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= Im * Im) return;
+  const int i = e % Im, j = e / Im;
+  const int up = min(i, j) + Im * max(i, j);  // the partials hold the upper triangle
   FFSum acc;
-  for (int p = 0; p < nparts; ++p) acc.add(part[(int64_t)p * Im * Im + e]);
+  for (int p = 0; p < nparts; ++p) acc.add(part[(int64_t)p * Im * Im + up]);
   S[e] = acc.value();
 }
 
 int rb_of(int64_t R) { return R <= 16 ? 16 : (R <= 32 ? 32 : 64); }
+int bm_of(int rb) { return rb == 16 ? 256 : 128; }
 int gi_of(int64_t Im) { return Im <= 32 ? 32 : (Im <= 64 ? 64 : 128); }
 
 size_t smem_of(int rb, int gi, int KG) {
-  return sizeof(float) * ((size_t)2 * FG_TK * (FG_BM + FG_PAD) + (size_t)2 * FG_TK * (rb + FG_PAD) +
-                          (size_t)KG * (gi + FG_PAD));
+  return sizeof(float) * ((size_t)2 * TK * (bm_of(rb) + PAD) + (size_t)2 * TK * (rb + PAD) + (size_t)KG * (gi + PAD));
 }
 
 // Fibre slots and group counts for the geometry; false if it does not fit.
 bool make_geom(const View& v, int64_t R, int64_t s, int64_t Im, FibreGeom& G) {
   const int64_t J = v.J();
-  if (R < 1 || R > 64 || Im < 16 || Im > FG_BM || s < 1 || J % (s * Im) != 0) return false;
+  if (R < 1 || R > 64 || Im < 16 || Im > 128 || s < 1 || J % (s * Im) != 0) return false;
   const int gi = gi_of(Im);
-  int64_t P = std::min<int64_t>(FG_BM / Im, FG_TG_FLOATS / (R * (gi + FG_PAD)));
+  int64_t P = std::min<int64_t>(bm_of(rb_of(R)) / Im, FG_TG_FLOATS / (R * (gi + PAD)));
   if (P < 1) return false;
   G.lo = (int)v.lo;
   G.n = (int)v.n;
@@ -265,21 +255,24 @@ bool make_geom(const View& v, int64_t R, int64_t s, int64_t Im, FibreGeom& G) {
 
 template <int RB, int GI>
 struct FgVariant {
-  static constexpr int MINB = (RB == 64 && GI == 128) ? 1 : 2;
+  static constexpr int BM = RB == 16 ? 256 : 128;
+  static constexpr int TM = 8, TN = RB == 64 ? 4 : 2;
+  static constexpr int MINB = 2;
+  static constexpr auto kernel = ttm_gram_kernel<BM, RB, TM, TN, GI, MINB>;
   static int occupancy(size_t smem) {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(ttm_gram_kernel<RB, GI, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_of(RB, GI, FG_TG_FLOATS / (GI + FG_PAD)));
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_of(RB, GI, FG_TG_FLOATS / (GI + PAD)));
       attr = true;
     }
     int o = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, ttm_gram_kernel<RB, GI, MINB>, FG_NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, NT, smem);
     return std::max(1, o);
   }
   static void launch(int grid, size_t smem, const float* y, const float* U, float* out, const FibreGeom& G,
                      float* part, cudaStream_t st) {
-    ttm_gram_kernel<RB, GI, MINB><<<grid, FG_NT, smem, st>>>(y, U, out, G, part);
+    kernel<<<grid, NT, smem, st>>>(y, U, out, G, part);
   }
 };
 
