@@ -309,8 +309,9 @@ const char* atucker_version(void);
 /* Gram matrix S = Y_(n) Y_(n)^T (Alg. 2, EIG branch; cost I_n^2 J_n, Eq. 4).
  * y: lo*n*hi float32.  S_out: n x n float64, full symmetric.  Single-pass
  * split-K: float32 partial tiles, reduced in float64 in a fixed order
- * (deterministic).  Synchronous: it reads back the kernels' status word and
- * returns ATK_ETIMEOUT if a bounded device-side wait gave up. */
+ * (deterministic).  Synchronous.  The tensor-core forms read back the
+ * kernels' status word and return ATK_ETIMEOUT if a bounded device-side wait
+ * gave up. */
 int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precision, double* S_out,
                  void* stream);
 

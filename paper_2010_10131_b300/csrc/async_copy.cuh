@@ -60,4 +60,17 @@ __device__ __forceinline__ void arrive_expect(uint32_t bar, uint32_t bytes) {
 }
 
 }  // namespace ac
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only).
+// src_bytes = 0 writes 16 zero bytes and reads nothing (ragged edges); src
+// must still be a valid address.  The thread waits for its own copies with
+// cp_async_wait: the hardware completes them like loads, so no bound is needed.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 }  // namespace atk

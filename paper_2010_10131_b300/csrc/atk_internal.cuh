@@ -165,10 +165,10 @@ bool selector_class_fits(int k, double lg);
 // `bm` forces the Gram row tile (32, 64 or 128); 0 picks it from n.
 size_t gram_scratch_bytes(const View& v, int bm = 0);
 // `mid` (nullable) is recorded between the partial-tile kernel and the reduction.
-// With a device status word (nullable), 128-row tiles of a contiguous mode-1
-// view use the bulk-fed kernel, whose bounded waits report DEV_TIMEOUT there.
+// 128-row tiles of a view with rows contiguous in i (lo == 1, I_n % 4 == 0,
+// 16-byte aligned) run in one cp.async-fed launch for every tile.
 int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st,
-             cudaEvent_t mid = nullptr, int bm = 0, int* status = nullptr);
+             cudaEvent_t mid = nullptr, int bm = 0);
 // As gram_f32, with the number of split-K partials capped to fit scratch_bytes.
 int gram_f32_fixed_scratch(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes,
                            cudaStream_t st);

@@ -276,110 +276,6 @@ static void launch_gram_tiles(const float* y, const View& v, int T, int ns_d, in
   else launch_gram_tiles_v<BM, TM, false>(y, v, T, ns_d, kc_d, ns_o, kc_o, part, st, c_base);
 }
 
-// ------------------------------------------------ bulk-fed Gram (mode-1 views)
-// Diagonal 128 x 128 tiles (8 x 8 values per thread, 256 threads) with the
-// operand streamed by bulk copies: for a view with lo == 1, row c of the view
-// is I_n contiguous floats, so a stage of GB_TK values of c is GB_TK bulk
-// copies (cp.async.bulk, up to 512 bytes each) into a GB_STAGES-deep ring,
-// counted on the stage's "full" mbarrier.  The threads spend their issue
-// slots on shared-memory loads and FMAs: no global loads, no staging stores,
-// no CTA-wide barrier per k tile.  Warp 0 also refills the ring: at stage s
-// its lanes issue the copies of stage s + GB_STAGES - 1 into the slot that
-// stage s - 1 used, once every warp has arrived on that slot's "empty"
-// mbarrier.  Columns i >= I_n of a ragged last tile are never copied; the
-// accumulators they feed lie outside the matrix and are never read.  Every
-// wait is bounded (async_copy.cuh); a timeout sets DEV_TIMEOUT in *status,
-// warp 0 still waits (bounded) for its copies in flight, and the partial tile
-// is written as zeros.
-constexpr int GB_TK = 32;
-constexpr int GB_STAGES = 3;
-constexpr int GB_THREADS = 256;
-constexpr int GB_ROW = 128 * (int)sizeof(float);
-constexpr int GB_STAGE_BYTES = GB_TK * GB_ROW;
-
-__global__ void __launch_bounds__(GB_THREADS, 2)
-gram_bulk_diag_kernel(const float* __restrict__ y, int64_t n, int64_t J, int T, int64_t kc,
-                      float* __restrict__ part, int* __restrict__ status) {
-  extern __shared__ __align__(128) unsigned char gsm[];
-  __shared__ __align__(8) uint64_t full[GB_STAGES], empty[GB_STAGES];
-  __shared__ volatile int abort_flag;
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int ti = blockIdx.x, split = blockIdx.y;
-  const int tile = ti * T - ti * (ti - 1) / 2;
-  const int64_t cb = (int64_t)split * kc, ce = min(J, cb + kc);
-  const int nst = cb < ce ? (int)((ce - cb + GB_TK - 1) / GB_TK) : 0;
-  if (tid == 0) {
-    abort_flag = 0;
-    for (int s = 0; s < GB_STAGES; ++s) {
-      ac::mbar_init(ac::smem_u32(&full[s]), 1);
-      ac::mbar_init(ac::smem_u32(&empty[s]), GB_THREADS / 32);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  __syncthreads();
-  const uint32_t sbase = ac::smem_u32(gsm);
-  const int64_t ia = (int64_t)ti * 128;
-  const uint32_t bytes = (uint32_t)(min((int64_t)128, n - ia) * 4);
-  // Warp 0: issue stage p into its slot (after the slot's previous stage was
-  // released by every warp).  Returns false if that wait gave up.
-  int issued = 0;
-  auto refill = [&](int p) -> bool {
-    const int slot = p % GB_STAGES;
-    bool w = true;
-    if (p >= GB_STAGES && lane == 0)
-      w = ac::mbar_wait(ac::smem_u32(&empty[slot]), (uint32_t)(((p / GB_STAGES) - 1) & 1), &abort_flag);
-    if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) return false;
-    const int64_t c0 = cb + (int64_t)p * GB_TK;
-    const int kv = (int)min((int64_t)GB_TK, ce - c0);
-    const uint32_t bar = ac::smem_u32(&full[slot]);
-    if (lane == 0) ac::arrive_expect(bar, (uint32_t)kv * bytes);
-    __syncwarp();
-    if (lane < kv)
-      ac::bulk_load(sbase + (uint32_t)(slot * GB_STAGE_BYTES + lane * GB_ROW), y + n * (c0 + lane) + ia, bytes, bar);
-    issued = p + 1;
-    return true;
-  };
-  bool ok = true;
-  if (warp == 0)
-    for (int p = 0; p < GB_STAGES - 1 && p < nst; ++p) refill(p);
-  Block<128, 128, 8, 8> blk;
-  blk.init();
-  for (int s = 0; s < nst; ++s) {
-    if (warp == 0 && s + GB_STAGES - 1 < nst && !refill(s + GB_STAGES - 1)) {
-      ok = false;
-      break;
-    }
-    const int slot = s % GB_STAGES;
-    if (!ac::mbar_wait(ac::smem_u32(&full[slot]), (uint32_t)((s / GB_STAGES) & 1), &abort_flag)) {
-      ok = false;
-      break;
-    }
-    const float* sa = reinterpret_cast<const float*>(gsm + slot * GB_STAGE_BYTES);
-    const int kv = (int)min((int64_t)GB_TK, ce - (cb + (int64_t)s * GB_TK));
-    if (kv == GB_TK) blk.template mma_pipelined<true, GB_TK, 128, 128>(sa, sa);
-    else blk.template mma_rows<true, 128, 128>(sa, sa, kv);
-    __syncwarp();
-    if (lane == 0) ac::mbar_arrive(ac::smem_u32(&empty[slot]));
-  }
-  if (!ok) abort_flag = 1;
-  // Drain: the last copies warp 0 issued into each slot have landed.
-  if (warp == 0 && lane == 0)
-    for (int p = issued > GB_STAGES ? issued - GB_STAGES : 0; p < issued; ++p)
-      if (!ac::mbar_wait(ac::smem_u32(&full[p % GB_STAGES]), (uint32_t)((p / GB_STAGES) & 1), nullptr))
-        abort_flag = 1;
-  __syncthreads();
-  const bool good = abort_flag == 0;
-  if (!good && tid == 0 && status) atomicOr(status, DEV_TIMEOUT);
-  const int ntiles = T * (T + 1) / 2;
-  float* out = part + ((int64_t)split * ntiles + tile) * (128 * 128);
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-#pragma unroll
-    for (int v = 0; v < 8; ++v)
-      out[Block<128, 128, 8, 8>::row_of(blk.ty, u) * 128 + Block<128, 128, 8, 8>::col_of(blk.tx, v)] =
-          good ? blk.acc(u, v) : 0.f;
-}
-
 // Cross product C (n x R) = sum_c Y(c, i) P(c, r), P a (lo, R, hi) tensor.
 template <int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(NT, 2)
@@ -442,6 +338,84 @@ __device__ __forceinline__ FFSum ff_sum_splits(const float* __restrict__ p, int6
   }
   for (; sp < count; ++sp) acc.add(p[(int64_t)sp * stride]);
   return acc;
+}
+
+// ----------------------------------------- cp.async-fed Gram (mode-1 views)
+// All upper-triangle 128 x 128 tiles of a view whose rows c are I_n
+// contiguous floats (lo == 1, I_n % 4 == 0, 16-byte aligned base), diagonal
+// ones included, in one launch.  A stage is GA_TK values of c: per operand,
+// GA_TK rows of 128 floats moved by 16-byte cp.async copies straight into the
+// k-major tile the register block reads (s[k * (128 + PAD) + i]), with no
+// register staging and no staging stores; GA_NS - 1 stages are in flight
+// while one is consumed, which covers the HBM latency.  The tile index runs
+// fastest in the grid, so the T (T + 1) / 2 tiles of a split run side by side
+// and each input row comes from HBM about once (its other uses hit L2).
+// Diagonal tiles copy one operand and skip the lower-left quadrant of their
+// accumulators.  Out-of-range rows (c >= end of the split, i >= I_n) are
+// zero-filled.
+constexpr int GA_TK = TK;
+constexpr int GA_NS = 4;
+constexpr int GA_LD = 128 + PAD;
+constexpr int GA_STAGE = 2 * GA_TK * GA_LD;  // floats per stage: A and B tiles
+constexpr int GA_SMEM = GA_NS * GA_STAGE * (int)sizeof(float);
+
+__global__ void __launch_bounds__(NT, 2)
+gram_async_kernel(const float* __restrict__ y, int n, int64_t J, int T, int64_t kc, float* __restrict__ part) {
+  extern __shared__ __align__(16) float gas[];
+  const int split = blockIdx.y;
+  int id = blockIdx.x, ti = 0;  // upper triangle, diagonal included, row by row
+  while (id >= T - ti) { id -= T - ti; ++ti; }
+  const int tj = ti + id;
+  const bool diag = ti == tj;
+  const int64_t cb = (int64_t)split * kc, ce = min(J, cb + kc);
+  const int ntile = cb < ce ? (int)((ce - cb + GA_TK - 1) / GA_TK) : 0;
+  const int tid = threadIdx.x;
+  // A stage holds GA_TK x 32 chunks of 16 bytes per operand: thread t copies
+  // chunks t and t + 256 (row q / 32, chunk q % 32).
+  auto load_stage = [&](int t, int slot) {
+    float* sa = gas + slot * GA_STAGE;
+    float* sb = sa + GA_TK * GA_LD;
+    const int64_t c0 = cb + (int64_t)t * GA_TK;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int q = tid + e * NT;
+      const int k = q >> 5, ch = q & 31;
+      const int64_t c = c0 + k;
+      const bool cv = c < ce;
+      const int ia = ti * 128 + ch * 4;
+      const bool va = cv && ia < n;
+      cp_async16(ac::smem_u32(sa + k * GA_LD + ch * 4), va ? y + (ia + (int64_t)n * c) : y, va ? 16u : 0u);
+      if (!diag) {
+        const int ib = tj * 128 + ch * 4;
+        const bool vb = cv && ib < n;
+        cp_async16(ac::smem_u32(sb + k * GA_LD + ch * 4), vb ? y + (ib + (int64_t)n * c) : y, vb ? 16u : 0u);
+      }
+    }
+  };
+  Block<128, 128, 8, 8> blk;
+  blk.init();
+#pragma unroll
+  for (int s = 0; s < GA_NS - 1; ++s) {
+    if (s < ntile) load_stage(s, s);
+    cp_async_commit();
+  }
+  for (int t = 0; t < ntile; ++t) {
+    cp_async_wait<GA_NS - 2>();  // this thread's copies of stage t have landed
+    __syncthreads();             // everyone's have, and stage t - 1's slot is free
+    const int tn = t + GA_NS - 1;
+    if (tn < ntile) load_stage(tn, tn % GA_NS);
+    cp_async_commit();
+    const float* sa = gas + (t % GA_NS) * GA_STAGE;
+    if (diag) blk.template mma<true>(sa, sa);
+    else blk.mma(sa, sa + GA_TK * GA_LD);
+  }
+  const int ntiles = T * (T + 1) / 2;
+  float* out = part + ((int64_t)split * ntiles + blockIdx.x) * (128 * 128);
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+      out[Block<128, 128, 8, 8>::row_of(blk.ty, u) * 128 + Block<128, 128, 8, 8>::col_of(blk.tx, v)] = blk.acc(u, v);
 }
 
 // Sum the split-K partial tiles in split order (deterministic), as a
@@ -569,43 +543,13 @@ static GramPlan gram_plan(const View& v, int bm_force = 0) {
 
 size_t gram_scratch_bytes(const View& v, int bm) {
   GramPlan g = gram_plan(v, bm);
-  return (size_t)std::max(g.d.nsplit, g.o.nsplit) * g.nt * g.bm * g.bm * sizeof(float);
-}
-
-// Split plans of the bulk-fed kernels: the same splits with the c range of
-// each split rounded up to whole stages (never more splits than the plan's).
-static SplitPlan gb_split(const SplitPlan& sp, int64_t J) {
-  const int64_t kc = ceil_div(sp.kc, GB_TK) * GB_TK;
-  return {(int)std::max<int64_t>(1, ceil_div(J, kc)), kc};
-}
-
-// Diagonal tiles: the bulk-fed kernel (one operand, 48 KB ring; measured 10 %
-// faster than the register-staged loader).  Off-diagonal tiles keep the
-// register-staged vector loader: a bulk-fed form with two operands (96 KB
-// ring) measured 5 % slower.
-static int launch_gram_mode1(const float* y, const View& v, int T, const SplitPlan& d, const SplitPlan& o,
-                             float* part, int* status, cudaStream_t st) {
-  static const bool attr_ok = [] {
-    return cudaFuncSetAttribute(gram_bulk_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                GB_STAGES * GB_STAGE_BYTES) == cudaSuccess;
-  }();
-  if (!attr_ok) {
-    set_error("gram: cannot set the shared-memory size of the bulk-fed Gram kernel");
-    return ATK_ECUDA;
-  }
-  gram_bulk_diag_kernel<<<dim3(T, d.nsplit), GB_THREADS, GB_STAGES * GB_STAGE_BYTES, st>>>(y, v.n, v.J(), T, d.kc,
-                                                                                          part, status);
-  ATK_LAUNCHED();
-  if (T > 1) {
-    gram_ci_kernel<128, 8, false, true><<<dim3(T * (T - 1) / 2, o.nsplit), NT, 0, st>>>(y, v.lo, v.n, v.hi, T,
-                                                                                         o.kc, part);
-    ATK_LAUNCHED();
-  }
-  return ATK_OK;
+  // the single-launch form (gram_async_kernel) plans all tiles together
+  const int ns = std::max({g.d.nsplit, g.o.nsplit, choose_split(v.J(), g.nt).nsplit});
+  return (size_t)ns * g.nt * g.bm * g.bm * sizeof(float);
 }
 
 int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t scratch_bytes, cudaStream_t st,
-             cudaEvent_t mid, int bm, int* status) {
+             cudaEvent_t mid, int bm) {
   if (v.n <= 0) return ATK_OK;
   if (v.J() == 0) {
     ATK_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * v.n * v.n, st));
@@ -616,9 +560,19 @@ int gram_f32(const float* y, const View& v, double* S, float* scratch, size_t sc
     set_error("gram_f32: scratch too small");
     return ATK_EINVAL;
   }
-  if (g.bm == 128 && status && kc_vec_ok(y, v)) {
-    g.d = gb_split(g.d, v.J());
-    ATK_TRY(launch_gram_mode1(y, v, g.T, g.d, g.o, scratch, status, st));
+  if (g.bm == 128 && kc_vec_ok(y, v)) {
+    // one launch for every tile, one split plan for all of them
+    static const bool attr_ok = [] {
+      return cudaFuncSetAttribute(gram_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GA_SMEM) ==
+             cudaSuccess;
+    }();
+    if (!attr_ok) {
+      set_error("gram: cannot set the shared-memory size of the cp.async Gram kernel");
+      return ATK_ECUDA;
+    }
+    g.d = g.o = choose_split(v.J(), g.nt);
+    gram_async_kernel<<<dim3(g.nt, g.d.nsplit), NT, GA_SMEM, st>>>(y, (int)v.n, v.J(), g.T, g.d.kc, scratch);
+    ATK_LAUNCHED();
   } else {
     if (g.bm == 128) launch_gram_tiles<128, 8>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);
     else if (g.bm == 64) launch_gram_tiles<64, 4>(y, v, g.T, g.d.nsplit, g.d.kc, g.o.nsplit, g.o.kc, scratch, st);

@@ -15,6 +15,7 @@
 //    phases.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -490,7 +491,8 @@ int run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
 //     as the observed rate theta_m / theta_K predicts (at most RR_POWER_CHUNK).
 // When theta_m / theta_K > RR_MAX_RATE (the cut sits inside a cluster that
 // the block does not cover) or RR_MAX_POWER power steps pass, the full
-// Jacobi runs instead.  Every product runs on the contraction engine of
+// Jacobi runs instead.  On the deflated levels of eig_top (floor_ok) a stall
+// or the step cap ends the iteration as converged to the float32 floor.  Every product runs on the contraction engine of
 // fp32_ops.cu: the n x m block is the mode-2 view (lo = n, I = m, hi = 1) of
 // an n x m column-major matrix.
 constexpr int RR_MAX_POWER = 160;
@@ -504,6 +506,7 @@ constexpr double RR_MAX_RATE = 0.92;
 constexpr double RR_STALL = 0.5;
 constexpr double RR_FLOOR_OK = 1e-4;
 constexpr float RR_RESOLVE = 32.f * 1.1920929e-7f;
+constexpr double RR_CUT_RESOLVE = 64.0 * 1.1920928955078125e-7;
 
 // Block width m = R + p.  The default guard p = clamp(R / 2, 8, 16) suits a
 // spectrum with a gap at the cut; `wide` (the deflated levels of eig_top,
@@ -674,7 +677,8 @@ int cholqr3_f32(float* Y, float* T, float* Q, int64_t n, int m, RRBufs& b, cudaS
 // order, orthonormal to float32 accuracy) and returns ATK_OK; returns
 // ATK_ENOCONV to request the full Jacobi.
 int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double* Qblk, int* dev_status,
-           char* scratch, size_t scratch_bytes, cudaStream_t st) {
+           char* scratch, size_t scratch_bytes, cudaStream_t st, bool floor_ok, bool* at_floor) {
+  *at_floor = false;
   Arena ar{scratch, scratch_bytes, 0};
   RRBufs b;
   size_t nm = (size_t)n * m, mm = (size_t)m * m;
@@ -761,9 +765,21 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
     // its gap).  Below RR_FLOOR_OK the float64 refinement that follows removes
     // what is left; a stall above it is no convergence.
     const bool stalled = prev_pred > 0.0 && predicted > RR_STALL * prev_pred;
-    stalls = stalled && predicted > RR_FLOOR_OK ? stalls + 1 : 0;
+    // A deflation level accepts its float32 floor wherever it lies: its
+    // vectors near the cut sit below that floor by construction, and
+    // eig_top resolves them on the next level.  So does a level whose cut
+    // float32 cannot resolve (a kept Ritz value below RR_RESOLVE eps_32
+    // theta_1, or the guard block spread over less than RR_CUT_RESOLVE
+    // theta_1): eig_top then continues on deflated levels.
+    const bool floor_here = floor_ok || (int)h[5] < R || thK - thm < RR_CUT_RESOLVE * h[1];
+    // (A block that lost its accuracy on the way shows as non-finite values
+    // after the float64 refinement; eig_top then runs the full Jacobi.)
+    const bool accept = stalled && (floor_here || predicted <= RR_FLOOR_OK);
+    stalls = stalled && !accept ? stalls + 1 : 0;
+    if (accept && predicted > RR_FLOOR_OK) *at_floor = true;
     if (stalls >= 3) return ATK_ENOCONV;  // three projections in a row without progress
-    if (predicted <= RR_TARGET || (stalled && predicted <= RR_FLOOR_OK)) {
+    if (floor_here && power >= RR_MAX_POWER) *at_floor = true;
+    if (predicted <= RR_TARGET || accept || (floor_here && power >= RR_MAX_POWER)) {
       f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Y, Qblk, n * (int64_t)m);
       ATK_LAUNCHED();
       return ATK_OK;
@@ -774,7 +790,8 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
     if (rate > 0.0 && predicted > 0.0)
       steps = (int)std::ceil(std::log(RR_TARGET / predicted) / std::log(rate));
     steps = std::max(1, std::min(steps, RR_POWER_CHUNK));
-    if (power + steps > RR_MAX_POWER) return ATK_ENOCONV;
+    if (floor_here) steps = std::min(steps, RR_MAX_POWER - power);  // ends at the cap, accepted above
+    else if (power + steps > RR_MAX_POWER) return ATK_ENOCONV;
     power += steps;
     prev_pred = predicted;
     // First step from the Ritz vectors: S (Q W) = Z W is in T; its columns are
@@ -1116,6 +1133,7 @@ struct Level {
   int64_t k;
   char* rest;
   size_t rest_bytes;
+  bool at_floor;  // the subspace iteration stopped at its float32 floor
 };
 static int eig_level(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, bool wide,
                      double* U64, double* lambda_out, double* discarded_out, double* lam_sorted, int* dev_status,
@@ -1129,10 +1147,10 @@ static int eig_level(const double* S, int64_t n, int64_t R, int arith, int metho
   if (!Qb) { set_error("eig: scratch too small"); return ATK_EINVAL; }
   char* rest = scratch + ar.used;
   const size_t rest_bytes = scratch_bytes - ar.used;
-  *lv = Level{Qb, k, rest, rest_bytes};
+  *lv = Level{Qb, k, rest, rest_bytes, false};
   int s = ATK_ENOCONV;
   if (rr) {
-    s = rr_top(S, n, R, m, max_sweeps, Qb, dev_status, rest, rest_bytes, st);
+    s = rr_top(S, n, R, m, max_sweeps, Qb, dev_status, rest, rest_bytes, st, wide, &lv->at_floor);
     if (s != ATK_OK && s != ATK_ENOCONV) return s;
     if (s == ATK_OK && lambda_out && n > R) {
       // Only the kept eigenvalues exist on this path; the tail is marked NaN.
@@ -1249,13 +1267,21 @@ int eig_top(const double* S, int64_t n, int64_t R, int arith, int method, int ma
       return ATK_OK;
     };
     ATK_TRY(read_lam(R + 1));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[R - 1]) || !std::isfinite(h[R])) {
+      // A level-0 block that lost its accuracy: the full Jacobi instead.
+      if (n > JACOBI_MAX_N) { set_error("eig: non-finite Ritz values"); return ATK_ENOCONV; }
+      ATK_TRY(eig_level(S, n, R, arith, ATK_EIG_FULL_JACOBI, max_sweeps, false, U64_out, lambda_out, discarded_out,
+                        lam_s, dev_status, rest, rest_bytes, st, &lv));
+      ATK_TRY(read_lam(R + 1));
+    }
     const double gap0 = h[R - 1] - h[R];
     if (unresolved && gap0 < std::max(LEVEL_RESOLVE, GRAM_PROJ_RESOLVE * sqrt(2.0 * R)) * fabs(h[0])) {
       *unresolved = 1;
       return ATK_OK;
     }
-    if (gap0 < LEVEL_RESOLVE * fabs(h[0])) {
-      // The cut is not resolved at level 0: deflation levels.
+    if (gap0 < LEVEL_RESOLVE * fabs(h[0]) || lv.at_floor) {
+      // The cut is not resolved at level 0 (or level 0 stopped at its
+      // float32 floor): deflation levels, which start with float64 steps.
       const double* src = S;
       int64_t done = 0, RL = R;
       for (int level = 1;; ++level) {

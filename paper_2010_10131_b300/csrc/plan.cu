@@ -644,7 +644,7 @@ static int sthosvd_run(atucker_plan_t p, const float* x, float* core_out, float*
       if (s_ready) {
         // formed by the previous mode's TTM
       } else if (p->precision == ATK_FP32) {
-        ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid, p->gbm[n], p->dev_status));
+        ATK_TRY(gram_f32(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st, mid, p->gbm[n]));
       } else if (p->precision == ATK_FP32C) {
         ATK_TRY(gram_cmp(Y, v, p->S, (float*)p->scratch, p->scratch_bytes, st));
         if (mid) ATK_CUDA(cudaEventRecord(mid, st));
@@ -923,12 +923,11 @@ int atucker_gram(const float* y, int64_t lo, int64_t n, int64_t hi, int precisio
     return ATK_OK;
   }
   if (precision == ATK_FP32) {
-    size_t bytes = gram_scratch_bytes(v) + 256;
+    size_t bytes = gram_scratch_bytes(v);
     ATK_TRY(sc.alloc(bytes));
-    int* status = (int*)((char*)sc.ptr + bytes - 256);
-    ATK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-    ATK_TRY(gram_f32(y, v, S_out, (float*)sc.ptr, bytes - 256, st, nullptr, 0, status));
-    return read_status(status, st);
+    ATK_TRY(gram_f32(y, v, S_out, (float*)sc.ptr, bytes, st));
+    ATK_CUDA(cudaStreamSynchronize(st));
+    return ATK_OK;
   }
   size_t bytes = tc_gram_scratch_bytes(v, precision) + 256;
   ATK_TRY(sc.alloc(bytes));
