@@ -40,7 +40,7 @@ UNIT = "GB/s"
 TENSORS = [((640, 640, 640), (64, 64, 64)), ((128, 128, 128, 128), (16, 16, 16, 16))]
 WORKLOAD = "plain FP32 st-HOSVD (EIG every mode): 640^3 R64 + 128^4 R16, random Tucker + 1e-3 noise"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
-GRAM_TRAFFIC_RATIO = 1.02  # DRAM bytes / input bytes per Gram launch (ncu capture of the mode-1 Gram)
+GRAM_TRAFFIC_RATIO = 1.07  # DRAM bytes / input bytes per Gram launch (ncu capture of the mode-1 Gram)
 CPU_SAMPLE = ((640, 640, 8), (64, 64, 8))       # cpu_baseline: a 640 x 640 x 8 slab of the workload
 REF_SAMPLE = ((640, 160, 8), (64, 64, 8))       # reference arm: one such slab sample per step
 
@@ -285,15 +285,18 @@ def run_ours(args):
     # Dominant kernel: the Gram partial-tile kernel (float32 CUDA cores).
     # DRAM traffic per Gram call, scaled from one ncu capture of a smaller view
     # of the mode-1 Gram: each launch reads its input once (measured traffic /
-    # input bytes = 1.02), and a call makes two launches (diagonal and
-    # off-diagonal tiles) when the Gram has more than 128 rows.
-    calls, traffic_bytes = 0, 0.0
+    # input bytes = 1.07).  A contiguous mode-1 view (lo == 1, I_n % 4 == 0)
+    # runs all its tiles in one launch; a strided view with more than 128 rows
+    # makes two (diagonal and off-diagonal tiles), each reading the input.
+    calls, traffic_bytes, alg_bytes = 0, 0.0, 0.0
     for d, r in TENSORS:
         cur = list(d)
         for nmode in range(len(d)):
             size = float(np.prod(cur)) * 4
-            launches = 1 if cur[nmode] <= 128 else 2
+            lo = int(np.prod(cur[:nmode]))
+            launches = 1 if (cur[nmode] <= 128 or (lo == 1 and cur[nmode] % 4 == 0)) else 2
             traffic_bytes += GRAM_TRAFFIC_RATIO * size * launches
+            alg_bytes += size
             calls += 1
             cur[nmode] = r[nmode]
     flops = sum(gram_flops(d, r, [0] * len(d)) for d, r in TENSORS) * args.steps
@@ -412,7 +415,8 @@ def run_ours(args):
                                      "launch has the GPU to itself",
                          "achieved_concurrent": achieved_conc,
                          "traffic": traffic_bytes / calls, "traffic_unit": "bytes per Gram call",
-                         "traffic_source": "scaled from ncu dram bytes of gram:1,640,80000 (ratio 1.02 x input)",
+                         "algorithmic_bytes": alg_bytes / calls,
+                         "traffic_source": "scaled from ncu dram bytes of gram:1,640,80000 (ratio 1.07 x input)",
                          "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
                          "flops_per_step": flops / max(args.steps, 1),
                          "ms_per_step": gram_ms / max(args.steps, 1)},
@@ -459,7 +463,8 @@ def run_ours(args):
 
 
 def run_case(args):
-    """Time one step-level operation: --case gram:LO,N,HI, ttm:LO,N,HI,R or eig:N,R[,METHOD].
+    """Time one step-level operation: --case gram:LO,N,HI, ttm:LO,N,HI,R, als:LO,N,HI,R,
+    ttmgram:LO,N,HI,R,S,I_M or eig:N,R[,METHOD].
 
     Used for kernel profiles: the input is synthetic N(0,1) float32 on the
     device, the call goes through the C ABI, and the line reports the
@@ -536,6 +541,17 @@ def run_case(args):
         U = torch.randn(n, R, device="cuda", generator=g)
         fn = lambda: atk.ttm(y, lo, n, hi, U, precision=prec)  # noqa: E731
         flops = 2.0 * n * R * lo * hi
+    elif kind == "als":
+        # one ALS mode update, 5 sweeps (Alg. 3): 4 I_n J_n R_n flops per sweep (Eq. 5)
+        R = vals[3]
+        fn = lambda: atk.als_mode(y, lo, n, hi, R, precision=prec)  # noqa: E731
+        flops = 5 * 4.0 * n * R * lo * hi
+    elif kind == "ttmgram":
+        # fused TTM + next-mode Gram: ttmgram:LO,N,HI,R,S,I_M
+        R, s_m, i_m = vals[3], vals[4], vals[5]
+        U = torch.linalg.qr(torch.randn(n, R, device="cuda", generator=g))[0]
+        fn = lambda: atk.ttm_gram(y, lo, n, hi, U, s_m, i_m)  # noqa: E731
+        flops = 2.0 * n * R * lo * hi + float(i_m) * lo * hi * R  # TTM + I_m^2 J_m with J_m = J R / I_m
     else:
         raise SystemExit(f"unknown case {kind}")
     for _ in range(args.warmup):
@@ -935,7 +951,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default=None, help="profile one op: gram:LO,N,HI, ttm:LO,N,HI,R, eig:N,R[,METHOD] or batched[:COUNT]")
+    ap.add_argument("--case", default=None, help="profile one op: gram:LO,N,HI, ttm:LO,N,HI,R, als:LO,N,HI,R, "
+                    "ttmgram:LO,N,HI,R,S,I_M, eig:N,R[,METHOD] or batched[:COUNT]")
     ap.add_argument("--precision", type=int, default=0,
                     help="0 FP32, 1 TF32, 2 BF16, 3 3xBF16, 4 FP8-e4m3, 5 FP32 compensated (--case)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
