@@ -20,8 +20,9 @@
 //  - P phase: warp w takes i = w, w + 8, ...; lane (c-quad q = lane % 8,
 //    r-group g = lane / 8) holds 4 c x RB/4 r partial sums; the eight warps'
 //    partials are summed through shared memory in a fixed order;
-//  - A phase: item q = tid + 256 k is row i = q % I_n and columns
-//    8 (q / I_n) .. + 7, so consecutive lanes read consecutive rows i.
+//  - A phase: item q = tid + 256 k is rows i = q % nh and i + nh (nh =
+//    ceil(I_n / 2)) and columns 4 (q / nh) .. + 3, so consecutive lanes read
+//    consecutive rows and each 128-bit load of P feeds eight FMAs.
 // The next slab is loaded into registers while the current one is used.
 // Each CTA writes its float32 partial A (I_n x RB); a second kernel sums the
 // partials in CTA order as float-float pairs (deterministic), rounded once
@@ -42,15 +43,18 @@ constexpr int AF_CHAIN = 8192;
 
 template <int RB>
 struct AfSmem {
-  static constexpr int SG = RB / 4;  // r values per lane in the P phase
-  float ys[AF_NMAX * AF_PITCH];      // Ys[i][c]
-  float lt[AF_NMAX * RB];            // L~[i][r]
-  float part[8 * AF_BC * RB];        // per-warp partial P
-  float p[AF_BC * RB];               // P[c][r]
+  static constexpr int SG = RB / 4;   // r values per lane in the P phase
+  static constexpr int PP = RB + 4;   // row pitch of the per-warp partials
+  float ys[AF_NMAX * AF_PITCH];       // Ys[i][c]
+  float lt[AF_NMAX * RB];             // L~[i][r]
+  float part[8 * AF_BC * PP];         // per-warp partial P, row 8 (c % 4) + c / 4
+  float p[AF_BC * RB];                // P[c][r]
 };
 
-template <int RB>
-__global__ void __launch_bounds__(AF_THREADS) als_fused_kernel(const float* __restrict__ y, int lo, int n, int64_t J,
+// CSN: the number of c ranges an A item is split over (a template
+// parameter, so the common CSN = 1 kernel carries none of the split's code).
+template <int RB, int CSN>
+__global__ void __launch_bounds__(AF_THREADS, 2) als_fused_kernel(const float* __restrict__ y, int lo, int n, int64_t J,
                                                                const float* __restrict__ Lt, int R, int64_t chunk,
                                                                float* __restrict__ part_out, float* __restrict__ Rk,
                                                                int write_rk) {
@@ -65,14 +69,22 @@ __global__ void __launch_bounds__(AF_THREADS) als_fused_kernel(const float* __re
     const int i = idx / RB, r = idx % RB;
     sm.lt[idx] = r < R ? Lt[i + (int64_t)n * r] : 0.f;
   }
-  // A items of this thread: q = tid + 256 k -> row q % n, columns 8 (q / n) ..
-  constexpr int MAXIT = AF_NMAX * RB / 8 / AF_THREADS > 0 ? AF_NMAX * RB / 8 / AF_THREADS : 1;
-  const int items = n * (RB / 8);
-  float acc[MAXIT][8];
+  // A items: (row pair, column quad) = rows i and i + nh (nh = ceil(n / 2);
+  // the second only when < n), columns 4 g .. + 3; when there are fewer than
+  // the 256 threads, each item is split over cs_n ranges of the slab's c
+  // (summed once, in range order, at the end).  Work unit q = tid + 256 k:
+  // range q / items, item q % items -> i = item % nh, g = item / nh.
+  constexpr int MAXIT = AF_NMAX / 2 * RB / 4 / AF_THREADS > 0 ? AF_NMAX / 2 * RB / 4 / AF_THREADS : 1;
+  const int nh = (n + 1) / 2;
+  const int items1 = nh * (RB / 4);
+  constexpr int cs_n = CSN;
+  const int items = items1 * cs_n;
+  constexpr int c_len = AF_BC / cs_n;  // c values of one range (4 .. 32)
+  float acc[MAXIT][2][4];
 #pragma unroll
   for (int k = 0; k < MAXIT; ++k)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[k][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[k][0][j] = acc[k][1][j] = 0.f;
   // Slab loader: this thread's values (c, i) of the slab starting at c0,
   // zero outside.  The (c, i) pattern is the same for every slab, so it is
   // stepped without divisions: lo == 1 (element (c, i) at i + n c):
@@ -122,12 +134,14 @@ __global__ void __launch_bounds__(AF_THREADS) als_fused_kernel(const float* __re
     }
   };
   // A items of this thread (fixed for the whole kernel).
-  int it_i[MAXIT], it_g[MAXIT];
+  int it_i[MAXIT], it_g[MAXIT], it_c[MAXIT];
 #pragma unroll
   for (int k = 0; k < MAXIT; ++k) {
     const int q = tid + AF_THREADS * k;
-    it_i[k] = q % n;
-    it_g[k] = q / n;
+    const int item = q % items1;
+    it_i[k] = item % nh;
+    it_g[k] = item / nh;
+    it_c[k] = (q / items1) * c_len;
   }
   const int64_t ntile = cb < ce ? (ce - cb + AF_BC - 1) / AF_BC : 0;
   if (ntile > 0) fetch(cb);
@@ -151,64 +165,116 @@ __global__ void __launch_bounds__(AF_THREADS) als_fused_kernel(const float* __re
       const float4 y4 = *reinterpret_cast<const float4*>(&sm.ys[i * AF_PITCH + 4 * cq]);
       const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
       float lv[SG];
+      if constexpr (SG % 4 == 0) {
 #pragma unroll
-      for (int v = 0; v < SG; v += 2) {
-        const float2 l2 = *reinterpret_cast<const float2*>(&sm.lt[i * RB + rg * SG + v]);
-        lv[v] = l2.x;
-        lv[v + 1] = l2.y;
+        for (int v = 0; v < SG; v += 4) {
+          const float4 l4 = *reinterpret_cast<const float4*>(&sm.lt[i * RB + rg * SG + v]);
+          lv[v] = l4.x; lv[v + 1] = l4.y; lv[v + 2] = l4.z; lv[v + 3] = l4.w;
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < SG; v += 2) {
+          const float2 l2 = *reinterpret_cast<const float2*>(&sm.lt[i * RB + rg * SG + v]);
+          lv[v] = l2.x;
+          lv[v + 1] = l2.y;
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < SG; ++v) ps[u][v] = fmaf(yv[u], lv[v], ps[u][v]);
     }
+    // Row 8 u + cq for c = 4 cq + u, pitch RB + 4: the lanes of a quarter-warp
+    // (or half-warp for 8-byte stores) hit distinct banks.
+    constexpr int PP = AfSmem<RB>::PP;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 4; ++u) {
+      float* dst = &sm.part[(warp * AF_BC + 8 * u + cq) * PP + rg * SG];
+      if constexpr (SG % 4 == 0) {
 #pragma unroll
-      for (int v = 0; v < SG; ++v) sm.part[(warp * AF_BC + 4 * cq + u) * RB + rg * SG + v] = ps[u][v];
+        for (int v = 0; v < SG; v += 4)
+          *reinterpret_cast<float4*>(dst + v) = make_float4(ps[u][v], ps[u][v + 1], ps[u][v + 2], ps[u][v + 3]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < SG; v += 2) *reinterpret_cast<float2*>(dst + v) = make_float2(ps[u][v], ps[u][v + 1]);
+      }
+    }
     __syncthreads();
     for (int o = tid; o < AF_BC * RB; o += AF_THREADS) {
+      const int c = o / RB, r = o % RB;
+      const int prow = 8 * (c % 4) + c / 4;
       float s = 0.f;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) s += sm.part[w * AF_BC * RB + o];
+      for (int w = 0; w < 8; ++w) s += sm.part[(w * AF_BC + prow) * PP + r];
       sm.p[o] = s;
       if (write_rk) {
-        const int c = o / RB, r = o % RB;
         const int64_t cg = c0 + c;
         if (r < R && cg < ce) Rk[(cg % lo) + (int64_t)lo * (r + (int64_t)R * (cg / lo))] = s;
       }
     }
     __syncthreads();
-    // A phase: A(i, r) += sum_c Y(c, i) P(c, r).
+    // A phase: A(i, r) += sum_c Y(c, i) P(c, r), two rows per item, over the
+    // item's range of c (a compile-time length, so the loop unrolls).
 #pragma unroll
     for (int k = 0; k < MAXIT; ++k) {
       if (tid + AF_THREADS * k >= items) break;
-      const int i = it_i[k], g = it_g[k];
+      const int i0 = it_i[k], i1 = it_i[k] + nh, g = it_g[k], cb0 = it_c[k];
+      const bool two = i1 < n;
 #pragma unroll
-      for (int c4 = 0; c4 < AF_BC; c4 += 4) {
-        // row i's 4 values of c in one 128-bit load (lanes along i: 16-byte
-        // pieces 144 bytes apart, distinct within each quarter-warp)
-        const float4 y4 = *reinterpret_cast<const float4*>(&sm.ys[i * AF_PITCH + c4]);
-        const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+      for (int c4 = 0; c4 < c_len; c4 += 4) {
+        // rows i0 and i1: 4 values of c each in one 128-bit load (lanes along
+        // i: 16-byte pieces 144 bytes apart, distinct within a quarter-warp)
+        const float4 ya = *reinterpret_cast<const float4*>(&sm.ys[i0 * AF_PITCH + cb0 + c4]);
+        const float4 yb = two ? *reinterpret_cast<const float4*>(&sm.ys[i1 * AF_PITCH + cb0 + c4])
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float va[4] = {ya.x, ya.y, ya.z, ya.w}, vb[4] = {yb.x, yb.y, yb.z, yb.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float4 p0 = *reinterpret_cast<const float4*>(&sm.p[(c4 + u) * RB + 8 * g]);
-          const float4 p1 = *reinterpret_cast<const float4*>(&sm.p[(c4 + u) * RB + 8 * g + 4]);
-          acc[k][0] = fmaf(yv[u], p0.x, acc[k][0]); acc[k][1] = fmaf(yv[u], p0.y, acc[k][1]);
-          acc[k][2] = fmaf(yv[u], p0.z, acc[k][2]); acc[k][3] = fmaf(yv[u], p0.w, acc[k][3]);
-          acc[k][4] = fmaf(yv[u], p1.x, acc[k][4]); acc[k][5] = fmaf(yv[u], p1.y, acc[k][5]);
-          acc[k][6] = fmaf(yv[u], p1.z, acc[k][6]); acc[k][7] = fmaf(yv[u], p1.w, acc[k][7]);
+          const float4 p4 = *reinterpret_cast<const float4*>(&sm.p[(cb0 + c4 + u) * RB + 4 * g]);
+          acc[k][0][0] = fmaf(va[u], p4.x, acc[k][0][0]); acc[k][0][1] = fmaf(va[u], p4.y, acc[k][0][1]);
+          acc[k][0][2] = fmaf(va[u], p4.z, acc[k][0][2]); acc[k][0][3] = fmaf(va[u], p4.w, acc[k][0][3]);
+          acc[k][1][0] = fmaf(vb[u], p4.x, acc[k][1][0]); acc[k][1][1] = fmaf(vb[u], p4.y, acc[k][1][1]);
+          acc[k][1][2] = fmaf(vb[u], p4.z, acc[k][1][2]); acc[k][1][3] = fmaf(vb[u], p4.w, acc[k][1][3]);
         }
       }
     }
   }
-  // Partial A of this CTA: part_out[(blockIdx.x * n + i) * RB + r].
+  // Partial A of this CTA: part_out[(blockIdx.x * n + i) * RB + r], the c
+  // ranges of an item summed in range order through shared memory.
   float* out = part_out + (int64_t)blockIdx.x * n * RB;
+  if constexpr (CSN == 1) {
 #pragma unroll
-  for (int k = 0; k < MAXIT; ++k) {
-    if (tid + AF_THREADS * k >= items) break;
+    for (int k = 0; k < MAXIT; ++k) {
+      if (tid + AF_THREADS * k >= items) break;
+      const int i0 = it_i[k], i1 = it_i[k] + nh, g = it_g[k];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) out[(int64_t)it_i[k] * RB + 8 * it_g[k] + j] = acc[k][j];
+      for (int j = 0; j < 4; ++j) out[(int64_t)i0 * RB + 4 * g + j] = acc[k][0][j];
+      if (i1 < n) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[(int64_t)i1 * RB + 4 * g + j] = acc[k][1][j];
+      }
+    }
+  } else {
+    // cs_n * n * RB <= AF_THREADS * 8 floats: fits in the slab buffer
+    float* red = sm.ys;
+    __syncthreads();  // the last slab's readers are done
+#pragma unroll
+    for (int k = 0; k < MAXIT; ++k) {
+      if (tid + AF_THREADS * k >= items) break;
+      const int i0 = it_i[k], i1 = it_i[k] + nh, g = it_g[k], cs = it_c[k] / c_len;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) red[(cs * n + i0) * RB + 4 * g + j] = acc[k][0][j];
+      if (i1 < n) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[(cs * n + i1) * RB + 4 * g + j] = acc[k][1][j];
+      }
+    }
+    __syncthreads();
+    for (int o = tid; o < n * RB; o += AF_THREADS) {
+      float a = red[o];
+      for (int cs = 1; cs < cs_n; ++cs) a += red[cs * n * RB + o];
+      out[o] = a;
+    }
   }
 }
 
@@ -233,16 +299,30 @@ __global__ void als_fused_reduce_kernel(const float* __restrict__ part, int npar
 
 int af_rb(int64_t R) { return R <= 8 ? 8 : (R <= 16 ? 16 : 32); }
 
+template <int RB, int CSN>
+int launch_fused_cs(const float* y, const View& v, const float* Lt, int64_t R, float* part, int nparts,
+                    int64_t chunk, float* Rk, cudaStream_t st) {
+  static const bool attr = cudaFuncSetAttribute(als_fused_kernel<RB, CSN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)sizeof(AfSmem<RB>)) == cudaSuccess;
+  if (!attr) { set_error("als_fused: cannot set the kernel's shared-memory size"); return ATK_ECUDA; }
+  als_fused_kernel<RB, CSN><<<nparts, AF_THREADS, sizeof(AfSmem<RB>), st>>>(y, (int)v.lo, (int)v.n, v.J(), Lt,
+                                                                            (int)R, chunk, part, Rk, Rk ? 1 : 0);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+
+// Items (row pair, column quad) of the A phase; while they fill at most half
+// of the CTA's threads, each is split over twice as many ranges of c (<= 8).
 template <int RB>
 int launch_fused(const float* y, const View& v, const float* Lt, int64_t R, float* part, int nparts, int64_t chunk,
                  float* Rk, cudaStream_t st) {
-  static const bool attr = cudaFuncSetAttribute(als_fused_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)sizeof(AfSmem<RB>)) == cudaSuccess;
-  if (!attr) { set_error("als_fused: cannot set the kernel's shared-memory size"); return ATK_ECUDA; }
-  als_fused_kernel<RB><<<nparts, AF_THREADS, sizeof(AfSmem<RB>), st>>>(y, (int)v.lo, (int)v.n, v.J(), Lt, (int)R,
-                                                                       chunk, part, Rk, Rk ? 1 : 0);
-  ATK_LAUNCHED();
-  return ATK_OK;
+  const int64_t items1 = (v.n + 1) / 2 * (RB / 4);
+  int cs = 1;
+  while (cs < 8 && items1 * cs * 2 <= AF_THREADS) cs *= 2;
+  if (cs == 1) return launch_fused_cs<RB, 1>(y, v, Lt, R, part, nparts, chunk, Rk, st);
+  if (cs == 2) return launch_fused_cs<RB, 2>(y, v, Lt, R, part, nparts, chunk, Rk, st);
+  if (cs == 4) return launch_fused_cs<RB, 4>(y, v, Lt, R, part, nparts, chunk, Rk, st);
+  return launch_fused_cs<RB, 8>(y, v, Lt, R, part, nparts, chunk, Rk, st);
 }
 
 void fused_plan(const View& v, int& nparts, int64_t& chunk) {
