@@ -43,6 +43,11 @@ GRAM_VIEWS = [
     (3, 1, 11),        # n == 1
     (1, 17, 1),        # J == 1
     (33, 130, 5),      # n just over a tile, lo odd
+    (1, 48, 100003),   # small-I_n form: 6 x 6 blocks, ragged last split
+    (1, 64, 50000),    # small-I_n form: 8 x 8 blocks, two-warp groups
+    (1, 60, 12345),    # small-I_n form: columns 60..63 zero-filled
+    (1, 8, 70001),     # small-I_n form: one block
+    (1, 4, 999),       # small-I_n form: half a block, fewer rows than a CTA's share
 ]
 
 
