@@ -507,6 +507,12 @@ constexpr double RR_STALL = 0.5;
 constexpr double RR_FLOOR_OK = 1e-4;
 constexpr float RR_RESOLVE = 32.f * 1.1920929e-7f;
 constexpr double RR_CUT_RESOLVE = 64.0 * 1.1920928955078125e-7;
+// Relative gap at the cut above which a converged Ritz block takes the light
+// float64 finish.
+constexpr double RR_LIGHT_GAP = 1e-3;
+// ... and whose largest kept residual is below this fraction of the gap to the
+// guard block (a Davis-Kahan bound on the float32 vectors themselves).
+constexpr double RR_LIGHT_RES = 1e-4;
 
 // Block width m = R + p.  The default guard p = clamp(R / 2, 8, 16) suits a
 // spectrum with a gap at the cut; `wide` (the deflated levels of eig_top,
@@ -614,6 +620,7 @@ __global__ void ritz_summary_kernel(const double* __restrict__ res, const double
   out[3] = theta[m - 1];
   out[4] = *breakdown ? 1.0 : 0.0;
   out[5] = (double)K;
+  out[6] = theta[R < m ? R : m - 1];  // the first Ritz value past the cut
   *breakdown = 0;
 }
 
@@ -677,8 +684,9 @@ int cholqr3_f32(float* Y, float* T, float* Q, int64_t n, int m, RRBufs& b, cudaS
 // order, orthonormal to float32 accuracy) and returns ATK_OK; returns
 // ATK_ENOCONV to request the full Jacobi.
 int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double* Qblk, int* dev_status,
-           char* scratch, size_t scratch_bytes, cudaStream_t st, bool floor_ok, bool* at_floor) {
+           char* scratch, size_t scratch_bytes, cudaStream_t st, bool floor_ok, bool* at_floor, bool* tight) {
   *at_floor = false;
+  *tight = false;
   Arena ar{scratch, scratch_bytes, 0};
   RRBufs b;
   size_t nm = (size_t)n * m, mm = (size_t)m * m;
@@ -750,7 +758,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
       ATK_LAUNCHED();
       return ATK_OK;
     }));
-    double h[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double h[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     ATK_CUDA(cudaMemcpyAsync(h, b.summary, sizeof(h), cudaMemcpyDeviceToHost, st));
     ATK_CUDA(cudaStreamSynchronize(st));
     const double res = h[0], thK = h[2], thm = fmax(h[3], 0.0);
@@ -779,6 +787,12 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
     if (accept && predicted > RR_FLOOR_OK) *at_floor = true;
     if (stalls >= 3) return ATK_ENOCONV;  // three projections in a row without progress
     if (floor_here && power >= RR_MAX_POWER) *at_floor = true;
+    // Converged outright, every kept Ritz value resolvable and a clear gap at
+    // the cut: the light float64 finish suffices (refine_light).
+    // (A guard Ritz value at or below zero makes `predicted` vanish whatever
+    // the residual, so the residual itself must be small too.)
+    *tight = !floor_ok && predicted <= RR_TARGET && (int)h[5] == R && h[2] - h[6] >= RR_LIGHT_GAP * h[1] &&
+             h[3] > 0.0 && res <= RR_LIGHT_RES * (thK - thm);
     if (predicted <= RR_TARGET || accept || (floor_here && power >= RR_MAX_POWER)) {
       f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Y, Qblk, n * (int64_t)m);
       ATK_LAUNCHED();
@@ -1025,6 +1039,67 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   return ATK_OK;
 }
 
+__global__ void diag_fill_kernel(const double* __restrict__ d, int64_t k, double* __restrict__ B) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < k * k) B[o] = (o % k == o / k) ? d[o % k] : 0.0;
+}
+
+// Light float64 finish of a Ritz block that the float32 iteration has
+// converged outright with a clear gap at the cut (rr_top's `tight`: its
+// predicted error after one float64 subspace step is below RR_TARGET and its
+// residuals are small).  It is the full refinement without the Rayleigh-Ritz
+// rotations:
+//  1. one float64 subspace step, Qb <- normalise(S Qb), then the
+//     orthonormalisation in Gram-Schmidt order (a CholeskyQR pass with a
+//     float32 factor, then two quadratic steps): the float32 block is not
+//     orthonormal beyond float32 level, and its basis may be far from it when
+//     S spans many decades;
+//  2. the columns' float64 Rayleigh quotients q^T S q rank them and give the
+//     kept eigenvalues and the discarded energy;
+//  3. the top R columns, the sign rule.
+// Without the rotations a column inside a cluster of kept eigenvalues is
+// accurate to the float32 level of the iteration, the level the float32 Gram
+// already sets; the kept subspace is accurate to float64 level.
+int refine_light(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, double* U64, double* lambda_out,
+                 double* discarded_out, double* lam_sorted, char* scratch, size_t scratch_bytes, cudaStream_t st) {
+  Arena ar{scratch, scratch_bytes, 0};
+  double* Z = (double*)ar.take(sizeof(double) * n * k);
+  double* B = (double*)ar.take(sizeof(double) * k * k);
+  double* T = (double*)ar.take(sizeof(double) * k * k);
+  float* Tf = (float*)ar.take(sizeof(float) * k * k);
+  double* norms = (double*)ar.take(sizeof(double) * (2 * k + 8));
+  int* order = (int*)ar.take(sizeof(int) * k);
+  double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
+  if (!pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
+  // 1. subspace step and orthonormalisation (as in refine_f64)
+  ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
+  colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
+  ATK_LAUNCHED();
+  normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k, 1e-5, 0.9,
+                                                                        Qb);
+  ATK_LAUNCHED();
+  ATK_TRY(gemm_tn_f64(Qb, Qb, n, k, B, st));
+  ATK_TRY(cholinv_f32(B, (int)k, 0.f, Tf, nullptr, st));
+  ATK_TRY(f32_to_f64(Tf, T, k * k, st));
+  ATK_TRY(gemm_f64(Qb, T, n, k, k, Z, st));
+  ATK_CUDA(cudaMemcpyAsync(Qb, Z, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
+  for (int it = 0; it < 2; ++it) ATK_TRY(gs_step_f64(Qb, n, k, pol, st));
+  // 2. Rayleigh quotients of the orthonormal columns
+  ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
+  colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
+  ATK_LAUNCHED();
+  diag_fill_kernel<<<(unsigned)ceil_div(k * k, 256), 256, 0, st>>>(norms + k, k, B);
+  ATK_LAUNCHED();
+  // 3. kept vectors
+  order_diag_kernel<<<1, 256, 0, st>>>(B, (int)k, (int)R, S, n, order, lambda_out, discarded_out, lam_sorted);
+  ATK_LAUNCHED();
+  gather_cols_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(Qb, order, n, R, U64);
+  ATK_LAUNCHED();
+  sign_fix_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(U64, n, R);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+
 // Scratch of one level (eig_level): the Ritz block, then the largest of the
 // solvers' and the refinement's needs.
 static size_t level_scratch_bytes(int64_t n, int arith) {
@@ -1134,6 +1209,7 @@ struct Level {
   char* rest;
   size_t rest_bytes;
   bool at_floor;  // the subspace iteration stopped at its float32 floor
+  bool tight;     // converged with a clear gap at the cut: the light finish ran
 };
 static int eig_level(const double* S, int64_t n, int64_t R, int arith, int method, int max_sweeps, bool wide,
                      double* U64, double* lambda_out, double* discarded_out, double* lam_sorted, int* dev_status,
@@ -1147,10 +1223,10 @@ static int eig_level(const double* S, int64_t n, int64_t R, int arith, int metho
   if (!Qb) { set_error("eig: scratch too small"); return ATK_EINVAL; }
   char* rest = scratch + ar.used;
   const size_t rest_bytes = scratch_bytes - ar.used;
-  *lv = Level{Qb, k, rest, rest_bytes, false};
+  *lv = Level{Qb, k, rest, rest_bytes, false, false};
   int s = ATK_ENOCONV;
   if (rr) {
-    s = rr_top(S, n, R, m, max_sweeps, Qb, dev_status, rest, rest_bytes, st, wide, &lv->at_floor);
+    s = rr_top(S, n, R, m, max_sweeps, Qb, dev_status, rest, rest_bytes, st, wide, &lv->at_floor, &lv->tight);
     if (s != ATK_OK && s != ATK_ENOCONV) return s;
     if (s == ATK_OK && lambda_out && n > R) {
       // Only the kept eigenvalues exist on this path; the tail is marked NaN.
@@ -1170,7 +1246,15 @@ static int eig_level(const double* S, int64_t n, int64_t R, int arith, int metho
     if (s != ATK_OK) return s;
   }
   // The refinement: no host synchronisation inside, so one cached graph per
-  // (buffers, sizes).
+  // (buffers, sizes, form).
+  if (s == ATK_OK && rr && lv->tight) {
+    const GraphKey lkey{{S, Qb, U64, lambda_out, discarded_out, lam_sorted, rest, (const void*)5},
+                        {n, k, R, (int64_t)rest_bytes}};
+    return run_graph(lkey, st, [&](cudaStream_t s2) -> int {
+      return refine_light(S, n, Qb, k, R, U64, lambda_out, discarded_out, lam_sorted, rest, rest_bytes, s2);
+    });
+  }
+  lv->tight = false;
   const GraphKey key{{S, Qb, U64, lambda_out, discarded_out, lam_sorted, rest, nullptr},
                      {n, k, R, (int64_t)rest_bytes}};
   return run_graph(key, st, [&](cudaStream_t s2) -> int {
