@@ -792,7 +792,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
     // (A guard Ritz value at or below zero makes `predicted` vanish whatever
     // the residual, so the residual itself must be small too.)
     *tight = !floor_ok && predicted <= RR_TARGET && (int)h[5] == R && h[2] - h[6] >= RR_LIGHT_GAP * h[1] &&
-             h[3] > 0.0 && res <= RR_LIGHT_RES * (thK - thm);
+             res <= RR_LIGHT_RES * (thK - thm);
     if (predicted <= RR_TARGET || accept || (floor_here && power >= RR_MAX_POWER)) {
       f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Y, Qblk, n * (int64_t)m);
       ATK_LAUNCHED();
