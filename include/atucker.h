@@ -179,8 +179,8 @@ typedef struct atucker_plan_s* atucker_plan_t;
  *                    atucker_sthosvd times the candidates on that input (an
  *                    exhaustive search, Sec. IV): with no selector loaded,
  *                    every class that can run the mode; with the network,
- *                    its two best classes when their predicted log2 times
- *                    differ by less than 0.15 (about 11 %).  That call runs
+ *                    its best class and up to two more whose predicted log2
+ *                    times are within 0.3 of it (about 23 %).  That call runs
  *                    each candidate twice (warm-up, then timed with CUDA
  *                    events), keeps each mode's fastest, and caches the choice
  *                    for the process, keyed by shape, ranks, order and the

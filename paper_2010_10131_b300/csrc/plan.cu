@@ -89,9 +89,11 @@ static void als_initial_guess(uint64_t seed, int mode, int64_t I, int64_t R, dou
 
 __global__ void sub_kernel(const double* a, const double* b, double* out) { *out = *a - *b; }
 
-// Two predicted classes closer than this (log2 of the time ratio, about 11 %)
-// are settled by timing them at the plan's first run.
-constexpr float SELECTOR_MARGIN = 0.15f;
+// Classes predicted within this of the best (log2 of the time ratio, about
+// 23 %), at most SELECTOR_SEARCH_MAX of them, are settled by timing them at
+// the plan's first run.
+constexpr float SELECTOR_MARGIN = 0.3f;
+constexpr int SELECTOR_SEARCH_MAX = 3;
 
 // Below this rank the float32 TTM reads Y at HBM speed, and the tensor-core
 // TTM of the precision forms is no faster (measured at I_n = 128, R = 16).
@@ -392,19 +394,23 @@ int atucker_plan_create(atucker_plan_t* plan, int order, const int64_t* dims, co
       if (solver_per_mode[k] != ATK_AUTO) continue;
       const double lg = feat[k * ATK_SELECTOR_FEATURES];  // log2 I_n
       if (have) {
-        // The prediction, and the runner-up when the two are too close to call.
+        // The prediction, and up to two runners-up whose predicted times are
+        // too close to it to call.
         cls[k] = pick[k];
-        int second = -1;
-        for (int c = 0; c < ATK_NUM_CLASSES; ++c)
-          if (c != pick[k] && selector_class_fits(c, lg) &&
-              (second < 0 || scores[k * ATK_NUM_CLASSES + c] < scores[k * ATK_NUM_CLASSES + second]))
-            second = c;
-        if (second >= 0 &&
-            scores[k * ATK_NUM_CLASSES + second] - scores[k * ATK_NUM_CLASSES + pick[k]] < SELECTOR_MARGIN) {
-          cand[k][0] = pick[k];
-          cand[k][1] = second;
-          ncand[k] = 2;
+        cand[k][0] = pick[k];
+        ncand[k] = 1;
+        const float* sk = scores + k * ATK_NUM_CLASSES;
+        for (int extra = 0; extra < SELECTOR_SEARCH_MAX - 1; ++extra) {
+          int next = -1;
+          for (int c = 0; c < ATK_NUM_CLASSES; ++c) {
+            bool taken = false;
+            for (int j = 0; j < ncand[k]; ++j) taken = taken || cand[k][j] == c;
+            if (!taken && selector_class_fits(c, lg) && (next < 0 || sk[c] < sk[next])) next = c;
+          }
+          if (next < 0 || sk[next] - sk[pick[k]] >= SELECTOR_MARGIN) break;
+          cand[k][ncand[k]++] = next;
         }
+        if (ncand[k] == 1) ncand[k] = 0;  // a clear call: no search
       } else {
         // No selector: every class that can run the mode is timed.
         for (int c = 0; c < ATK_NUM_CLASSES; ++c)

@@ -248,9 +248,45 @@ def regret(T, chosen):
     return float(tc[ok].sum() / best[ok].sum() - 1.0), ok
 
 
+# The product path's policy (atucker_plan_create): the network's best class
+# and up to SEARCH_MAX - 1 more predicted within SEARCH_MARGIN log2 units of
+# it are timed at the plan's first run, which keeps the fastest.
+SEARCH_MARGIN = 0.3
+SEARCH_MAX = 3
+
+
+def class_fits(k: int, lg: float) -> bool:
+    """Whether class k can run a mode with log2 I_n = lg (the full Jacobi needs I_n <= 1024)."""
+    if k == NUM_CLASSES - 1:
+        return True
+    return lg <= (10.0 if k in (2, 3) else 15.0) + 1e-9
+
+
+def with_search(F, T, cls, scores, margin: float = SEARCH_MARGIN, top: int = SEARCH_MAX):
+    """Classes the product path ends with: the prediction, or, where other
+    fitting classes are predicted within `margin` of it (at most `top`
+    candidates in all), whichever candidate measured fastest (the timed
+    search).  Returns (classes, number of modes searched)."""
+    out = np.array(cls, copy=True)
+    searched = 0
+    for i in range(len(F)):
+        if not np.all(np.isfinite(scores[i])):
+            continue
+        pick = int(cls[i])
+        rest = sorted((k for k in range(NUM_CLASSES) if k != pick and class_fits(k, float(F[i, 0]))),
+                      key=lambda k: scores[i, k])
+        cands = [pick] + [k for k in rest[:top - 1] if scores[i, k] - scores[i, pick] < margin]
+        if len(cands) < 2:
+            continue
+        searched += 1
+        tt = [T[i, k] if np.isfinite(T[i, k]) else np.inf for k in cands]
+        out[i] = cands[int(np.argmin(tt))]
+    return out, searched
+
+
 def evaluate(F, T, shapes_rows=None):
     """Regret of the loaded selector on (F, T), and its gain over fixed classes."""
-    cls, _ = predict(F)
+    cls, scores = predict(F)
     r, ok = regret(T, cls)
     best = np.nanmin(T, axis=1)
     out = {"rows": int(ok.sum()), "regret": r,
@@ -267,6 +303,14 @@ def evaluate(F, T, shapes_rows=None):
             rr, _ = regret(T[a:b], cls[a:b])
             per_shape.append(rr)
         out["max_shape_regret"] = float(np.max(per_shape))
+    if np.any(scores != 0):
+        # the product path: the network, with the timed search on close calls;
+        # and, for scale, the search over the network's top three always
+        for key, margin in (("with_timed_search", SEARCH_MARGIN), ("top3_always_searched", np.inf)):
+            cs, searched = with_search(F, T, cls, scores, margin=margin)
+            rs, _ = regret(T, cs)
+            out[key] = {"regret": rs, "modes_searched": searched,
+                        "gain_vs_fixed_EIG": float(T[:, 0][ok].sum() / T[np.arange(len(T)), cs][ok].sum())}
     return out
 
 

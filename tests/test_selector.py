@@ -98,6 +98,35 @@ def test_auto_plan_uses_the_selector():
 
 
 @pytest.mark.gpu
+def test_auto_times_the_networks_close_calls():
+    """A network that scores EIG and EIG-small-tile equal (and the rest far
+    worse) leaves those two as candidates: the first run keeps one of them,
+    and the result is bit for bit that of a plan built with the kept classes."""
+    torch = _gpu()
+    from paper_2010_10131_b300 import selector
+    mean, scale, p = _packed(6)
+    p = p.copy()
+    p[-K:] = [-5.0, -5.0, 5.0, 5.0, 5.0]
+    p[-K - K * H:-K] = 0.0
+    selector.install(selector.pack(mean, scale, p))
+    try:
+        dims, ranks = [160, 40, 36], [8, 6, 5]
+        x = torch.randn(dims[0] * dims[1] * dims[2], generator=torch.Generator().manual_seed(4)).cuda()
+        p1 = atk.Plan(dims, ranks, solver=[atk.AUTO] * 3)
+        c1, f1 = p1.run(x)
+        chosen = p1.classes
+        assert all(c in (atk.CLASS_EIG, atk.CLASS_EIG_SMALL) for c in chosen)
+        p2 = atk.Plan(dims, ranks, classes=chosen)
+        c2, f2 = p2.run(x)
+        torch.cuda.synchronize()
+        assert torch.equal(c1, c2) and torch.equal(f1, f2)
+        p1.close()
+        p2.close()
+    finally:
+        atk.lib().atucker_selector_clear()
+
+
+@pytest.mark.gpu
 def test_auto_without_selector_settles_classes_by_timing():
     """No selector loaded: the first run times every class that fits each AUTO
     mode and keeps the fastest; a second plan of the same key takes the cached
