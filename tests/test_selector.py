@@ -97,6 +97,27 @@ def test_auto_plan_uses_the_selector():
     plan.close()
 
 
+def test_search_policy_keeps_the_fastest_close_candidate():
+    """Host logic of the product path's policy (with_search): candidates are
+    the prediction plus up to two fitting classes predicted within the margin;
+    the measured fastest of them wins; clear calls and unfit classes are left
+    alone."""
+    from paper_2010_10131_b300 import selector
+    lg = np.array([[6.0], [6.0], [12.0], [6.0]])  # log2 I_n: 64, 64, 4096, 64
+    F = np.concatenate([lg, np.zeros((4, IN - 1))], axis=1)
+    scores = np.array([[0.0, 0.1, 0.2, 0.9, 0.05],   # EIG, ALS, EIG-small close: timed
+                       [0.0, 2.0, 2.0, 2.0, 2.0],    # clear call
+                       [0.0, 0.1, 0.05, 0.05, 3.0],  # I_n = 4096: Jacobi classes cannot run
+                       [0.0, 0.1, 0.2, 0.25, 0.29]], dtype=np.float32)  # four close: at most three timed
+    T = np.array([[5.0, 4.0, 1.0, 9.0, 3.0],
+                  [5.0, 1.0, 1.0, 1.0, 1.0],
+                  [5.0, 4.0, 1.0, 1.0, 9.0],
+                  [5.0, 4.0, 3.0, 1.0, 0.5]])
+    cls = np.zeros(4, dtype=int)
+    out, searched = selector.with_search(F, T, cls, scores, margin=0.3, top=3)
+    assert list(out) == [4, 0, 1, 2] and searched == 3
+
+
 @pytest.mark.gpu
 def test_auto_times_the_networks_close_calls():
     """A network that scores EIG and EIG-small-tile equal (and the rest far
