@@ -1039,27 +1039,35 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   return ATK_OK;
 }
 
-__global__ void diag_fill_kernel(const double* __restrict__ d, int64_t k, double* __restrict__ B) {
+// B = diag(d_j / q_j^2): the Rayleigh quotients u^T S u / u^T u from
+// d_j = u_j^T S u_j and q_j = ||u_j||.
+__global__ void rq_diag_kernel(const double* __restrict__ d, const double* __restrict__ q, int64_t k,
+                               double* __restrict__ B) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o < k * k) B[o] = (o % k == o / k) ? d[o % k] : 0.0;
+  if (o >= k * k) return;
+  const int64_t i = o % k;
+  B[o] = (i == o / k) ? d[i] / (q[i] * q[i]) : 0.0;
 }
 
 // Light float64 finish of a Ritz block that the float32 iteration has
 // converged outright with a clear gap at the cut (rr_top's `tight`: its
 // predicted error after one float64 subspace step is below RR_TARGET and its
-// residuals are small).  It is the full refinement without the Rayleigh-Ritz
-// rotations:
-//  1. one float64 subspace step, Qb <- normalise(S Qb), then the
-//     orthonormalisation in Gram-Schmidt order (a CholeskyQR pass with a
-//     float32 factor, then two quadratic steps): the float32 block is not
-//     orthonormal beyond float32 level, and its basis may be far from it when
-//     S spans many decades;
-//  2. the columns' float64 Rayleigh quotients q^T S q rank them and give the
-//     kept eigenvalues and the discarded energy;
-//  3. the top R columns, the sign rule.
-// Without the rotations a column inside a cluster of kept eigenvalues is
-// accurate to the float32 level of the iteration, the level the float32 Gram
-// already sets; the kept subspace is accurate to float64 level.
+// kept residuals are below RR_LIGHT_RES of the gap to the guard block, so
+// each float32 vector is within about 1e-4 of the leading space).
+//  1. Z = S Qb in float64.  q_j^T z_j / q_j^T q_j are the columns' Rayleigh
+//     quotients, exact to second order in the vectors' error (below 1e-8
+//     relative): they rank the columns and give the kept eigenvalues and the
+//     discarded energy.
+//  2. The subspace step Qb <- normalise(Z), then the orthonormalisation in
+//     Gram-Schmidt order: a CholeskyQR pass with a float32 factor (the float32
+//     block is not orthonormal beyond float32 level, and may be far from it
+//     when S spans many decades), then one quadratic step, which takes the
+//     float32-level error of that pass to float64 level.
+//  3. The top R columns, the sign rule.
+// Without the Rayleigh-Ritz rotations a column inside a cluster of kept
+// eigenvalues is accurate to the float32 level of the iteration, the level
+// the float32 Gram already sets; the kept subspace is accurate to float64
+// level.
 int refine_light(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, double* U64, double* lambda_out,
                  double* discarded_out, double* lam_sorted, char* scratch, size_t scratch_bytes, cudaStream_t st) {
   Arena ar{scratch, scratch_bytes, 0};
@@ -1068,28 +1076,28 @@ int refine_light(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, d
   double* T = (double*)ar.take(sizeof(double) * k * k);
   float* Tf = (float*)ar.take(sizeof(float) * k * k);
   double* norms = (double*)ar.take(sizeof(double) * (2 * k + 8));
+  double* qn = (double*)ar.take(sizeof(double) * (k + 8));
   int* order = (int*)ar.take(sizeof(int) * k);
   double* pol = (double*)ar.take(smallla_scratch_bytes(std::max(n, k), k));
   if (!pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
-  // 1. subspace step and orthonormalisation (as in refine_f64)
+  // 1. Z = S Qb and the Rayleigh quotients of the float32 columns
   ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
   colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
   ATK_LAUNCHED();
+  colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Qb, nullptr, n, k, qn, nullptr);
+  ATK_LAUNCHED();
+  rq_diag_kernel<<<(unsigned)ceil_div(k * k, 256), 256, 0, st>>>(norms + k, qn, k, B);
+  ATK_LAUNCHED();
+  // 2. subspace step and orthonormalisation in Gram-Schmidt order
   normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k, 1e-5, 0.9,
                                                                         Qb);
   ATK_LAUNCHED();
-  ATK_TRY(gemm_tn_f64(Qb, Qb, n, k, B, st));
-  ATK_TRY(cholinv_f32(B, (int)k, 0.f, Tf, nullptr, st));
+  ATK_TRY(gemm_tn_f64(Qb, Qb, n, k, T, st));
+  ATK_TRY(cholinv_f32(T, (int)k, 0.f, Tf, nullptr, st));
   ATK_TRY(f32_to_f64(Tf, T, k * k, st));
   ATK_TRY(gemm_f64(Qb, T, n, k, k, Z, st));
   ATK_CUDA(cudaMemcpyAsync(Qb, Z, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
-  for (int it = 0; it < 2; ++it) ATK_TRY(gs_step_f64(Qb, n, k, pol, st));
-  // 2. Rayleigh quotients of the orthonormal columns
-  ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
-  colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
-  ATK_LAUNCHED();
-  diag_fill_kernel<<<(unsigned)ceil_div(k * k, 256), 256, 0, st>>>(norms + k, k, B);
-  ATK_LAUNCHED();
+  ATK_TRY(gs_step_f64(Qb, n, k, pol, st));
   // 3. kept vectors
   order_diag_kernel<<<1, 256, 0, st>>>(B, (int)k, (int)R, S, n, order, lambda_out, discarded_out, lam_sorted);
   ATK_LAUNCHED();
