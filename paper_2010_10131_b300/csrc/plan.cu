@@ -174,8 +174,8 @@ struct atucker_plan_s {
   cudaStream_t st = nullptr;
   int eig_arith = ATK_EIG_ROT_FP32, eig_method = ATK_EIG_AUTO, sync = 0, max_sweeps = 40, gram_refine = 1;
   long long wait_polls = 0;  // ATK_OPT_WAIT_LIMIT (0: default)
-  int explicit_unfold = 0;
-  int fuse_tg = 0;  // ATK_OPT_FUSE_TTM_GRAM   // ATK_OPT_EXPLICIT_UNFOLD
+  int explicit_unfold = 0;  // ATK_OPT_EXPLICIT_UNFOLD
+  int fuse_tg = 0;          // ATK_OPT_FUSE_TTM_GRAM
   // Exhaustive timed search (AUTO modes without a confident prediction):
   // candidate classes per mode, timed at the first run.
   int ncand[8] = {0, 0, 0, 0, 0, 0, 0, 0};
