@@ -214,15 +214,14 @@ int gemm_tn_f64(const double* A, const double* B, int64_t n, int64_t R, double* 
 
 // One CTA: Cholesky G = C C^T (C lower) and Cinv = C^{-1} (lower), R <= 128,
 // float64 (Golub & Van Loan, Matrix Computations, Alg. 4.2.2 for the
-// factor, row-oriented forward substitution for the inverse).  Both live in
-// one shared-memory R x (R + 1) array: C on and below the diagonal, the
-// strictly lower part of Cinv transposed into the upper part, the diagonals
-// in two vectors.  The factor is right-looking, three barriers per column
-// (the pivot's root and reciprocal by one thread, the column scaled, the
-// rank-1 update of the trailing triangle); row i of the inverse, X_ik = -(sum_{k<=t<i} C_it
-// X_tk) / C_ii, takes one barrier per row, its sums split over lane groups of
-// four and combined by shuffles.  A non-positive pivot sets DEV_CHOL and
-// leaves identity factors, so later kernels stay finite.
+// factor; forward substitution on the identity for the inverse, both
+// right-looking and in the same loop).  Both live in one shared-memory
+// R x (R + 1) array: C on and below the diagonal, the strictly lower part of
+// Cinv transposed into the upper part, the diagonals in two vectors.  One
+// barrier per column (the loop's comment gives the steps): the float64 pipe,
+// not barriers, then bounds the kernel (about R^3 / 3 float64 FMAs).  A
+// non-positive pivot sets DEV_CHOL and leaves identity factors, so later
+// kernels stay finite.
 constexpr int CI_THREADS = 512;
 size_t chol_inv_smem(int R) { return sizeof(double) * ((size_t)R * (R + 1) + 2 * (size_t)R) + 16; }
 
@@ -241,35 +240,64 @@ __global__ void __launch_bounds__(CI_THREADS) chol_inv_kernel(const double* __re
     const int i = idx % R, j = idx / R;
     if (i >= j) M[i * ld + j] = G[i + (int64_t)R * j];
   }
+  __shared__ double pinv[2];
+  // One barrier per column j.  Pivot d_j = sqrt(M_jj) is known from the step
+  // before; the step then, with L_ij = M_ij / d_j formed on the fly:
+  //  - applies the rank-1 update of the Cholesky factorisation to the
+  //    trailing lower triangle, M_ik -= L_ij L_kj (i >= k > j);
+  //  - eliminates column j from the rows below of the inverse, by forward
+  //    substitution run right-looking on the identity: with Xu the rows not
+  //    yet divided by their pivot (Xu_jj = 1), X_j = Xu_j / d_j and
+  //    Xu_ic -= L_ij X_jc for i > j, c <= j;
+  //  - the thread that owns (j + 1, j + 1) finishes that entry first and takes
+  //    the next pivot (square root and reciprocal on one thread: float64
+  //    division and square root are long instruction sequences on B300's
+  //    float64 pipe).
+  // After the barrier, column j of L and row j of X are divided by d_j in
+  // place (nothing in step j + 1 reads them).  X is stored transposed in the
+  // strict upper triangle of M (X_ic at M[c][i]), its diagonal 1 / d_j in dX.
+  auto take_pivot = [&](int j, double piv) {
+    if (!(piv > 0.0)) {
+      bad = 1;
+      piv = 1.0;
+    }
+    const double d = sqrt(piv);
+    dC[j] = d;
+    dX[j] = 1.0 / d;
+    pinv[j & 1] = dX[j];
+  };
+  if (tid == 0) take_pivot(0, M[0]);
   __syncthreads();
-  __shared__ double pinv;
   for (int j = 0; j < R; ++j) {
-    // One thread takes the square root and reciprocal (float64 division and
-    // square root are long instruction sequences on the float64 pipe, which
-    // B300 issues at about two per clock per SM: every thread recomputing
-    // them cost more than the whole factorisation).
-    if (tid == 0) {
-      double piv = M[j * ld + j];
-      if (!(piv > 0.0)) {
-        bad = 1;
-        piv = 1.0;
-      }
-      const double d = sqrt(piv);
-      dC[j] = d;
-      dX[j] = 1.0 / d;
-      pinv = dX[j];
-    }
-    __syncthreads();
-    const double inv = pinv;
-    for (int i = j + 1 + tid; i < R; i += CI_THREADS) M[i * ld + j] *= inv;
-    __syncthreads();
+    const double inv = pinv[j & 1];
     const int rem = R - j - 1;
-    for (int idx = tid; idx < rem * rem; idx += CI_THREADS) {
-      const int i = j + 1 + idx / rem, k = j + 1 + idx % rem;
-      if (k <= i) M[i * ld + k] -= M[i * ld + j] * M[k * ld + j];
+    const int tri = rem * (rem + 1) / 2;     // trailing Cholesky entries
+    const int total = tri + rem * (j + 1);   // and inverse entries
+    // work item 0 is (j + 1, j + 1): thread 0 takes the next pivot
+    for (int idx = tid; idx < total; idx += CI_THREADS) {
+      if (idx < tri) {
+        // idx -> (a, b), 0 <= b <= a < rem, row by row
+        int a = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+        while (a * (a + 1) / 2 > idx) --a;
+        while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+        const int b = idx - a * (a + 1) / 2;
+        const int i = j + 1 + a, k = j + 1 + b;
+        const double v = M[i * ld + k] - (M[i * ld + j] * inv) * (M[k * ld + j] * inv);
+        M[i * ld + k] = v;
+        if (idx == 0) take_pivot(j + 1, v);  // (j + 1, j + 1) is final now
+      } else {
+        const int q = idx - tri;
+        const int i = j + 1 + q / (j + 1), c = q % (j + 1);
+        const double xj = c == j ? inv : M[c * ld + j] * inv;  // X_jc = Xu_jc / d_j (Xu_jj = 1)
+        const double lij = M[i * ld + j] * inv;
+        M[c * ld + i] = (c == j ? 0.0 : M[c * ld + i]) - lij * xj;
+      }
     }
     __syncthreads();
+    for (int i = j + 1 + tid; i < R; i += CI_THREADS) M[i * ld + j] *= inv;  // L column j
+    for (int c = tid; c < j; c += CI_THREADS) M[c * ld + j] *= inv;          // X row j
   }
+  __syncthreads();
   if (bad) {
     for (int idx = tid; idx < R * R; idx += CI_THREADS) {
       const double e = (idx % R == idx / R) ? 1.0 : 0.0;
@@ -278,21 +306,6 @@ __global__ void __launch_bounds__(CI_THREADS) chol_inv_kernel(const double* __re
     }
     if (tid == 0) atomicOr(status, DEV_CHOL);
     return;
-  }
-  // Inverse, row by row: lane group g (4 lanes) takes column k = g.
-  const int grp = tid / 4, sub = tid % 4;
-  for (int i = 0; i < R; ++i) {
-    const int k = grp;
-    double acc = 0.0;
-    if (k < i) {
-      if (sub == 0) acc = M[i * ld + k] * dX[k];  // t = k term: C_ik X_kk
-      for (int t = k + 1 + sub; t < i; t += 4) acc += M[i * ld + t] * M[k * ld + t];  // X_tk sits at M[k][t]
-    }
-    // every lane takes part in the shuffles (the groups of a warp diverge above)
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (sub == 0 && k < i) M[k * ld + i] = -acc * dX[i];
-    __syncthreads();
   }
   for (int idx = tid; idx < R * R; idx += CI_THREADS) {
     const int i = idx % R, j = idx / R;  // column-major outputs
