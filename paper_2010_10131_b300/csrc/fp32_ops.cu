@@ -350,14 +350,61 @@ __device__ __forceinline__ FFSum ff_sum_splits(const float* __restrict__ p, int6
 // while one is consumed, which covers the HBM latency.  The tile index runs
 // fastest in the grid, so the T (T + 1) / 2 tiles of a split run side by side
 // and each input row comes from HBM about once (its other uses hit L2).
-// Diagonal tiles copy one operand and skip the lower-left quadrant of their
-// accumulators.  Out-of-range rows (c >= end of the split, i >= I_n) are
-// zero-filled.
+// Diagonal tiles copy one operand and compute only the 4 x 4 blocks that meet
+// the upper triangle (gram_async_diag); the reduction reads nothing else of
+// them.  Out-of-range rows (c >= end of the split, i >= I_n) are zero-filled.
 constexpr int GA_TK = TK;
 constexpr int GA_NS = 4;
 constexpr int GA_LD = 128 + PAD;
 constexpr int GA_STAGE = 2 * GA_TK * GA_LD;  // floats per stage: A and B tiles
 constexpr int GA_SMEM = GA_NS * GA_STAGE * (int)sizeof(float);
+
+// A diagonal 128 x 128 tile as 4 x 4 blocks (bi, bj), bi, bj < 32: the
+// blocks at or above the diagonal are the 256 of the top-right quadrant and
+// the 136 + 136 upper ones of the two diagonal 64 x 64 quadrants.  Thread t
+// takes top-right block (t / 16, t % 16) and one block of the diagonal
+// quadrants: those 272 are 16 "pairs" of 17 (quadrant row p with row 15 - p,
+// p < 8, which hold 16 - p and p + 1 blocks), thread t block t % 16 of pair
+// t / 16, and the lanes l < 16 of one warp (it rotates with the CTA, to
+// spread the extra work over the SM sub-partitions) the 17th block of pair l.
+// Every warp's fragment loads touch at most 16 distinct 16-byte chunks of a
+// stage row, as in the full-tile layout, and a thread holds 8 or 12 packed
+// accumulators: 7 of 8 warps issue 16 packed FMAs per k instead of 24.
+struct DiagBlocks {
+  int ra[3], cb[3];  // first row and column of each block in the tile
+  bool extra;        // this warp takes the 17th blocks
+  __device__ explicit DiagBlocks(int tid, unsigned cta) {
+    const int warp = tid >> 5, lane = tid & 31;
+    ra[0] = 4 * (tid >> 4);
+    cb[0] = 64 + 4 * (tid & 15);
+    {
+      const int P = tid >> 4, q = tid & 15, p = P & 7, off = P < 8 ? 0 : 64;
+      const bool first = q < 16 - p;
+      ra[1] = off + 4 * (first ? p : 15 - p);
+      cb[1] = off + 4 * (first ? p + q : q - 1);
+    }
+    {
+      const int P = lane & 15, off = P < 8 ? 0 : 64;
+      ra[2] = off + 4 * (15 - (P & 7));
+      cb[2] = off + 60;
+    }
+    extra = warp == (int)(cta & 7u);
+  }
+};
+
+// One 4 x 4 block's outer product for row k of a stage.
+__device__ __forceinline__ void diag_block_step(const float* s, int ra, int cb, unsigned long long (&d)[4][2]) {
+  const float4 a = *reinterpret_cast<const float4*>(s + ra);
+  const float4 b = *reinterpret_cast<const float4*>(s + cb);
+  const unsigned long long b0 = pack2(b.x, b.y), b1 = pack2(b.z, b.w);
+  const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const unsigned long long a2 = pack2(av[u], av[u]);
+    fma2(d[u][0], a2, b0);
+    fma2(d[u][1], a2, b1);
+  }
+}
 
 __global__ void __launch_bounds__(NT, 2)
 gram_async_kernel(const float* __restrict__ y, int n, int64_t J, int T, int64_t kc, float* __restrict__ part) {
@@ -392,25 +439,61 @@ gram_async_kernel(const float* __restrict__ y, int n, int64_t J, int T, int64_t 
       }
     }
   };
-  Block<128, 128, 8, 8> blk;
-  blk.init();
+  // The ring: GA_NS - 1 stages in flight, stage t consumed by `consume`.
+  auto run = [&](auto&& consume) {
 #pragma unroll
-  for (int s = 0; s < GA_NS - 1; ++s) {
-    if (s < ntile) load_stage(s, s);
-    cp_async_commit();
-  }
-  for (int t = 0; t < ntile; ++t) {
-    cp_async_wait<GA_NS - 2>();  // this thread's copies of stage t have landed
-    __syncthreads();             // everyone's have, and stage t - 1's slot is free
-    const int tn = t + GA_NS - 1;
-    if (tn < ntile) load_stage(tn, tn % GA_NS);
-    cp_async_commit();
-    const float* sa = gas + (t % GA_NS) * GA_STAGE;
-    if (diag) blk.template mma<true>(sa, sa);
-    else blk.mma(sa, sa + GA_TK * GA_LD);
-  }
+    for (int s = 0; s < GA_NS - 1; ++s) {
+      if (s < ntile) load_stage(s, s);
+      cp_async_commit();
+    }
+    for (int t = 0; t < ntile; ++t) {
+      cp_async_wait<GA_NS - 2>();  // this thread's copies of stage t have landed
+      __syncthreads();             // everyone's have, and stage t - 1's slot is free
+      const int tn = t + GA_NS - 1;
+      if (tn < ntile) load_stage(tn, tn % GA_NS);
+      cp_async_commit();
+      consume(gas + (t % GA_NS) * GA_STAGE);
+    }
+  };
   const int ntiles = T * (T + 1) / 2;
   float* out = part + ((int64_t)split * ntiles + blockIdx.x) * (128 * 128);
+  if (diag) {
+    const DiagBlocks db(tid, blockIdx.x + blockIdx.y);
+    unsigned long long d[3][4][2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) d[b][u][0] = d[b][u][1] = 0ull;
+    run([&](const float* sa) {
+      if (db.extra) {
+#pragma unroll
+        for (int k = 0; k < GA_TK; ++k)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) diag_block_step(sa + k * GA_LD, db.ra[b], db.cb[b], d[b]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < GA_TK; ++k)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) diag_block_step(sa + k * GA_LD, db.ra[b], db.cb[b], d[b]);
+      }
+    });
+    // lanes >= 16 of the extra warp computed a copy of lane - 16's block
+    const int nb = db.extra && (tid & 31) < 16 ? 3 : 2;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b < nb) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 f0 = unpack2(d[b][u][0]), f1 = unpack2(d[b][u][1]);
+          *reinterpret_cast<float4*>(out + (db.ra[b] + u) * 128 + db.cb[b]) = make_float4(f0.x, f0.y, f1.x, f1.y);
+        }
+      }
+    }
+    return;
+  }
+  Block<128, 128, 8, 8> blk;
+  blk.init();
+  run([&](const float* sa) { blk.mma(sa, sa + GA_TK * GA_LD); });
 #pragma unroll
   for (int u = 0; u < 8; ++u)
 #pragma unroll
