@@ -41,7 +41,24 @@ constexpr int DG_T = 32, DG_K = 16, DG_THREADS = 256, DG_MAXSPLIT = 8;
 struct FF {
   float hi, lo;
 };
+// x = hi + lo: hi is x with its significand cut to the leading 24 bits and
+// lo the remaining 29-bit integer of the significand, rounded to 24 bits and
+// scaled by the exact power of two 2^(e - 1075) (e the biased exponent), so
+// hi + lo = x to 2^-48 relative.  Both come from the bit pattern on the
+// integer and float32 pipes: float64 conversions and arithmetic would run on
+// B300's float64 pipe, about two per clock per SM, and every CTA splits its
+// whole share of both operands.  Outside 949 <= e <= 1150 (|x| < 2^-74, where
+// lo leaves float32's normal range, or |x| >= 2^128) the float64 conversions.
 __device__ __forceinline__ FF ff_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)(b >> 52) & 0x7FF;
+  if ((unsigned)(e - 949) <= 201u) {
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu));
+    const float scale = __uint_as_float(sign | ((unsigned)(e - 948) << 23));  // +-2^(e - 1075)
+    return {hi, __uint2float_rn((unsigned)b & 0x1FFFFFFFu) * scale};
+  }
+  if ((b << 1) == 0) return {0.f, 0.f};  // +-0
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - (double)h)};
 }
