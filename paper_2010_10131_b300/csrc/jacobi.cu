@@ -684,9 +684,11 @@ int cholqr3_f32(float* Y, float* T, float* Q, int64_t n, int m, RRBufs& b, cudaS
 // order, orthonormal to float32 accuracy) and returns ATK_OK; returns
 // ATK_ENOCONV to request the full Jacobi.
 int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double* Qblk, int* dev_status,
-           char* scratch, size_t scratch_bytes, cudaStream_t st, bool floor_ok, bool* at_floor, bool* tight) {
+           char* scratch, size_t scratch_bytes, cudaStream_t st, bool floor_ok, bool* at_floor, bool* tight,
+           double* theta_cut) {
   *at_floor = false;
   *tight = false;
+  *theta_cut = 0.0;
   Arena ar{scratch, scratch_bytes, 0};
   RRBufs b;
   size_t nm = (size_t)n * m, mm = (size_t)m * m;
@@ -793,6 +795,7 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
     // the residual, so the residual itself must be small too.)
     *tight = !floor_ok && predicted <= RR_TARGET && (int)h[5] == R && h[2] - h[6] >= RR_LIGHT_GAP * h[1] &&
              res <= RR_LIGHT_RES * (thK - thm);
+    *theta_cut = h[6];
     if (predicted <= RR_TARGET || accept || (floor_here && power >= RR_MAX_POWER)) {
       f32_to_f64_kernel2<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(b.Y, Qblk, n * (int64_t)m);
       ATK_LAUNCHED();
@@ -1232,9 +1235,11 @@ static int eig_level(const double* S, int64_t n, int64_t R, int arith, int metho
   char* rest = scratch + ar.used;
   const size_t rest_bytes = scratch_bytes - ar.used;
   *lv = Level{Qb, k, rest, rest_bytes, false, false};
+  double theta_cut = 0.0;  // float32 Ritz value R + 1 (rr_top)
   int s = ATK_ENOCONV;
   if (rr) {
-    s = rr_top(S, n, R, m, max_sweeps, Qb, dev_status, rest, rest_bytes, st, wide, &lv->at_floor, &lv->tight);
+    s = rr_top(S, n, R, m, max_sweeps, Qb, dev_status, rest, rest_bytes, st, wide, &lv->at_floor, &lv->tight,
+               &theta_cut);
     if (s != ATK_OK && s != ATK_ENOCONV) return s;
     if (s == ATK_OK && lambda_out && n > R) {
       // Only the kept eigenvalues exist on this path; the tail is marked NaN.
@@ -1255,11 +1260,18 @@ static int eig_level(const double* S, int64_t n, int64_t R, int arith, int metho
   }
   // The refinement: no host synchronisation inside, so one cached graph per
   // (buffers, sizes, form).
+  // The light finish refines the R kept columns only: both of its
+  // orthonormalisations build column j from columns <= j, so the guard
+  // columns do not enter the kept ones, and with the gap its gate demands no
+  // guard can overtake a kept column in the ordering.  The value past the cut
+  // that eig_top's gap test reads is the float32 Ritz value theta_R (the gate
+  // puts the gap at >= RR_LIGHT_GAP theta_1, far above that value's error).
   if (s == ATK_OK && rr && lv->tight) {
+    if (lam_sorted) ATK_CUDA(cudaMemcpyAsync(lam_sorted + R, &theta_cut, sizeof(double), cudaMemcpyHostToDevice, st));
     const GraphKey lkey{{S, Qb, U64, lambda_out, discarded_out, lam_sorted, rest, (const void*)5},
-                        {n, k, R, (int64_t)rest_bytes}};
+                        {n, R, R, (int64_t)rest_bytes}};
     return run_graph(lkey, st, [&](cudaStream_t s2) -> int {
-      return refine_light(S, n, Qb, k, R, U64, lambda_out, discarded_out, lam_sorted, rest, rest_bytes, s2);
+      return refine_light(S, n, Qb, R, R, U64, lambda_out, discarded_out, lam_sorted, rest, rest_bytes, s2);
     });
   }
   lv->tight = false;
