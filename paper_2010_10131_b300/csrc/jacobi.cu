@@ -220,15 +220,17 @@ __global__ void __launch_bounds__(256) jacobi_block_kernel(BlockJacobiArgs args,
 // Sort eigenvalues descending (stable in index), keep the first R vectors,
 // sign each so that its largest-magnitude entry is positive (ties: lowest
 // row), write U (n x R column-major, float64), all eigenvalues (descending)
-// and the discarded sum.  One CTA.  V is row-major with leading dimension ldv.
+// and the discarded sum.  One CTA, a warp per selected column.  V is row-major
+// with leading dimension ldv.
+constexpr int SEL_THREADS = 1024;
 template <typename T>
-__global__ void __launch_bounds__(256) select_kernel(const T* __restrict__ diag, int64_t dstride,
+__global__ void __launch_bounds__(SEL_THREADS) select_kernel(const T* __restrict__ diag, int64_t dstride,
                                                      const T* __restrict__ V, int ldv, int n, int R,
                                                      double* __restrict__ U, double* __restrict__ lam_out,
                                                      double* __restrict__ disc_out) {
   __shared__ int order[1024];
   __shared__ T lam[1024];
-  __shared__ double wsum[8];
+  __shared__ double wsum[SEL_THREADS / 32];
   // Sort key: the eigenvalue, with NaN ordered below everything, ties broken by
   // index.  That is a total order, so the ranks below are a permutation of
   // 0..n-1 whatever the input holds, and every gathered column stays in range.
@@ -351,7 +353,7 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
     ATK_TRY(raise_smem_limit((const void*)jacobi_small_kernel<T>, sm));
     jacobi_small_kernel<T><<<1, 256, sm, st>>>(S, (int)n, m, max_sweeps, diag, V, dev_status);
     ATK_LAUNCHED();
-    select_kernel<T><<<1, 256, 0, st>>>(diag, 1, V, (int)n, (int)n, (int)R, U64, lam_out, nullptr);
+    select_kernel<T><<<1, SEL_THREADS, 0, st>>>(diag, 1, V, (int)n, (int)n, (int)R, U64, lam_out, nullptr);
     ATK_LAUNCHED();
     return ATK_OK;
   }
@@ -395,7 +397,7 @@ int eig_top_t(const double* S, int64_t n, int64_t R, int max_sweeps, double* U64
   void* kargs[] = {(void*)&args, (void*)&A, (void*)&V, (void*)&W, (void*)&fro};
   ATK_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_block_kernel<T>, dim3(grid), dim3(256), kargs, sm, st));
   count_launch();
-  select_kernel<T><<<1, 256, 0, st>>>(A, (int64_t)m + 1, V, m, (int)n, (int)R, U64, lam_out, nullptr);
+  select_kernel<T><<<1, SEL_THREADS, 0, st>>>(A, (int64_t)m + 1, V, m, (int)n, (int)R, U64, lam_out, nullptr);
   ATK_LAUNCHED();
   return ATK_OK;
 }
@@ -560,35 +562,51 @@ __global__ void shift_axpy_kernel(float* __restrict__ Y, const float* __restrict
   if (i < count) Y[i] = fmaf(sigma, X[i], Y[i]);
 }
 
-// Normalise each column of Y (n x m) to unit length; one warp per column.
-__global__ void colnorm_f32_kernel(float* __restrict__ Y, int64_t n, int64_t m) {
-  const int64_t col = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x % 32;
-  if (col >= m) return;
-  float* y = Y + n * col;
+// Column kernels of the eigensolver: one CTA of COL_THREADS threads per
+// column (a warp per column left each of them 20 dependent trips to L2 at
+// I_n = 640).  Per-thread strided partial sums, then warp shuffles and the
+// warps' sums in warp order: a fixed order, so results do not depend on
+// scheduling.
+constexpr int COL_THREADS = 128;
+constexpr int COL_WARPS = COL_THREADS / 32;
+__device__ __forceinline__ double col_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x % 32 == 0) sh[threadIdx.x / 32] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < COL_WARPS; ++w) t += sh[w];
+  __syncthreads();  // sh is free for the next reduction
+  return t;
+}
+
+// Normalise each column of Y (n x m) to unit length; one CTA per column.
+__global__ void __launch_bounds__(COL_THREADS) colnorm_f32_kernel(float* __restrict__ Y, int64_t n) {
+  __shared__ double sh[COL_WARPS];
+  float* y = Y + n * blockIdx.x;
   double s = 0.0;
-  for (int64_t i = lane; i < n; i += 32) s += (double)y[i] * y[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  float inv = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f;
-  for (int64_t i = lane; i < n; i += 32) y[i] *= inv;
+  for (int64_t i = threadIdx.x; i < n; i += COL_THREADS) s += (double)y[i] * y[i];
+  s = col_sum(s, sh);
+  const float inv = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f;
+  for (int64_t i = threadIdx.x; i < n; i += COL_THREADS) y[i] *= inv;
 }
 
 
-// res[j] = ||Z[:, j] - theta_j Q[:, j]|| for j < R; one warp per column.
-__global__ void ritz_residual_kernel(const float* __restrict__ Z, const float* __restrict__ Q,
-                                     const double* __restrict__ theta, int64_t n, int64_t R,
-                                     double* __restrict__ res) {
-  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x % 32;
-  if (j >= R) return;
+// res[j] = ||Z[:, j] - theta_j Q[:, j]|| for j < R; one CTA per column.
+__global__ void __launch_bounds__(COL_THREADS) ritz_residual_kernel(const float* __restrict__ Z,
+                                                                     const float* __restrict__ Q,
+                                                                     const double* __restrict__ theta, int64_t n,
+                                                                     double* __restrict__ res) {
+  __shared__ double sh[COL_WARPS];
+  const int64_t j = blockIdx.x;
   const double th = theta[j];
   double s = 0.0;
-  for (int64_t i = lane; i < n; i += 32) {
-    double d = (double)Z[i + n * j] - th * Q[i + n * j];
+  for (int64_t i = threadIdx.x; i < n; i += COL_THREADS) {
+    const double d = (double)Z[i + n * j] - th * Q[i + n * j];
     s += d * d;
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) res[j] = sqrt(s);
+  s = col_sum(s, sh);
+  if (threadIdx.x == 0) res[j] = sqrt(s);
 }
 
 // K = the number of leading Ritz values (theta descending) at or above
@@ -661,7 +679,7 @@ int sq_product(const float* Sf, int64_t n, const float* Q, int m, float* out, RR
 // normalising the columns of Y (in place).
 int cholqr_pass_f32(float* Y, float* Q, int64_t n, int m, float shift, RRBufs& b, cudaStream_t st) {
   const View v{n, m, 1};
-  colnorm_f32_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Y, n, m);
+  colnorm_f32_kernel<<<(unsigned)m, COL_THREADS, 0, st>>>(Y, n);
   ATK_LAUNCHED();
   ATK_TRY(gram_f32(Y, v, b.G, b.part, b.part_bytes, st));
   ATK_TRY(cholinv_f32(b.G, m, shift, b.LinvT, b.breakdown, st));
@@ -749,12 +767,12 @@ int rr_top(const double* S, int64_t n, int64_t R, int m, int max_sweeps, double*
       ATK_TRY(sq_product(b.Sf, n, b.Q, m, b.Z, b, s2));
       ATK_TRY(cross_f32(b.Q, qv, b.Z, m, b.G, b.part, b.part_bytes, s2));
       ATK_TRY(tridiag_eig_f32(b.G, m, b.diag, b.Vb, s2));
-      select_kernel<float><<<1, 256, 0, s2>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
+      select_kernel<float><<<1, SEL_THREADS, 0, s2>>>(b.diag, 1, b.Vb, m, m, m, b.W64, b.theta, nullptr);
       ATK_LAUNCHED();
       ATK_TRY(f64_to_f32(b.W64, b.Wf, (int64_t)mm, s2));
       ATK_TRY(ttm_f32(b.Q, qv, b.Wf, m, b.Y, s2));
       ATK_TRY(ttm_f32(b.Z, qv, b.Wf, m, b.T, s2));
-      ritz_residual_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, s2>>>(b.T, b.Y, b.theta, n, R, b.res);
+      ritz_residual_kernel<<<(unsigned)R, COL_THREADS, 0, s2>>>(b.T, b.Y, b.theta, n, b.res);
       ATK_LAUNCHED();
       ritz_summary_kernel<<<1, 32, 0, s2>>>(b.res, b.theta, (int)R, m, b.breakdown, b.summary);
       ATK_LAUNCHED();
@@ -988,9 +1006,9 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   // 1. subspace steps (none: only orthonormalise Qb)
   for (int step = 0; step < subspace_steps; ++step) {
     ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
-    colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
+    colnorms_f64_kernel<<<(unsigned)k, COL_THREADS, 0, st>>>(Z, Qb, n, k, norms, norms + k);
     ATK_LAUNCHED();
-    normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k, keep_rel,
+    normalize_cols_kernel<<<(unsigned)k, COL_THREADS, 0, st>>>(Z, Qb, n, k, norms, norms + k, keep_rel,
                                                                           0.9, Qb);
     ATK_LAUNCHED();
     // Orthonormalise in Gram-Schmidt order (column j against the columns
@@ -1037,7 +1055,7 @@ int refine_f64(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, dou
   gather_cols_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(QW, order, n, R, U64);
   ATK_LAUNCHED();
   ATK_TRY(polar_step_f64(U64, n, R, pol, st));
-  sign_fix_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(U64, n, R);
+  sign_fix_kernel<<<(unsigned)R, COL_THREADS, 0, st>>>(U64, n, R);
   ATK_LAUNCHED();
   return ATK_OK;
 }
@@ -1085,14 +1103,14 @@ int refine_light(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, d
   if (!pol) { set_error("eig: scratch too small for the refinement"); return ATK_EINVAL; }
   // 1. Z = S Qb and the Rayleigh quotients of the float32 columns
   ATK_TRY(gemm_f64(S, Qb, n, n, k, Z, st));
-  colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k);
+  colnorms_f64_kernel<<<(unsigned)k, COL_THREADS, 0, st>>>(Z, Qb, n, k, norms, norms + k);
   ATK_LAUNCHED();
-  colnorms_f64_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Qb, nullptr, n, k, qn, nullptr);
+  colnorms_f64_kernel<<<(unsigned)k, COL_THREADS, 0, st>>>(Qb, nullptr, n, k, qn, nullptr);
   ATK_LAUNCHED();
   rq_diag_kernel<<<(unsigned)ceil_div(k * k, 256), 256, 0, st>>>(norms + k, qn, k, B);
   ATK_LAUNCHED();
   // 2. subspace step and orthonormalisation in Gram-Schmidt order
-  normalize_cols_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(Z, Qb, n, k, norms, norms + k, 1e-5, 0.9,
+  normalize_cols_kernel<<<(unsigned)k, COL_THREADS, 0, st>>>(Z, Qb, n, k, norms, norms + k, 1e-5, 0.9,
                                                                         Qb);
   ATK_LAUNCHED();
   ATK_TRY(gemm_tn_f64(Qb, Qb, n, k, T, st));
@@ -1106,7 +1124,7 @@ int refine_light(const double* S, int64_t n, double* Qb, int64_t k, int64_t R, d
   ATK_LAUNCHED();
   gather_cols_kernel<<<(unsigned)ceil_div(n * R, 256), 256, 0, st>>>(Qb, order, n, R, U64);
   ATK_LAUNCHED();
-  sign_fix_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(U64, n, R);
+  sign_fix_kernel<<<(unsigned)R, COL_THREADS, 0, st>>>(U64, n, R);
   ATK_LAUNCHED();
   return ATK_OK;
 }
@@ -1134,22 +1152,20 @@ size_t eig_scratch_bytes(int64_t n, int arith) {
 // One warp per column.
 __global__ void colnorms_f64_kernel(const double* __restrict__ Z, const double* __restrict__ U, int64_t n, int64_t R,
                                     double* __restrict__ norms, double* __restrict__ dots) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
-  if (warp >= R) return;
-  const double* z = Z + (int64_t)warp * n;
-  const double* u = U ? U + (int64_t)warp * n : nullptr;
+  __shared__ double sh[COL_WARPS];
+  const int64_t j = blockIdx.x;
+  const double* z = Z + j * n;
+  const double* u = U ? U + j * n : nullptr;
   double s = 0.0, d = 0.0;
-  for (int64_t i = lane; i < n; i += 32) {
+  for (int64_t i = threadIdx.x; i < n; i += COL_THREADS) {
     s += z[i] * z[i];
     if (u) d += u[i] * z[i];
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_xor_sync(0xffffffffu, s, o);
-    d += __shfl_xor_sync(0xffffffffu, d, o);
-  }
-  if (lane == 0) {
-    norms[warp] = sqrt(s);
-    if (dots) dots[warp] = d;
+  s = col_sum(s, sh);
+  if (u) d = col_sum(d, sh);
+  if (threadIdx.x == 0) {
+    norms[j] = sqrt(s);
+    if (dots) dots[j] = d;
   }
 }
 
@@ -1161,49 +1177,59 @@ __global__ void colnorms_f64_kernel(const double* __restrict__ Z, const double* 
 // null-space or small-eigenvalue Ritz vector with float32 errors along the
 // leading directions) is not improved by S u; normalising would turn that
 // leakage into a near copy of a leading direction.  Such columns keep their
-// vectors.  One warp per column; W may be U (each element is read and then
+// vectors.  One CTA per column; W may be U (each element is read and then
 // written by the same thread).
 __global__ void normalize_cols_kernel(const double* __restrict__ Z, const double* U, int64_t n, int64_t R,
                                       const double* __restrict__ norms, const double* __restrict__ dots, double rel,
                                       double min_ratio, double* W) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
-  if (warp >= R) return;
+  __shared__ double sh[COL_WARPS];
+  const int64_t j = blockIdx.x;
   double mx = 0.0;
-  for (int64_t r = lane; r < R; r += 32) mx = fmax(mx, norms[r]);
+  for (int64_t r = threadIdx.x; r < R; r += COL_THREADS) mx = fmax(mx, norms[r]);
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x % 32 == 0) sh[threadIdx.x / 32] = mx;
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < COL_WARPS; ++w) mx = fmax(mx, sh[w]);
   const double thr = rel * mx;
-  const double* z = Z + (int64_t)warp * n;
-  double nz = norms[warp];
-  double* w = W + (int64_t)warp * n;
-  if (nz > thr && (!dots || dots[warp] >= min_ratio * nz)) {
+  const double* z = Z + j * n;
+  const double nz = norms[j];
+  double* w = W + j * n;
+  if (nz > thr && (!dots || dots[j] >= min_ratio * nz)) {
     const double inv = 1.0 / nz;
-    for (int64_t i = lane; i < n; i += 32) w[i] = z[i] * inv;
+    for (int64_t i = threadIdx.x; i < n; i += COL_THREADS) w[i] = z[i] * inv;
   } else {
-    const double* u = U + (int64_t)warp * n;
-    for (int64_t i = lane; i < n; i += 32) w[i] = u[i];
+    const double* u = U + j * n;
+    for (int64_t i = threadIdx.x; i < n; i += COL_THREADS) w[i] = u[i];
   }
 }
 
 // Sign rule: flip each column so that its largest-magnitude entry is positive
-// (ties: lowest row).  One warp per column.
+// (ties: lowest row).  One CTA per column.
 __global__ void sign_fix_kernel(double* __restrict__ U, int64_t n, int64_t R) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
-  if (warp >= R) return;
-  double* u = U + (int64_t)warp * n;
+  __shared__ double sbest[COL_WARPS];
+  __shared__ int64_t sarg[COL_WARPS];
+  double* u = U + (int64_t)blockIdx.x * n;
   double best = -1.0;
   int64_t arg = 0;
-  for (int64_t i = lane; i < n; i += 32) {
-    double a = fabs(u[i]);
+  for (int64_t i = threadIdx.x; i < n; i += COL_THREADS) {
+    const double a = fabs(u[i]);
     if (a > best) { best = a; arg = i; }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    double ob = __shfl_down_sync(0xffffffffu, best, o);
-    int64_t oa = __shfl_down_sync(0xffffffffu, arg, o);
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int64_t oa = __shfl_xor_sync(0xffffffffu, arg, o);
     if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
   }
-  arg = __shfl_sync(0xffffffffu, arg, 0);
-  if (u[arg] < 0.0)
-    for (int64_t i = lane; i < n; i += 32) u[i] = -u[i];
+  if (threadIdx.x % 32 == 0) { sbest[threadIdx.x / 32] = best; sarg[threadIdx.x / 32] = arg; }
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < COL_WARPS; ++w)
+    if (sbest[w] > best || (sbest[w] == best && sarg[w] < arg)) { best = sbest[w]; arg = sarg[w]; }
+  const bool neg = u[arg] < 0.0;
+  __syncthreads();  // every thread has read u[arg] before any flips it
+  if (neg)
+    for (int64_t i = threadIdx.x; i < n; i += COL_THREADS) u[i] = -u[i];
 }
 
 // One level of the eigensolver: the R leading eigenvectors of the symmetric
