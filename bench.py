@@ -40,7 +40,7 @@ UNIT = "GB/s"
 TENSORS = [((640, 640, 640), (64, 64, 64)), ((128, 128, 128, 128), (16, 16, 16, 16))]
 WORKLOAD = "plain FP32 st-HOSVD (EIG every mode): 640^3 R64 + 128^4 R16, random Tucker + 1e-3 noise"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
-GRAM_TRAFFIC_RATIO = 1.07  # DRAM bytes / input bytes per Gram launch (ncu capture of the mode-1 Gram)
+GRAM_TRAFFIC_RATIO = 1.19  # DRAM read + write bytes / input bytes per Gram launch (ncu, mode-1 Gram)
 CPU_SAMPLE = ((640, 640, 8), (64, 64, 8))       # cpu_baseline: a 640 x 640 x 8 slab of the workload
 REF_SAMPLE = ((640, 160, 8), (64, 64, 8))       # reference arm: one such slab sample per step
 
@@ -284,10 +284,11 @@ def run_ours(args):
 
     # Dominant kernel: the Gram partial-tile kernel (float32 CUDA cores).
     # DRAM traffic per Gram call, scaled from one ncu capture of a smaller view
-    # of the mode-1 Gram: each launch reads its input once (measured traffic /
-    # input bytes = 1.07).  A contiguous mode-1 view (lo == 1, I_n % 4 == 0)
-    # runs all its tiles in one launch; a strided view with more than 128 rows
-    # makes two (diagonal and off-diagonal tiles), each reading the input.
+    # of the mode-1 Gram: each launch reads its input about once (measured read
+    # + write / input bytes = 1.19; the writes are the split-K partial tiles).
+    # A contiguous mode-1 view (lo == 1, I_n % 4 == 0) runs all its tiles in
+    # one launch; a strided view with more than 128 rows makes two (diagonal
+    # and off-diagonal tiles), each reading the input.
     calls, traffic_bytes, alg_bytes = 0, 0.0, 0.0
     for d, r in TENSORS:
         cur = list(d)
@@ -408,7 +409,9 @@ def run_ours(args):
                        "execution": "the tensors' plans run concurrently (atucker_sthosvd_many), one stream each, "
                                     "the 640^3 tensor's at the highest priority",
                        "serial_ms_per_step": serial_ms},
-            "roofline": {"bound": "alu", "kernel": "gram_ci_kernel (float32 FMA)",
+            "roofline": {"bound": "alu",
+                         "kernel": "FP32 Gram (gram_async_kernel for contiguous mode-1 views, gram_ci_kernel for "
+                                   "strided ones; float32 FMA)",
                          "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": (achieved / FP32_ALU_PEAK_TFLOPS) if achieved else None,
                          "timed_in": "serial leg of this run (one tensor at a time, same steps), so each Gram "
@@ -416,7 +419,7 @@ def run_ours(args):
                          "achieved_concurrent": achieved_conc,
                          "traffic": traffic_bytes / calls, "traffic_unit": "bytes per Gram call",
                          "algorithmic_bytes": alg_bytes / calls,
-                         "traffic_source": "scaled from ncu dram bytes of gram:1,640,80000 (ratio 1.07 x input)",
+                         "traffic_source": "scaled from ncu dram read + write bytes of gram:1,640,80000 (ratio 1.19 x input)",
                          "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
                          "flops_per_step": flops / max(args.steps, 1),
                          "ms_per_step": gram_ms / max(args.steps, 1)},
