@@ -180,7 +180,7 @@ typedef struct atucker_plan_s* atucker_plan_t;
  *                    exhaustive search, Sec. IV): with no selector loaded,
  *                    every class that can run the mode; with the network,
  *                    its best class and up to two more whose predicted log2
- *                    times are within 0.3 of it (about 23 %).  That call runs
+ *                    times are within 2 of it (4 x).  That call runs
  *                    each candidate twice (warm-up, then timed with CUDA
  *                    events), keeps each mode's fastest, and caches the choice
  *                    for the process, keyed by shape, ranks, order and the

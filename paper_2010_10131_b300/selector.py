@@ -251,7 +251,7 @@ def regret(T, chosen):
 # The product path's policy (atucker_plan_create): the network's best class
 # and up to SEARCH_MAX - 1 more predicted within SEARCH_MARGIN log2 units of
 # it are timed at the plan's first run, which keeps the fastest.
-SEARCH_MARGIN = 0.3
+SEARCH_MARGIN = 2.0
 SEARCH_MAX = 3
 
 
