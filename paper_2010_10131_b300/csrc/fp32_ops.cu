@@ -727,6 +727,117 @@ ttm_co_kernel(const float* __restrict__ y, int64_t lo, int64_t n, int64_t hi, co
   }
 }
 
+// ------------------------------------------- cp.async-fed TTM (mode-1 views)
+// O(c, r) = sum_i Y(c, i) U(i, r) for a view whose rows c are I_n contiguous
+// floats (lo == 1, I_n % 4 == 0, Y and U 16-byte aligned).  Both operands
+// are staged as they lie in memory: a row c of Y and a column r of U each
+// hold the stage's TA_KS consecutive values of i, moved by 16-byte cp.async
+// copies into shared rows of TA_LD floats.  That is one pass with no
+// transpose and no register staging (the ttm_co_kernel loader transposes
+// through registers into k-major tiles, and its stores conflict).  The ring
+// holds TA_NS stages, TA_NS - 1 of them in flight.  A thread takes rows
+// m = u TY + ty and columns r = v TX + tx (interleaved, so a warp's rows fall
+// in different banks), reads each row's or column's fragment four values of i
+// at a time (one 128-bit load), then takes the four outer products: the same
+// two 128-bit loads per k for eight rows as a k-major tile.  Rows past J,
+// columns past R and (n % 4 == 0) whole chunks past I_n are zero-filled.
+// Used for R <= 32, where the TTM is bound by the movement of Y: against
+// ttm_co_kernel, 128 x 2097152 R 16 0.45 -> 0.32 ms, 48 x 5308416 R 8
+// 0.48 -> 0.32 ms, 640 x 409600 R 32 0.60 -> 0.48 ms.  At R = 64 the FMAs
+// dominate, and there the k-major register block with packed FMAs is faster
+// (0.81 against 1.10 ms): its column pairs come straight from one load, where
+// here they would have to be assembled from two.
+constexpr int TA_KS = 16;          // values of i per stage
+constexpr int TA_LD = TA_KS + 4;   // row pitch in floats: 16-byte aligned rows, spread over the banks
+constexpr int TA_NS = 4;
+template <int BM, int BN>
+constexpr int ttm_async_smem() { return TA_NS * (BM + BN) * TA_LD * (int)sizeof(float); }
+
+template <int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(NT, 2)
+ttm_async_kernel(const float* __restrict__ y, int n, int64_t J, const float* __restrict__ U, int R,
+                 float* __restrict__ out) {
+  constexpr int TX = BN / TN, TY = BM / TM;
+  static_assert(TX * TY == NT, "thread grid must cover 256 threads");
+  constexpr int STAGE = (BM + BN) * TA_LD;
+  constexpr int CHUNKS = (BM + BN) * (TA_KS / 4);
+  extern __shared__ __align__(16) float tas[];
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  const int64_t c0 = (int64_t)blockIdx.x * BM;
+  const int r0 = (int)blockIdx.y * BN;
+  const int ntile = (n + TA_KS - 1) / TA_KS;
+  auto load_stage = [&](int t, int slot) {
+    float* s = tas + slot * STAGE;
+    const int i0 = t * TA_KS;
+#pragma unroll
+    for (int q0 = 0; q0 < CHUNKS; q0 += NT) {
+      const int q = q0 + tid;
+      if (q < CHUNKS) {
+        const int row = q / (TA_KS / 4), ch = q % (TA_KS / 4);
+        const int i = i0 + 4 * ch;
+        const float* src;
+        bool ok;
+        if (row < BM) {
+          const int64_t c = c0 + row;
+          ok = c < J && i < n;
+          src = y + (i + (int64_t)n * c);
+        } else {
+          const int r = r0 + (row - BM);
+          ok = r < R && i < n;
+          src = U + (i + (int64_t)n * r);
+        }
+        cp_async16(ac::smem_u32(s + row * TA_LD + 4 * ch), ok ? src : y, ok ? 16u : 0u);
+      }
+    }
+  };
+  float acc[TM][TN];
+#pragma unroll
+  for (int u = 0; u < TM; ++u)
+#pragma unroll
+    for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
+#pragma unroll
+  for (int s = 0; s < TA_NS - 1; ++s) {
+    if (s < ntile) load_stage(s, s);
+    cp_async_commit();
+  }
+  for (int t = 0; t < ntile; ++t) {
+    cp_async_wait<TA_NS - 2>();  // this thread's copies of stage t have landed
+    __syncthreads();             // everyone's have, and stage t - 1's slot is free
+    const int tn = t + TA_NS - 1;
+    if (tn < ntile) load_stage(tn, tn % TA_NS);
+    cp_async_commit();
+    const float* sa = tas + (t % TA_NS) * STAGE;
+    const float* sb = sa + BM * TA_LD;
+#pragma unroll
+    for (int g = 0; g < TA_KS / 4; ++g) {
+      float4 a[TM], b[TN];
+#pragma unroll
+      for (int u = 0; u < TM; ++u) a[u] = *reinterpret_cast<const float4*>(sa + (u * TY + ty) * TA_LD + 4 * g);
+#pragma unroll
+      for (int v = 0; v < TN; ++v) b[v] = *reinterpret_cast<const float4*>(sb + (v * TX + tx) * TA_LD + 4 * g);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        auto el = [kk](const float4& f) { return kk == 0 ? f.x : kk == 1 ? f.y : kk == 2 ? f.z : f.w; };
+#pragma unroll
+        for (int u = 0; u < TM; ++u)
+#pragma unroll
+          for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(el(a[u]), el(b[v]), acc[u][v]);
+      }
+    }
+  }
+  // O(c, r) at c R + r (lo == 1): lanes along r.
+#pragma unroll
+  for (int u = 0; u < TM; ++u) {
+    const int64_t c = c0 + u * TY + ty;
+    if (c >= J) continue;
+#pragma unroll
+    for (int v = 0; v < TN; ++v) {
+      const int r = r0 + v * TX + tx;
+      if (r < R) out[c * R + r] = acc[u][v];
+    }
+  }
+}
+
 // ------------------------------------------------------------ host side
 int gram_tile(int64_t n) { return n > 64 ? 128 : (n > 32 ? 64 : 32); }
 
@@ -937,9 +1048,33 @@ int cross_f32(const float* y, const View& v, const float* P, int64_t R, double* 
   return ATK_OK;
 }
 
+namespace {
+template <int BM, int BN, int TM, int TN>
+int launch_ttm_async(const float* y, const View& v, const float* U, int64_t R, float* out, cudaStream_t st) {
+  constexpr int smem = ttm_async_smem<BM, BN>();
+  static const bool attr_ok =
+      cudaFuncSetAttribute(ttm_async_kernel<BM, BN, TM, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+      cudaSuccess;
+  if (!attr_ok) {
+    set_error("ttm: cannot set the shared-memory size of the cp.async TTM kernel");
+    return ATK_ECUDA;
+  }
+  const dim3 grid((unsigned)ceil_div(v.J(), BM), (unsigned)ceil_div(R, BN));
+  ttm_async_kernel<BM, BN, TM, TN><<<grid, NT, smem, st>>>(y, (int)v.n, v.J(), U, (int)R, out);
+  ATK_LAUNCHED();
+  return ATK_OK;
+}
+}  // namespace
+
 int ttm_f32(const float* y, const View& v, const float* U, int64_t R, float* out, cudaStream_t st) {
   const int64_t J = v.J();
   if (J == 0 || R <= 0) return ATK_OK;
+  // Contiguous mode-1 views (16-byte aligned Y and U) with R <= 32 and at
+  // least a CTA per SM: the cp.async-fed kernel.
+  if (kc_vec_ok(y, v) && (reinterpret_cast<uintptr_t>(U) & 15) == 0 && R <= 32) {
+    if (R <= 16 && ceil_div(J, 256) >= num_sms()) return launch_ttm_async<256, 16, 8, 2>(y, v, U, R, out, st);
+    if (R > 16 && ceil_div(J, 128) >= num_sms()) return launch_ttm_async<128, 32, 8, 2>(y, v, U, R, out, st);
+  }
   int bn = cross_bn(R);
   dim3 grid((unsigned)ceil_div(J, 128), (unsigned)ceil_div(R, bn));
   if ((int64_t)grid.x * grid.y < num_sms() / 2) {

@@ -73,6 +73,22 @@ def test_ttm_matches_oracle(atk, lo, n, hi, R):
     assert np.abs(out - ref).max() <= 1e-5 * np.sqrt(n) * np.abs(ref).max() + 1e-6
 
 
+# Contiguous mode-1 views large enough (a CTA per SM) for the cp.async-fed
+# TTM: both column classes (R <= 16, <= 32) with R not a multiple of the
+# column tile, J ragged against the row tile, I_n % 16 != 0 (a stage half
+# past I_n) and I_n = 4 (one chunk per row); R = 50 and 64 check that larger
+# ranks keep the k-major kernel.
+@pytest.mark.parametrize("n,J,R", [(68, 40001, 12), (128, 39000, 16), (36, 20011, 20), (100, 19999, 32),
+                                   (52, 19000, 50), (640, 19457, 64), (4, 40000, 3)])
+def test_ttm_async_form_matches_oracle(atk, n, J, R):
+    g = np.random.default_rng(n * 31 + J + R)
+    y = g.standard_normal(n * J).astype(np.float32)
+    U = g.standard_normal((n, R)).astype(np.float32)
+    out = atk.ttm(_cuda(y), 1, n, J, _cuda(U)).cpu().numpy()
+    ref = oracle.ttm(y.astype(np.float64), [n, J], 0, U.astype(np.float64))
+    assert np.abs(out - ref).max() <= 1e-5 * np.sqrt(n) * np.abs(ref).max() + 1e-6
+
+
 def _spd_with_gap(n, R, seed):
     g = np.random.default_rng(seed)
     Q = np.linalg.qr(g.standard_normal((n, n)))[0]
