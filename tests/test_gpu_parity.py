@@ -43,6 +43,8 @@ GRAM_VIEWS = [
     (3, 1, 11),        # n == 1
     (1, 17, 1),        # J == 1
     (33, 130, 5),      # n just over a tile, lo odd
+    (5, 300, 40),      # strided, three tile rows: all six tiles in one launch
+    (64, 257, 30),     # strided, the third tile row holds one row
     (1, 48, 100003),   # small-I_n form: 6 x 6 blocks, ragged last split
     (1, 64, 50000),    # small-I_n form: 8 x 8 blocks, two-warp groups
     (1, 60, 12345),    # small-I_n form: columns 60..63 zero-filled
