@@ -121,50 +121,10 @@ struct Block {
           if (!(SKIP_LOWER && TN > 1 && u >= TM / 2 && v < TN / 2)) acc1[u][v] = fmaf(a[u], b[v], acc1[u][v]);
     }
   }
-  // Split form of step(): fetch the fragments of row k, then the outer product.
-  template <int LDA, int LDB>
-  __device__ __forceinline__ void frag(const float* sa, const float* sb, int k, float* a, float* b) const {
-    ld<TM / 2>(a, sa + k * LDA + ty * (TM / 2));
-    ld<TM / 2>(a + TM / 2, sa + k * LDA + BM / 2 + ty * (TM / 2));
-    ld<TN / 2>(b, sb + k * LDB + tx * (TN / 2));
-    ld<TN / 2>(b + TN / 2, sb + k * LDB + BN / 2 + tx * (TN / 2));
-  }
-  template <bool SKIP_LOWER>
-  __device__ __forceinline__ void outer(const float* a, const float* b) {
-    static_assert(PAIRS || SKIP_LOWER != SKIP_LOWER, "the split form needs column pairs");
-    unsigned long long b2[TN / 2];
-#pragma unroll
-    for (int p = 0; p < TN / 2; ++p) b2[p] = pack2(b[2 * p], b[2 * p + 1]);
-#pragma unroll
-    for (int u = 0; u < TM; ++u) {
-      const unsigned long long a2 = pack2(a[u], a[u]);
-#pragma unroll
-      for (int p = 0; p < TN / 2; ++p)
-        if (!(SKIP_LOWER && u >= TM / 2 && p < TN / 4)) fma2(acc2[u][p], a2, b2[p]);
-    }
-  }
-  // KT rows with the fragments of row k+1 fetched before the products of row
-  // k, so the shared-memory latency overlaps the FMAs.
-  template <bool SKIP_LOWER, int KT, int LDA, int LDB>
-  __device__ void mma_pipelined(const float* sa, const float* sb) {
-    float a[2][TM], b[2][TN];
-    frag<LDA, LDB>(sa, sb, 0, a[0], b[0]);
-#pragma unroll
-    for (int k = 0; k < KT; ++k) {
-      if (k + 1 < KT) frag<LDA, LDB>(sa, sb, k + 1, a[(k + 1) & 1], b[(k + 1) & 1]);
-      outer<SKIP_LOWER>(a[k & 1], b[k & 1]);
-    }
-  }
   template <bool SKIP_LOWER = false, int KT = TK, int LDA = BM + PAD, int LDB = BN + PAD>
   __device__ void mma(const float* sa, const float* sb) {
 #pragma unroll
     for (int k = 0; k < KT; ++k) step<SKIP_LOWER, LDA, LDB>(sa, sb, k);
-  }
-  // The first kv (< KT) rows only: a ragged last stage.
-  template <bool SKIP_LOWER, int LDA, int LDB>
-  __device__ void mma_rows(const float* sa, const float* sb, int kv) {
-#pragma unroll 1
-    for (int k = 0; k < kv; ++k) step<SKIP_LOWER, LDA, LDB>(sa, sb, k);
   }
 };
 
